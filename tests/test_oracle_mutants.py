@@ -1,0 +1,82 @@
+"""Planted mistakes in the CPU reference must fail its pins.
+
+Each case copies the reference source, plants one plausible mistake, builds
+it on the CPU and checks that the pin meant to guard that spot now fails.
+"""
+import contextlib
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+from golden import fixtures
+from paper_1711_04556_gb300.instances import Instance
+
+import test_oracle_pins as pins
+
+MUTANTS = {
+    # the loop bound printed in Algs. 5-6 (reading R1 replaces it)
+    "alg5_alg6_k_lt_M_minus_1": ("for (int k = 0; k < M; ++k)                          /* reading R1 */",
+                                 "for (int k = 0; k < M - 1; ++k)"),
+    # Eq. 6 range shortened by one position
+    "eq6_short_range": ("for (int x = u; x <= v - 1; ++x)", "for (int x = u; x <= v - 2; ++x)"),
+    # Alg. 4 line "timeDiff = newTime - max(c, s)" without the max
+    "alg4_no_max_with_s": ("int timeDiff = newTime - imax(c[resIdx], s);", "int timeDiff = newTime - c[resIdx];"),
+    # Alg. 4 shifted copy taken one element late
+    "alg4_copy_offset": ("if (copyIdx >= r) newTime", "if (copyIdx > r) newTime"),
+    # Alg. 5 window not restarted on an insufficient step
+    "alg5_no_restart": ("{ loadTime = 0; sufficient = 0; }", "{ sufficient = 0; }"),
+}
+
+
+@contextlib.contextmanager
+def mutant(oracle, tmp_path, name):
+    src = open(oracle.SRC).read()
+    old, new = MUTANTS[name]
+    assert src.count(old) >= 1, name
+    mut = tmp_path / f"{name}.c"
+    mut.write_text(src.replace(old, new))
+    (tmp_path / "rcpsp_oracle.h").write_text(open(oracle.HDR).read())
+    so = tmp_path / f"lib{name}.so"
+    subprocess.run(["gcc", "-O1", "-std=c11", "-shared", "-fPIC", "-pthread", "-o", str(so), str(mut)],
+                   check=True)
+    saved = oracle._handle
+    oracle._handle = oracle.load(str(so))
+    try:
+        yield
+    finally:
+        oracle._handle = saved
+
+
+def table1_cmax(oracle, mode):
+    text, vals = fixtures.read("table1_instance.txt")
+    inst = Instance.from_text(text)
+    return oracle.decode(inst, np.array(vals["W"], np.int32), mode)[0]
+
+
+def test_mutant_loop_bound_breaks_table1(oracle, tmp_path):
+    with mutant(oracle, tmp_path, "alg5_alg6_k_lt_M_minus_1"):
+        assert table1_cmax(oracle, 1) != 22
+
+
+def test_mutant_eq6_breaks_feasibility_pin(oracle, tmp_path):
+    with mutant(oracle, tmp_path, "eq6_short_range"):
+        with pytest.raises(AssertionError):
+            pins.test_eq5_eq6_equal_list_feasibility(oracle)
+
+
+@pytest.mark.parametrize("name", ["alg4_no_max_with_s", "alg4_copy_offset"])
+def test_mutant_alg4_breaks_envelope_pin(oracle, tmp_path, name):
+    with mutant(oracle, tmp_path, name):
+        with pytest.raises(AssertionError):
+            pins.test_alg4_equals_upper_envelope(oracle)
+        if name == "alg4_copy_offset":
+            with pytest.raises(AssertionError):
+                pins.test_fig4_update(oracle)
+
+
+def test_mutant_alg5_breaks_earliest_fit_pin(oracle, tmp_path):
+    with mutant(oracle, tmp_path, "alg5_no_restart"):
+        with pytest.raises(AssertionError):
+            pins.test_decoders_on_random_lists(oracle)
