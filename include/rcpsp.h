@@ -1,0 +1,184 @@
+/*
+ * rcpsp.h -- C interface of the GB300 tabu-search library for the Resource
+ * Constrained Project Scheduling Problem (makespan), after Bukata, Sucha and
+ * Hanzalek, "Solving the RCPSP using the parallel tabu search designed for the
+ * CUDA platform" (J. Parallel Distrib. Comput. 77, 2015).
+ *
+ * Conventions for every call:
+ *   - all integers are int32 unless stated; arrays are dense and row-major;
+ *   - a pointer argument documented "host" must point to host memory;
+ *   - the library copies every input it is given before the call returns;
+ *     the caller keeps ownership of its buffers;
+ *   - device memory belongs to the context; it is taken from the allocator
+ *     passed to rcpsp_create (for example PyTorch's caching allocator) or,
+ *     without one, from cudaMalloc;
+ *   - calls return RCPSP_OK (0) or a negative RCPSP_E_* code; the text of the
+ *     last failure of a context is given by rcpsp_last_error; no call throws
+ *     across the interface;
+ *   - a context is used by one host thread at a time.
+ */
+#ifndef RCPSP_H
+#define RCPSP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ limits */
+#define RCPSP_MAX_N 1024        /* activities, dummies included            */
+#define RCPSP_MAX_M 8           /* renewable resources                      */
+#define RCPSP_MAX_CAP 32767     /* largest capacity R_k                     */
+#define RCPSP_MAX_HORIZON 32767 /* largest sum of durations (UB of Sec. 5.2) */
+#define RCPSP_MAX_TABU 8192     /* largest |tabuList|                       */
+
+/* ------------------------------------------------------- error codes */
+enum {
+    RCPSP_OK = 0,
+    RCPSP_E_INVALID_ARG = -1,         /* bad pointer, size or parameter           */
+    RCPSP_E_CYCLE = -2,               /* precedence graph has a cycle             */
+    RCPSP_E_DUMMY = -3,               /* 0 / N-1 are not the unique source / sink
+                                         with zero duration and demand            */
+    RCPSP_E_DEMAND_EXCEEDS_CAP = -4,  /* r_{i,k} > R_k                            */
+    RCPSP_E_TOO_LARGE = -5,           /* beyond a RCPSP_MAX_* limit or shared memory */
+    RCPSP_E_CUDA = -6,                /* a CUDA runtime call failed               */
+    RCPSP_E_TIMEOUT = -7,             /* a bounded wait ran out                   */
+    RCPSP_E_NOT_FOUND = -8,           /* unknown instance id                      */
+    RCPSP_E_DEVICE = -9               /* a kernel reported an internal error      */
+};
+
+/* Resource evaluation algorithm (Sec. 5). */
+enum {
+    RCPSP_EVAL_AUTO = 0,      /* per instance, by the selection rule (Sec. 5.4) */
+    RCPSP_EVAL_TIME = 1,      /* time-indexed: Algs. 5-6                         */
+    RCPSP_EVAL_CAPACITY = 2   /* capacity-indexed: Eq. 7 and Alg. 4             */
+};
+
+/* One instance, as in the problem statement (Sec. 2): N activities with
+ * dummies 0 and N-1 (zero duration and demand, 0 the only activity without a
+ * predecessor, N-1 the only one without a successor), durations d_i, M
+ * resources with capacities R_k, demands r_{i,k} <= R_k, and the precedence
+ * arcs E as successor lists.  Activities need not be numbered topologically.
+ * All pointers are host pointers. */
+typedef struct {
+    int32_t n;                  /* N, dummies included, 3 <= N <= RCPSP_MAX_N  */
+    int32_t m;                  /* M, 1 <= M <= RCPSP_MAX_M                     */
+    const int32_t *dur;         /* [N] durations d_i >= 0, d_0 = d_{N-1} = 0    */
+    const int32_t *cap;         /* [M] capacities 1 <= R_k <= RCPSP_MAX_CAP    */
+    const int32_t *req;         /* [N*M] demands, req[i*M+k] = r_{i,k}          */
+    const int32_t *succ_off;    /* [N+1] CSR offsets into succ                   */
+    const int32_t *succ;        /* [succ_off[N]] successor lists (arcs (i,j))   */
+    const int32_t *level_key;   /* [N] or NULL: order inside a level of the
+                                   initial list (Sec. 4.1 "shuffling"); the
+                                   list sorts by (level, key, label)          */
+} rcpsp_instance;
+
+/* Search parameters (Sec. 6, Table 2) and launch shape. */
+typedef struct {
+    int32_t iterations;         /* iteration limit per instance, >= 0            */
+    int32_t max_swap_dist;      /* delta of the reduced neighbourhood (Sec. 4.3) */
+    int32_t tabu_len;           /* |tabuList| of the simple tabu list (Sec. 4.5) */
+    int32_t eval_mode;          /* RCPSP_EVAL_*                                  */
+    int32_t stop_at_cp;         /* 1: stop once C*_max equals the critical path  */
+    int32_t group_size;         /* lanes per neighbour decode: 1,2,4,8,16,32;
+                                   0 = choose automatically                      */
+    int32_t warps_per_cta;      /* 1..32; 0 = choose automatically               */
+    int32_t record_trace;       /* 1: keep (u, v, C) of every iteration          */
+    int32_t use_graph;          /* 1: capture the launch in a CUDA graph and
+                                   replay it on later identical calls            */
+} rcpsp_params;
+
+/* Result statistics of one instance. */
+typedef struct {
+    int64_t evaluated;          /* neighbour schedules decoded (Sched_sec count) */
+    int64_t work;               /* Alg. 5 loop steps (time-indexed) or Alg. 4
+                                   loop steps (capacity-indexed) of those decodes */
+    int32_t iterations;         /* iterations performed                         */
+    int32_t eval_mode;          /* evaluator used (RCPSP_EVAL_TIME / _CAPACITY)  */
+    int32_t critical_path;      /* critical-path length (Sec. 2)                */
+    int32_t status;             /* 0, or a negative RCPSP_E_* code              */
+} rcpsp_stats;
+
+/* Optional device allocator.  alloc returns device memory of `bytes` bytes
+ * usable on `stream` (NULL on failure); release returns it. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *stream, void *user);
+    void (*release)(void *ptr, size_t bytes, void *stream, void *user);
+    void *user;
+} rcpsp_allocator;
+
+typedef struct rcpsp_ctx rcpsp_ctx;
+
+/* Creates a context on CUDA device `device`.  `alloc` may be NULL (then
+ * cudaMalloc / cudaFree are used); the struct is copied.  Errors:
+ * RCPSP_E_INVALID_ARG, RCPSP_E_CUDA. */
+int rcpsp_create(rcpsp_ctx **ctx, int device, const rcpsp_allocator *alloc);
+
+/* Waits for the context's work, frees its device memory and the context. */
+int rcpsp_destroy(rcpsp_ctx *ctx);
+
+/* Validates `count` instances (host memory), computes for each the critical
+ * path (Sec. 2), the level-ordered initial list (Sec. 4.1) and the evaluator
+ * of the selection rule (Sec. 5.4), packs them and copies them to the
+ * device.  Writes one id per instance to out_ids (host).  On any validation
+ * error nothing is loaded and the code of the first bad instance is
+ * returned (RCPSP_E_CYCLE, RCPSP_E_DUMMY, RCPSP_E_DEMAND_EXCEEDS_CAP,
+ * RCPSP_E_TOO_LARGE, RCPSP_E_INVALID_ARG). */
+int rcpsp_load_instances(rcpsp_ctx *ctx, const rcpsp_instance *inst, int32_t count,
+                         int32_t *out_ids);
+
+/* Frees the device memory of loaded instances (their ids become unknown). */
+int rcpsp_free_instances(rcpsp_ctx *ctx, const int32_t *ids, int32_t count);
+
+/* Runs one tabu search per listed instance (Sec. 6: neighbourhood of swap
+ * moves with Eqs. 5-6 filtering, serial-SGS decoding with the chosen
+ * evaluator, best admissible move under the simple tabu list (Algs. 2-3)
+ * and the aspiration rule).  All searches share one persistent launch on
+ * `cuda_stream` (a cudaStream_t; NULL = legacy default stream); the call is
+ * asynchronous.  Results stay on the device until rcpsp_get_schedules. */
+int rcpsp_tabu_search(rcpsp_ctx *ctx, const int32_t *ids, int32_t count,
+                      const rcpsp_params *params, void *cuda_stream);
+
+/* Waits for the last search of the context and copies results to host
+ * buffers: order = best list W* and start = its start times S (both [sum of N
+ * over the ids], concatenated in id order), makespan = C*_max [count].  Any
+ * output pointer may be NULL.  stats (NULL allowed) gets [count] entries.
+ * Returns RCPSP_E_DEVICE if a search reported an internal error. */
+int rcpsp_get_schedules(rcpsp_ctx *ctx, const int32_t *ids, int32_t count,
+                        int32_t *order, int32_t *start, int32_t *makespan,
+                        rcpsp_stats *stats);
+
+/* Copies the iteration trace of the last search of an instance run with
+ * record_trace = 1: [iterations][3] = (u, v, C_max after the move), (0, 0)
+ * for an iteration without an admissible move.  `capacity` is the number of
+ * int32 elements of `trace` (host); *written gets the number of iterations. */
+int rcpsp_get_trace(rcpsp_ctx *ctx, int32_t id, int32_t *trace, int32_t capacity,
+                    int32_t *written);
+
+/* Decodes `count` activity lists of one loaded instance on the device with
+ * the serial SGS of Alg. 7 and the given evaluator (TIME or CAPACITY; AUTO =
+ * the instance's selected one).  lists [count*N] (host) must be
+ * precedence-feasible.  Writes start [count*N], makespan [count] and work
+ * [count] (Alg. 5 or Alg. 4 loop steps; any may be NULL).  Synchronous. */
+int rcpsp_evaluate_lists(rcpsp_ctx *ctx, int32_t id, const int32_t *lists, int32_t count,
+                         int32_t eval_mode, int32_t *start, int32_t *makespan,
+                         int64_t *work, void *cuda_stream);
+
+/* Validates one instance (host memory) and reports what
+ * rcpsp_load_instances would prepare for it, without using a GPU: the
+ * critical-path length (Sec. 2), the horizon UB = sum d_i (Sec. 5.2), the
+ * initial list W (Sec. 4.1, [N]) and the evaluator of the selection rule
+ * (Sec. 5.4).  Any output may be NULL; `msg` (msg_len bytes, may be NULL)
+ * gets the reason of a failure.  Returns the same codes as loading. */
+int rcpsp_prepare_instance(const rcpsp_instance *inst, int32_t *critical_path, int32_t *horizon,
+                           int32_t *initial_order, int32_t *eval_mode, char *msg, int32_t msg_len);
+
+/* Text of the last error of the context (never NULL). */
+const char *rcpsp_last_error(const rcpsp_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RCPSP_H */

@@ -1,0 +1,581 @@
+// C interface of the library (include/rcpsp.h): contexts, device memory,
+// instance loading, launch planning (longest-first work queue, launch shape,
+// CUDA-graph replay) and result retrieval.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "host_prep.h"
+#include "kernels.h"
+#include "rcpsp_internal.h"
+
+using rcpsp::InstHeader;
+using rcpsp::LaunchItem;
+
+namespace {
+
+struct Block {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    size_t out_offset = 0;   // byte offset of the outputs of this block
+    size_t out_bytes = 0;
+    int live = 0;            // instances still loaded from this block
+};
+
+struct Inst {
+    InstHeader h{};
+    int block = -1;
+    int32_t *record = nullptr;
+    int32_t *out = nullptr;
+    size_t out_word = 0;     // word offset of the outputs inside the block's output region
+    int32_t *trace = nullptr;
+    size_t trace_bytes = 0;
+    int trace_iters = -1;    // iterations recorded by the last traced search, -1 = none
+    bool alive = false;
+};
+
+int out_words(int n) { return rcpsp::align4(2 * n + rcpsp::kOutStats); }
+
+}  // namespace
+
+struct rcpsp_ctx {
+    int device = 0;
+    rcpsp_allocator alloc{};
+    bool has_alloc = false;
+    cudaDeviceProp prop{};
+    std::vector<Block> blocks;
+    std::vector<Inst> insts;
+    std::string err;
+    LaunchItem *items_dev = nullptr;
+    size_t items_cap = 0;
+    LaunchItem *items_host = nullptr;   // pinned staging
+    int *queue_dev = nullptr;
+    cudaEvent_t done = nullptr;
+    bool pending = false;
+    // graph replay: the cached graph corresponds to the items now on the device
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<LaunchItem> g_items;
+    int g_shape[5] = {0, 0, 0, 0, 0};
+    cudaStream_t g_stream = nullptr;
+};
+
+namespace {
+
+int set_err(rcpsp_ctx *c, int code, const std::string &msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_err(rcpsp_ctx *c, cudaError_t e, const char *what) {
+    return set_err(c, RCPSP_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void *dev_alloc(rcpsp_ctx *c, size_t bytes, cudaStream_t st) {
+    if (bytes == 0) bytes = 16;
+    if (c->has_alloc) return c->alloc.alloc(bytes, st, c->alloc.user);
+    void *p = nullptr;
+    return cudaMalloc(&p, bytes) == cudaSuccess ? p : nullptr;
+}
+
+void dev_free(rcpsp_ctx *c, void *p, size_t bytes, cudaStream_t st) {
+    if (!p) return;
+    if (c->has_alloc) c->alloc.release(p, bytes, st, c->alloc.user);
+    else cudaFree(p);
+}
+
+// Waits for the context's last search with a deadline (seconds from the
+// environment variable RCPSP_WAIT_SECONDS, default 900).
+int wait_done(rcpsp_ctx *c) {
+    if (!c->pending) return RCPSP_OK;
+    double limit = 900.0;
+    if (const char *s = std::getenv("RCPSP_WAIT_SECONDS")) limit = std::atof(s);
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaEventQuery(c->done);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) return cuda_err(c, e, "search");
+        double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > limit) return set_err(c, RCPSP_E_TIMEOUT, "search did not finish within the wait limit");
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    c->pending = false;
+    return RCPSP_OK;
+}
+
+// Default launch shape: G lanes per neighbour decode and warps per CTA.
+void default_shape(const std::vector<LaunchItem> &items, int *G, int *warps) {
+    double avg_d = 0, feas = 0;
+    for (const LaunchItem &it : items) {
+        avg_d += it.h.n > 2 ? static_cast<double>(it.h.ub) / (it.h.n - 2) : 1.0;
+        feas += it.h.n > 3 ? 0.12 * (it.h.n - 3) * it.delta : 1.0;
+    }
+    avg_d /= std::max<size_t>(1, items.size());
+    feas /= std::max<size_t>(1, items.size());
+    int g = 1;
+    while (g < 32 && g < avg_d) g *= 2;
+    *G = g;
+    const int groups_wanted = static_cast<int>(feas) + 1;
+    int w = (groups_wanted * g + 31) / 32;
+    *warps = std::max(1, std::min(16, w));
+}
+
+size_t smem_bytes(const std::vector<LaunchItem> &items, int ngroups, int move_cap) {
+    int words = 0;
+    for (const LaunchItem &it : items) {
+        const int pw = rcpsp::profile_words(it.mode, it.h.wps, it.h.ub, it.h.sum_cap);
+        const rcpsp::StateLayout S =
+            rcpsp::state_layout(it.h.inst_words, it.h.n, it.tabu_len, it.delta, move_cap, pw, ngroups);
+        words = std::max(words, S.total);
+    }
+    return static_cast<size_t>(words) * 4;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rcpsp_create(rcpsp_ctx **ctx, int device, const rcpsp_allocator *alloc) {
+    if (!ctx) return RCPSP_E_INVALID_ARG;
+    *ctx = nullptr;
+    if (alloc && (!alloc->alloc || !alloc->release)) return RCPSP_E_INVALID_ARG;
+    rcpsp_ctx *c = new (std::nothrow) rcpsp_ctx();
+    if (!c) return RCPSP_E_INVALID_ARG;
+    c->device = device;
+    if (alloc) {
+        c->alloc = *alloc;
+        c->has_alloc = true;
+    }
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaGetDeviceProperties(&c->prop, device);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        delete c;
+        return RCPSP_E_CUDA;
+    }
+    c->queue_dev = static_cast<int *>(dev_alloc(c, 16, nullptr));
+    if (!c->queue_dev) {
+        cudaEventDestroy(c->done);
+        delete c;
+        return RCPSP_E_CUDA;
+    }
+    *ctx = c;
+    return RCPSP_OK;
+}
+
+int rcpsp_destroy(rcpsp_ctx *c) {
+    if (!c) return RCPSP_E_INVALID_ARG;
+    cudaSetDevice(c->device);
+    wait_done(c);
+    cudaDeviceSynchronize();
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    for (Inst &in : c->insts) dev_free(c, in.trace, in.trace_bytes, nullptr);
+    for (Block &b : c->blocks) dev_free(c, b.ptr, b.bytes, nullptr);
+    dev_free(c, c->items_dev, c->items_cap, nullptr);
+    dev_free(c, c->queue_dev, 16, nullptr);
+    if (c->items_host) cudaFreeHost(c->items_host);
+    cudaEventDestroy(c->done);
+    delete c;
+    return RCPSP_OK;
+}
+
+const char *rcpsp_last_error(const rcpsp_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+int rcpsp_prepare_instance(const rcpsp_instance *inst, int32_t *critical_path, int32_t *horizon,
+                           int32_t *initial_order, int32_t *eval_mode, char *msg, int32_t msg_len) {
+    if (!inst) return RCPSP_E_INVALID_ARG;
+    rcpsp::PackedInstance pk;
+    std::string err;
+    const int rc = rcpsp::prepare_instance(*inst, pk, err);
+    if (msg && msg_len > 0) {
+        std::strncpy(msg, err.c_str(), static_cast<size_t>(msg_len) - 1);
+        msg[msg_len - 1] = 0;
+    }
+    if (rc != RCPSP_OK) return rc;
+    if (critical_path) *critical_path = pk.h.cp;
+    if (horizon) *horizon = pk.h.ub;
+    if (eval_mode) *eval_mode = pk.h.sel_mode;
+    if (initial_order) std::memcpy(initial_order, pk.initial.data(), pk.initial.size() * 4);
+    return RCPSP_OK;
+}
+
+int rcpsp_load_instances(rcpsp_ctx *c, const rcpsp_instance *inst, int32_t count, int32_t *out_ids) {
+    if (!c) return RCPSP_E_INVALID_ARG;
+    if (count < 0 || (count > 0 && (!inst || !out_ids))) return set_err(c, RCPSP_E_INVALID_ARG, "bad arguments");
+    if (count == 0) return RCPSP_OK;
+    cudaSetDevice(c->device);
+    std::vector<rcpsp::PackedInstance> packed(count);
+    size_t rec_words = 0, o_words = 0;
+    for (int k = 0; k < count; ++k) {
+        std::string msg;
+        int rc = rcpsp::prepare_instance(inst[k], packed[k], msg);
+        if (rc != RCPSP_OK) return set_err(c, rc, "instance " + std::to_string(k) + ": " + msg);
+        rec_words += packed[k].h.record_words;
+        o_words += out_words(packed[k].h.n);
+    }
+    Block b;
+    b.out_offset = rec_words * 4;
+    b.out_bytes = o_words * 4;
+    b.bytes = b.out_offset + b.out_bytes;
+    b.ptr = dev_alloc(c, b.bytes, nullptr);
+    if (!b.ptr) return set_err(c, RCPSP_E_CUDA, "device allocation failed");
+    std::vector<int32_t> host(rec_words);
+    size_t ro = 0;
+    for (int k = 0; k < count; ++k) {
+        std::memcpy(host.data() + ro, packed[k].record.data(), packed[k].record.size() * 4);
+        ro += packed[k].record.size();
+    }
+    cudaError_t e = cudaMemcpy(b.ptr, host.data(), rec_words * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(static_cast<char *>(b.ptr) + b.out_offset, 0, b.out_bytes);
+    if (e != cudaSuccess) {
+        dev_free(c, b.ptr, b.bytes, nullptr);
+        return cuda_err(c, e, "instance upload");
+    }
+    b.live = count;
+    const int bid = static_cast<int>(c->blocks.size());
+    c->blocks.push_back(b);
+    ro = 0;
+    size_t oo = 0;
+    int32_t *base = static_cast<int32_t *>(b.ptr);
+    for (int k = 0; k < count; ++k) {
+        Inst in;
+        in.h = packed[k].h;
+        in.block = bid;
+        in.record = base + ro;
+        in.out_word = oo;
+        in.out = base + rec_words + oo;
+        in.alive = true;
+        ro += packed[k].record.size();
+        oo += out_words(in.h.n);
+        out_ids[k] = static_cast<int32_t>(c->insts.size());
+        c->insts.push_back(in);
+    }
+    return RCPSP_OK;
+}
+
+int rcpsp_free_instances(rcpsp_ctx *c, const int32_t *ids, int32_t count) {
+    if (!c) return RCPSP_E_INVALID_ARG;
+    if (count < 0 || (count > 0 && !ids)) return set_err(c, RCPSP_E_INVALID_ARG, "bad arguments");
+    int rc = wait_done(c);
+    if (rc != RCPSP_OK) return rc;
+    for (int k = 0; k < count; ++k) {
+        const int id = ids[k];
+        if (id < 0 || id >= static_cast<int>(c->insts.size()) || !c->insts[id].alive)
+            return set_err(c, RCPSP_E_NOT_FOUND, "unknown instance id");
+        Inst &in = c->insts[id];
+        in.alive = false;
+        dev_free(c, in.trace, in.trace_bytes, nullptr);
+        in.trace = nullptr;
+        in.trace_bytes = 0;
+        Block &b = c->blocks[in.block];
+        if (--b.live == 0) {
+            dev_free(c, b.ptr, b.bytes, nullptr);
+            b.ptr = nullptr;
+        }
+    }
+    return RCPSP_OK;
+}
+
+int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcpsp_params *p, void *stream) {
+    if (!c) return RCPSP_E_INVALID_ARG;
+    if (!p || count < 0 || (count > 0 && !ids)) return set_err(c, RCPSP_E_INVALID_ARG, "bad arguments");
+    if (p->iterations < 0 || p->max_swap_dist < 0 || p->tabu_len < 0 || p->tabu_len > RCPSP_MAX_TABU ||
+        p->eval_mode < 0 || p->eval_mode > 2 || p->warps_per_cta < 0 || p->warps_per_cta > 32)
+        return set_err(c, RCPSP_E_INVALID_ARG, "bad search parameters");
+    const int gs = p->group_size;
+    if (gs != 0 && gs != 1 && gs != 2 && gs != 4 && gs != 8 && gs != 16 && gs != 32)
+        return set_err(c, RCPSP_E_INVALID_ARG, "group_size must be 0, 1, 2, 4, 8, 16 or 32");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (p->use_graph && st == nullptr)
+        return set_err(c, RCPSP_E_INVALID_ARG, "graph capture needs a non-default stream");
+    cudaSetDevice(c->device);
+    int rc = wait_done(c);
+    if (rc != RCPSP_OK) return rc;
+    if (count == 0) return RCPSP_OK;
+    std::vector<LaunchItem> items(count);
+    std::vector<double> cost(count);
+    for (int k = 0; k < count; ++k) {
+        const int id = ids[k];
+        if (id < 0 || id >= static_cast<int>(c->insts.size()) || !c->insts[id].alive)
+            return set_err(c, RCPSP_E_NOT_FOUND, "unknown instance id");
+        Inst &in = c->insts[id];
+        LaunchItem &it = items[k];
+        std::memset(&it, 0, sizeof(it));
+        it.h = in.h;
+        it.record = in.record;
+        it.out = in.out;
+        it.mode = p->eval_mode == RCPSP_EVAL_AUTO ? in.h.sel_mode : p->eval_mode;
+        int dd, tl;
+        rcpsp::default_search_params(in.h.n, &dd, &tl);
+        it.delta = p->max_swap_dist ? p->max_swap_dist : dd;
+        it.tabu_len = p->tabu_len ? p->tabu_len : tl;
+        it.iterations = p->iterations;
+        it.stop_at_cp = p->stop_at_cp ? 1 : 0;
+        if (p->record_trace) {
+            const size_t need = static_cast<size_t>(std::max(1, p->iterations)) * 3 * 4;
+            if (in.trace_bytes < need) {
+                dev_free(c, in.trace, in.trace_bytes, nullptr);
+                in.trace = static_cast<int32_t *>(dev_alloc(c, need, nullptr));
+                in.trace_bytes = in.trace ? need : 0;
+                if (!in.trace) return set_err(c, RCPSP_E_CUDA, "trace allocation failed");
+            }
+            it.trace = in.trace;
+            in.trace_iters = p->iterations;
+        } else {
+            in.trace_iters = -1;
+        }
+        cost[k] = rcpsp::estimate_cost(in.h, it.mode, it.iterations, it.delta);
+    }
+    // longest first (LPT) on the work queue
+    std::vector<int> order(count);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<LaunchItem> sorted(count);
+    for (int k = 0; k < count; ++k) sorted[k] = items[order[k]];
+    // launch shape
+    int G = gs, warps = p->warps_per_cta;
+    int dG, dW;
+    default_shape(sorted, &dG, &dW);
+    if (!G) G = dG;
+    if (!warps) warps = std::max(dW, (G + 31) / 32);
+    const int move_cap = rcpsp::kDefaultMoveCap;
+    const size_t smem_limit = c->prop.sharedMemPerBlockOptin > 1024 ? c->prop.sharedMemPerBlockOptin - 1024 : 0;
+    size_t smem = smem_bytes(sorted, warps * (32 / G), move_cap);
+    while (smem > smem_limit && p->warps_per_cta == 0 && warps > 1) {
+        --warps;
+        smem = smem_bytes(sorted, warps * (32 / G), move_cap);
+    }
+    if (smem > smem_limit)
+        return set_err(c, RCPSP_E_TOO_LARGE, "instance state does not fit in shared memory at this launch shape");
+    const int threads = warps * 32;
+    cudaError_t e = rcpsp::prepare_search(G, smem);
+    if (e != cudaSuccess) return cuda_err(c, e, "kernel attributes");
+    int per_sm = 0;
+    e = rcpsp::search_occupancy(G, threads, smem, &per_sm);
+    if (e != cudaSuccess) return cuda_err(c, e, "occupancy");
+    if (per_sm < 1) return set_err(c, RCPSP_E_TOO_LARGE, "launch shape does not fit on an SM");
+    const int blocks = std::max(1, std::min(count, per_sm * c->prop.multiProcessorCount));
+    // device copy of the plan
+    const size_t ibytes = sizeof(LaunchItem) * count;
+    const int shape[5] = {G, threads, static_cast<int>(smem), blocks, move_cap};
+    const bool same_plan = c->gexec && c->g_stream == st && c->g_items.size() == sorted.size() &&
+                           std::memcmp(c->g_items.data(), sorted.data(), ibytes) == 0 &&
+                           std::memcmp(c->g_shape, shape, sizeof(shape)) == 0;
+    if (!(p->use_graph && same_plan)) {
+        if (c->items_cap < ibytes) {
+            cudaStreamSynchronize(st);
+            dev_free(c, c->items_dev, c->items_cap, nullptr);
+            if (c->items_host) cudaFreeHost(c->items_host);
+            c->items_host = nullptr;
+            c->items_dev = static_cast<LaunchItem *>(dev_alloc(c, ibytes, nullptr));
+            c->items_cap = c->items_dev ? ibytes : 0;
+            if (!c->items_dev) return set_err(c, RCPSP_E_CUDA, "plan allocation failed");
+            e = cudaMallocHost(reinterpret_cast<void **>(&c->items_host), ibytes);
+            if (e != cudaSuccess) return cuda_err(c, e, "pinned staging");
+        } else {
+            cudaStreamSynchronize(st);   // the staging buffer may still feed a copy
+        }
+        std::memcpy(c->items_host, sorted.data(), ibytes);
+        e = cudaMemcpyAsync(c->items_dev, c->items_host, ibytes, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_err(c, e, "plan upload");
+        if (c->gexec) {
+            cudaGraphExecDestroy(c->gexec);
+            c->gexec = nullptr;
+            c->g_items.clear();
+        }
+    }
+    if (p->use_graph) {
+        if (!c->gexec) {
+            cudaGraph_t graph = nullptr;
+            e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return cuda_err(c, e, "begin capture");
+            cudaMemsetAsync(c->queue_dev, 0, sizeof(int), st);
+            rcpsp::launch_search(G, c->items_dev, count, c->queue_dev, move_cap, blocks, threads, smem, st);
+            e = cudaStreamEndCapture(st, &graph);
+            if (e != cudaSuccess) return cuda_err(c, e, "end capture");
+            e = cudaGraphInstantiate(&c->gexec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                c->gexec = nullptr;
+                return cuda_err(c, e, "graph instantiate");
+            }
+            c->g_items = sorted;
+            std::memcpy(c->g_shape, shape, sizeof(shape));
+            c->g_stream = st;
+        }
+        e = cudaGraphLaunch(c->gexec, st);
+        if (e != cudaSuccess) return cuda_err(c, e, "graph launch");
+    } else {
+        e = cudaMemsetAsync(c->queue_dev, 0, sizeof(int), st);
+        if (e == cudaSuccess)
+            e = rcpsp::launch_search(G, c->items_dev, count, c->queue_dev, move_cap, blocks, threads, smem, st);
+        if (e != cudaSuccess) return cuda_err(c, e, "search launch");
+    }
+    e = cudaEventRecord(c->done, st);
+    if (e != cudaSuccess) return cuda_err(c, e, "event record");
+    c->pending = true;
+    return RCPSP_OK;
+}
+
+int rcpsp_get_schedules(rcpsp_ctx *c, const int32_t *ids, int32_t count, int32_t *order, int32_t *start,
+                        int32_t *makespan, rcpsp_stats *stats) {
+    if (!c) return RCPSP_E_INVALID_ARG;
+    if (count < 0 || (count > 0 && !ids)) return set_err(c, RCPSP_E_INVALID_ARG, "bad arguments");
+    cudaSetDevice(c->device);
+    int rc = wait_done(c);
+    if (rc != RCPSP_OK) return rc;
+    // one copy per block touched
+    std::vector<int> touched;
+    for (int k = 0; k < count; ++k) {
+        const int id = ids[k];
+        if (id < 0 || id >= static_cast<int>(c->insts.size()) || !c->insts[id].alive)
+            return set_err(c, RCPSP_E_NOT_FOUND, "unknown instance id");
+        touched.push_back(c->insts[id].block);
+    }
+    std::sort(touched.begin(), touched.end());
+    touched.erase(std::unique(touched.begin(), touched.end()), touched.end());
+    std::vector<std::vector<int32_t>> host(c->blocks.size());
+    for (int b : touched) {
+        Block &bl = c->blocks[b];
+        host[b].resize(bl.out_bytes / 4);
+        cudaError_t e = cudaMemcpy(host[b].data(), static_cast<char *>(bl.ptr) + bl.out_offset, bl.out_bytes,
+                                   cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_err(c, e, "result copy");
+    }
+    size_t at = 0;
+    int status = RCPSP_OK;
+    for (int k = 0; k < count; ++k) {
+        const Inst &in = c->insts[ids[k]];
+        const int n = in.h.n;
+        const int32_t *o = host[in.block].data() + in.out_word;
+        const int32_t *s = o + 2 * n;
+        if (order) std::memcpy(order + at, o, n * 4);
+        if (start) std::memcpy(start + at, o + n, n * 4);
+        at += n;
+        if (makespan) makespan[k] = s[rcpsp::kOutCmax];
+        if (stats) {
+            rcpsp_stats &x = stats[k];
+            x.evaluated = (static_cast<int64_t>(s[rcpsp::kOutEvalHi]) << 32) | static_cast<uint32_t>(s[rcpsp::kOutEvalLo]);
+            x.work = (static_cast<int64_t>(s[rcpsp::kOutWorkHi]) << 32) | static_cast<uint32_t>(s[rcpsp::kOutWorkLo]);
+            x.iterations = s[rcpsp::kOutIters];
+            x.eval_mode = s[rcpsp::kOutMode];
+            x.critical_path = in.h.cp;
+            x.status = s[rcpsp::kOutStatus];
+        }
+        if (s[rcpsp::kOutStatus] != 0) status = RCPSP_E_DEVICE;
+    }
+    if (status != RCPSP_OK) return set_err(c, status, "a search reported an internal error");
+    return RCPSP_OK;
+}
+
+int rcpsp_get_trace(rcpsp_ctx *c, int32_t id, int32_t *trace, int32_t capacity, int32_t *written) {
+    if (!c) return RCPSP_E_INVALID_ARG;
+    if (!trace || capacity < 0 || !written) return set_err(c, RCPSP_E_INVALID_ARG, "bad arguments");
+    cudaSetDevice(c->device);
+    int rc = wait_done(c);
+    if (rc != RCPSP_OK) return rc;
+    if (id < 0 || id >= static_cast<int>(c->insts.size()) || !c->insts[id].alive)
+        return set_err(c, RCPSP_E_NOT_FOUND, "unknown instance id");
+    const Inst &in = c->insts[id];
+    if (in.trace_iters < 0 || !in.trace) return set_err(c, RCPSP_E_INVALID_ARG, "no trace recorded");
+    int32_t iters = 0;
+    cudaError_t e = cudaMemcpy(&iters, in.out + 2 * in.h.n + rcpsp::kOutIters, 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_err(c, e, "trace copy");
+    if (static_cast<long long>(iters) * 3 > capacity) return set_err(c, RCPSP_E_INVALID_ARG, "trace buffer too small");
+    if (iters > 0) {
+        e = cudaMemcpy(trace, in.trace, static_cast<size_t>(iters) * 3 * 4, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_err(c, e, "trace copy");
+    }
+    *written = iters;
+    return RCPSP_OK;
+}
+
+int rcpsp_evaluate_lists(rcpsp_ctx *c, int32_t id, const int32_t *lists, int32_t count, int32_t eval_mode,
+                         int32_t *start, int32_t *makespan, int64_t *work, void *stream) {
+    if (!c) return RCPSP_E_INVALID_ARG;
+    if (count < 0 || (count > 0 && !lists) || eval_mode < 0 || eval_mode > 2)
+        return set_err(c, RCPSP_E_INVALID_ARG, "bad arguments");
+    cudaSetDevice(c->device);
+    if (id < 0 || id >= static_cast<int>(c->insts.size()) || !c->insts[id].alive)
+        return set_err(c, RCPSP_E_NOT_FOUND, "unknown instance id");
+    if (count == 0) return RCPSP_OK;
+    const Inst &in = c->insts[id];
+    const int n = in.h.n;
+    for (long long x = 0; x < static_cast<long long>(count) * n; ++x)
+        if (lists[x] < 0 || lists[x] >= n) return set_err(c, RCPSP_E_INVALID_ARG, "list entry out of range");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    LaunchItem it;
+    std::memset(&it, 0, sizeof(it));
+    it.h = in.h;
+    it.record = in.record;
+    it.mode = eval_mode == RCPSP_EVAL_AUTO ? in.h.sel_mode : eval_mode;
+    // largest of a few shapes whose profiles fit in shared memory
+    const int pw = rcpsp::profile_words(it.mode, in.h.wps, in.h.ub, in.h.sum_cap);
+    const int shapes[][2] = {{8, 4}, {8, 2}, {8, 1}, {16, 1}, {32, 1}};
+    int G = 0, warps = 0, ngroups = 0;
+    size_t smem = 0;
+    for (const auto &sh : shapes) {
+        const int ng = sh[1] * (32 / sh[0]);
+        const rcpsp::StateLayout S =
+            rcpsp::state_layout(in.h.inst_words, n, 0, 0, ng * rcpsp::align4(n), pw, ng);
+        smem = static_cast<size_t>(S.total) * 4;
+        if (smem + 1024 <= c->prop.sharedMemPerBlockOptin) {
+            G = sh[0];
+            warps = sh[1];
+            ngroups = ng;
+            break;
+        }
+    }
+    if (!G) return set_err(c, RCPSP_E_TOO_LARGE, "profile too large for shared memory");
+    // output block: work [count] int64 first (8-byte aligned), then start
+    // [count*N], makespan [count] and the error word, each 16-byte aligned
+    auto up16 = [](size_t x) { return (x + 15) & ~static_cast<size_t>(15); };
+    const size_t lbytes = static_cast<size_t>(count) * n * 4;
+    const size_t o_work = 0;
+    const size_t o_start = up16(static_cast<size_t>(count) * 8);
+    const size_t o_cmax = o_start + up16(lbytes);
+    const size_t o_err = o_cmax + up16(static_cast<size_t>(count) * 4);
+    const size_t obytes = o_err + 16;
+    char *dl = static_cast<char *>(dev_alloc(c, lbytes, st));
+    char *dout = static_cast<char *>(dev_alloc(c, obytes, st));
+    if (!dl || !dout) {
+        dev_free(c, dl, lbytes, st);
+        dev_free(c, dout, obytes, st);
+        return set_err(c, RCPSP_E_CUDA, "device allocation failed");
+    }
+    long long *d_work = reinterpret_cast<long long *>(dout + o_work);
+    int32_t *d_start = reinterpret_cast<int32_t *>(dout + o_start);
+    int32_t *d_cmax = reinterpret_cast<int32_t *>(dout + o_cmax);
+    int *d_err = reinterpret_cast<int *>(dout + o_err);
+    std::vector<char> host(obytes);
+    int rc = RCPSP_OK;
+    cudaError_t e = cudaMemcpyAsync(dl, lists, lbytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, 4, st);
+    if (e == cudaSuccess) {
+        const int blocks = std::max(1, std::min((count + ngroups - 1) / ngroups, 4 * c->prop.multiProcessorCount));
+        e = rcpsp::launch_evaluate(G, it, reinterpret_cast<int32_t *>(dl), count, d_start, d_cmax, d_work, d_err,
+                                   blocks, warps * 32, smem, st);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host.data(), dout, obytes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = cuda_err(c, e, "evaluate");
+    dev_free(c, dl, lbytes, st);
+    dev_free(c, dout, obytes, st);
+    if (rc != RCPSP_OK) return rc;
+    if (start) std::memcpy(start, host.data() + o_start, lbytes);
+    if (work) std::memcpy(work, host.data() + o_work, static_cast<size_t>(count) * 8);
+    if (makespan) std::memcpy(makespan, host.data() + o_cmax, static_cast<size_t>(count) * 4);
+    int derr = 0;
+    std::memcpy(&derr, host.data() + o_err, 4);
+    if (derr) return set_err(c, RCPSP_E_DEVICE, "decode reported an internal error");
+    return RCPSP_OK;
+}
+
+}  // extern "C"

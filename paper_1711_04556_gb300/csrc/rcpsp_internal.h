@@ -1,0 +1,116 @@
+// Internal layout shared by the host runtime and the sm_103a kernels.
+//
+// One instance is packed once, at load time, into an int32 record in device
+// memory whose first section has exactly the layout the search kernel uses
+// in shared memory, so that staging an instance into a CTA is one contiguous
+// copy.  The record is followed by the initial activity list W (Sec. 4.1).
+#pragma once
+
+#include <stdint.h>
+
+#include "../../include/rcpsp.h"
+
+#if defined(__CUDACC__)
+#define RC_HD __host__ __device__ __forceinline__
+#else
+#define RC_HD inline
+#endif
+
+namespace rcpsp {
+
+constexpr int kMaxGroupsPerCta = 1024;
+constexpr int kDefaultMoveCap = 2048;   // potential moves examined per stripe
+
+// Per-instance header (64 bytes).
+struct InstHeader {
+    int32_t n, m, ub, cp;       // N, M, UB = sum d_i (Sec. 5.2), critical path
+    int32_t sel_mode;           // evaluator of the selection rule (Sec. 5.4)
+    int32_t wps;                // 32-bit words per time step of the packed profile
+    int32_t lane_bits;          // 8 or 16 bits per resource inside a word
+    int32_t sum_cap;            // sum R_k: length of the capacity-indexed state
+    int32_t n_arcs;             // |E|
+    int32_t inst_words;         // words of the shared-memory section
+    int32_t record_words;       // inst_words + initial list, multiple of 4
+    int32_t pad[5];
+};
+static_assert(sizeof(InstHeader) == 64, "InstHeader is 64 bytes");
+
+// One entry of a launch (96 bytes), ordered by estimated cost on the host.
+struct LaunchItem {
+    InstHeader h;
+    const int32_t *record;      // packed record in device memory
+    int32_t *out;               // outputs: W*[N], S*[N], then kOutStats words
+    int32_t *trace;             // [iterations*3] or nullptr
+    int32_t mode;               // evaluator for this search
+    int32_t iterations;         // iteration limit
+    int32_t delta;              // max swap distance
+    int32_t tabu_len;           // tabu list length
+    int32_t stop_at_cp;
+    int32_t pad;
+};
+static_assert(sizeof(LaunchItem) == 112, "LaunchItem is 112 bytes");
+
+// Statistics words after W* and S* in the output block of an instance.
+enum : int {
+    kOutEvalLo = 0, kOutEvalHi, kOutWorkLo, kOutWorkHi,
+    kOutIters, kOutCmax, kOutMode, kOutStatus, kOutStats
+};
+
+RC_HD int align4(int x) { return (x + 3) & ~3; }
+
+// Offsets (in 32-bit words) of the shared-memory image of an instance.
+struct InstLayout {
+    int dur, reqw, capw, cap, cbase, reqk, poff, plist, soff, slist, words;
+};
+
+RC_HD InstLayout inst_layout(int n, int m, int wps, int n_arcs) {
+    InstLayout L;
+    int o = 0;
+    L.dur = o;   o += align4(n);          // d_i
+    L.reqw = o;  o += align4(n * wps);    // packed r_{i,k}: word w of activity i at i*wps+w
+    L.capw = o;  o += 4;                  // packed R_k per word (initial profile value)
+    L.cap = o;   o += 8;                  // R_k
+    L.cbase = o; o += 8;                  // start of c_k in the capacity-indexed state
+    L.reqk = o;  o += align4(n * m);      // r_{i,k}
+    L.poff = o;  o += align4(n + 1);      // predecessor CSR
+    L.plist = o; o += align4(n_arcs);
+    L.soff = o;  o += align4(n + 1);      // successor CSR
+    L.slist = o; o += align4(n_arcs);
+    L.words = o;
+    return L;
+}
+
+// Search state and per-group scratch that follow the instance image.
+struct StateLayout {
+    int W, pos, Wbest, fsp, lpp, stl, tc, moves;
+    int groups;          // first word of the per-warp group areas
+    int prof_words;      // profile words of one group (time- or capacity-indexed)
+    int group_words;     // profile + finish times of one group
+    int total;           // words of dynamic shared memory
+};
+
+RC_HD int profile_words(int mode, int wps, int ub, int sum_cap) {
+    return mode == RCPSP_EVAL_CAPACITY ? sum_cap : wps * (ub > 0 ? ub : 1);
+}
+
+RC_HD StateLayout state_layout(int inst_words, int n, int tabu_len, int delta, int move_cap,
+                               int prof_words, int ngroups) {
+    StateLayout S;
+    int o = inst_words;
+    S.W = o;     o += align4(n);
+    S.pos = o;   o += align4(n);
+    S.Wbest = o; o += align4(n);
+    S.fsp = o;   o += align4(n);
+    S.lpp = o;   o += align4(n);
+    S.stl = o;   o += align4(tabu_len);
+    S.tc = o;    o += align4((n * delta + 31) / 32);
+    S.moves = o; o += align4(move_cap);
+    S.groups = o;
+    S.prof_words = prof_words;
+    S.group_words = prof_words + n;
+    o += ngroups * S.group_words;
+    S.total = o;
+    return S;
+}
+
+}  // namespace rcpsp

@@ -1,0 +1,606 @@
+// sm_103a kernels of the tabu search for the RCPSP (Bukata, Sucha, Hanzalek).
+//
+// One persistent CTA runs one search at a time and pops the next instance
+// from a device work queue when it is done (Sec. 6: one block = one tabu
+// search; the homogeneous model: instance and state stay on the device for
+// the whole run).  Inside a CTA the neighbourhood is split over "groups" of
+// G lanes (G = 1, 2, ..., 32, chosen at launch); a group decodes one
+// neighbour at a time with the serial SGS of Alg. 7, its lanes cooperating
+// on the resource scan and update.  Each group owns a private resource
+// profile in shared memory, interleaved with the other groups of its warp so
+// that the G lanes of every group always hit G distinct banks and the groups
+// of a warp hit disjoint bank sets.
+//
+// Per iteration (Sec. 6):
+//   1. first-successor / last-predecessor positions of the current list;
+//      swap(u,v) satisfies Eqs. 5-6 iff v < firstSucc(u) and
+//      u > lastPred(v) -- the same predicate, evaluated in O(1);
+//   2. feasible moves of the reduced neighbourhood (v - u <= delta) are
+//      ballot-compacted into shared memory (Alg. 1's filter, one pass);
+//   3. the groups decode the neighbours (time-indexed: Algs. 5-6 on a
+//      SWAR-packed profile; capacity-indexed: Eq. 7 and Alg. 4 in a
+//      per-index closed form) and form the key (C_max, u, v) of every
+//      admissible move (not tabu, or strictly better than C*_max);
+//   4. warp-shuffle min, then a shared-memory atomicMin, give the move;
+//   5. one thread applies it and updates the simple tabu list (Alg. 3).
+//
+// The kernel never spins: the work queue is a single atomicAdd.  Internal
+// inconsistencies set an error word that the host reads as a status.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kernels.h"
+#include "rcpsp_internal.h"
+
+namespace rcpsp {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kErrHorizon = 1;     // a profile window ran past UB
+
+template <int G>
+struct Group {
+    int lane;        // lane inside the group
+    int gbase;       // first warp lane of the group
+    unsigned mask;   // warp lanes of the group
+    __device__ Group() {
+        int wl = threadIdx.x & 31;
+        lane = wl & (G - 1);
+        gbase = wl & ~(G - 1);
+        mask = G == 32 ? kFull : (((1u << G) - 1u) << gbase);
+    }
+    __device__ unsigned ballot(bool p) const {
+        unsigned b = __ballot_sync(mask, p);
+        return G == 32 ? b : (b >> gbase) & ((1u << G) - 1u);
+    }
+    __device__ int max(int x) const {
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) x = ::max(x, __shfl_xor_sync(mask, x, o, G));
+        return x;
+    }
+    __device__ void sync() const { __syncwarp(mask); }
+};
+
+// Shared-memory view of one instance.
+struct SInst {
+    const int *dur;
+    const uint32_t *reqw;
+    const uint32_t *capw;
+    const int *cap;
+    const int *cbase;
+    const int *reqk;
+    const int *poff;
+    const int *plist;
+    const int *soff;
+    const int *slist;
+    int n, m, ub, wps, sum_cap;
+    uint32_t hi;     // high bit of every packed field
+};
+
+__device__ SInst bind_instance(const int *sm, const InstHeader &h) {
+    InstLayout L = inst_layout(h.n, h.m, h.wps, h.n_arcs);
+    SInst I;
+    I.dur = sm + L.dur;
+    I.reqw = reinterpret_cast<const uint32_t *>(sm + L.reqw);
+    I.capw = reinterpret_cast<const uint32_t *>(sm + L.capw);
+    I.cap = sm + L.cap;
+    I.cbase = sm + L.cbase;
+    I.reqk = sm + L.reqk;
+    I.poff = sm + L.poff;
+    I.plist = sm + L.plist;
+    I.soff = sm + L.soff;
+    I.slist = sm + L.slist;
+    I.n = h.n;
+    I.m = h.m;
+    I.ub = h.ub;
+    I.wps = h.wps;
+    I.sum_cap = h.sum_cap;
+    I.hi = h.lane_bits == 8 ? 0x80808080u : 0x80008000u;
+    return I;
+}
+
+// Copies the instance image (a multiple of 16 bytes) into shared memory.
+__device__ void stage_instance(int *sm, const int32_t *record, int words) {
+    const int4 *src = reinterpret_cast<const int4 *>(record);
+    int4 *dst = reinterpret_cast<int4 *>(sm);
+    for (int x = threadIdx.x; x < words / 4; x += blockDim.x) dst[x] = __ldg(src + x);
+}
+
+// ---------------------------------------------------------------------------
+// Serial SGS (Alg. 7) of the list W with positions u and v swapped
+// (u == v leaves W unchanged), decoded by one group.  `area` is the group's
+// interleaved scratch: profile element e at area[e*NG], finish time of
+// activity i at area[(prof_words + i)*NG].  Returns C_max; `work` gets the
+// Alg. 5 (time-indexed) or Alg. 4 (capacity-indexed) loop steps.
+// ---------------------------------------------------------------------------
+template <int G>
+__device__ int decode_time(const SInst &I, const int *W, int u, int v, int *area, int NG,
+                           const Group<G> &g, long long &work, int &err) {
+    const int n = I.n, ub = I.ub, wps = I.wps;
+    uint32_t *prof = reinterpret_cast<uint32_t *>(area);
+    int *fin = area + wps * (ub > 0 ? ub : 1) * NG;
+    // every time step starts with R_k free units of every resource (Sec. 5.2.1)
+    for (int w = 0; w < wps; ++w) {
+        const uint32_t cw = I.capw[w];
+        for (int t = g.lane; t < ub; t += G) prof[(w * ub + t) * NG] = cw;
+    }
+    g.sync();
+    int cmax = 0;
+    for (int p = 0; p < n; ++p) {
+        int i = W[p];
+        if (p == u) i = W[v];
+        else if (p == v) i = W[u];
+        // precedence earliest start (Alg. 7): max over predecessors of s_j + d_j
+        int es = 0;
+        for (int e = I.poff[i] + g.lane; e < I.poff[i + 1]; e += G) es = ::max(es, fin[I.plist[e] * NG]);
+        es = g.max(es);
+        const int d = I.dur[i];
+        int s = es;
+        if (d > 0) {
+            uint32_t rq[4];
+#pragma unroll
+            for (int w = 0; w < 4; ++w) rq[w] = w < wps ? I.reqw[i * wps + w] : 0u;
+            // Alg. 5: first window of d consecutive steps that fit, from es on.
+            // The G lanes test G steps at once; a step that does not fit
+            // moves the window start past it.
+            for (;;) {
+                bool found = true;
+                for (int off = 0; off < d; off += G) {
+                    const int t = s + off + g.lane;
+                    bool fit = true;
+                    if (off + g.lane < d) {
+                        if (t < ub) {
+#pragma unroll
+                            for (int w = 0; w < 4; ++w)
+                                if (w < wps) {
+                                    const uint32_t x = prof[(w * ub + t) * NG];
+                                    fit = fit && (((x | I.hi) - rq[w]) & I.hi) == I.hi;
+                                }
+                        } else {
+                            err |= kErrHorizon;
+                        }
+                    }
+                    const unsigned bad = g.ballot(!fit);
+                    if (bad) {
+                        s += off + (31 - __clz(bad)) + 1;
+                        found = false;
+                        break;
+                    }
+                }
+                if (found) break;
+            }
+            // Alg. 6: take r_{i,k} units over [s, s+d); fields never borrow
+            for (int t = s + g.lane; t < s + d; t += G) {
+                if (t < ub) {
+#pragma unroll
+                    for (int w = 0; w < 4; ++w)
+                        if (w < wps) prof[(w * ub + t) * NG] -= rq[w];
+                }
+            }
+        }
+        if (g.lane == 0) fin[i * NG] = s + d;
+        work += s + d - es;
+        cmax = ::max(cmax, s + d);
+        g.sync();
+    }
+    return cmax;
+}
+
+template <int G>
+__device__ int decode_capacity(const SInst &I, const int *W, int u, int v, int *area, int NG,
+                               const Group<G> &g, long long &work, int &err) {
+    const int n = I.n, m = I.m;
+    int *cst = area;                                   // c_k, concatenated
+    int *fin = area + I.sum_cap * NG;
+    for (int j = g.lane; j < I.sum_cap; j += G) cst[j * NG] = 0;   // Sec. 5.1.1
+    g.sync();
+    int cmax = 0;
+    for (int p = 0; p < n; ++p) {
+        int i = W[p];
+        if (p == u) i = W[v];
+        else if (p == v) i = W[u];
+        int es = 0;
+        for (int e = I.poff[i] + g.lane; e < I.poff[i + 1]; e += G) es = ::max(es, fin[I.plist[e] * NG]);
+        es = g.max(es);
+        // Eq. 7: es_res = max over used resources of c_k[R_k - r_{i,k}]
+        int er = 0;
+        for (int k = g.lane; k < m; k += G) {
+            const int r = I.reqk[i * m + k];
+            if (r > 0) er = ::max(er, cst[(I.cbase[k] + I.cap[k] - r) * NG]);
+        }
+        er = g.max(er);
+        const int s = ::max(es, er);
+        const int d = I.dur[i];
+        if (d > 0) {
+            for (int k = 0; k < m; ++k) {
+                const int r = I.reqk[i * m + k];
+                if (r == 0) continue;
+                // Alg. 4 as a per-index closed form of its result:
+                //   j <  r : c'[j] = max(c[j], s+d)
+                //   j >= r : c'[j] = c[j-r] <= s ? c[j] : max(c[j], min(c[j-r], s+d))
+                // Chunks are processed from the top so that c[j-r] is still
+                // the old value when it is read.
+                const int R = I.cap[k];
+                int *ck = cst + I.cbase[k] * NG;
+                int last = -1;
+                for (int J = ((R - 1) / G) * G; J >= 0; J -= G) {
+                    const int j = J + g.lane;
+                    int old = 0, prev = 0;
+                    if (j < R) {
+                        old = ck[j * NG];
+                        if (j >= r) prev = ck[(j - r) * NG];
+                    }
+                    g.sync();
+                    if (j < R) {
+                        const int nv = j < r ? ::max(old, s + d)
+                                             : (prev <= s ? old : ::max(old, ::min(prev, s + d)));
+                        if (nv != old) {
+                            ck[j * NG] = nv;
+                            last = ::max(last, j);
+                        }
+                    }
+                    g.sync();
+                }
+                // Alg. 4 stops right after its last change
+                work += g.max(last) + 1;
+            }
+        }
+        if (g.lane == 0) fin[i * NG] = s + d;
+        cmax = ::max(cmax, s + d);
+        g.sync();
+    }
+    (void)err;
+    return cmax;
+}
+
+template <int G>
+__device__ __forceinline__ int decode(const SInst &I, int mode, const int *W, int u, int v, int *area,
+                                      int NG, const Group<G> &g, long long &work, int &err) {
+    return mode == RCPSP_EVAL_CAPACITY ? decode_capacity<G>(I, W, u, v, area, NG, g, work, err)
+                                       : decode_time<G>(I, W, u, v, area, NG, g, work, err);
+}
+
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long y = __shfl_xor_sync(kFull, x, o);
+        x = y < x ? y : x;
+    }
+    return x;
+}
+
+__device__ __forceinline__ long long warp_sum_i64(long long x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+    return x;
+}
+
+__device__ __forceinline__ bool tc_get(const unsigned *tc, int u, int v, int delta) {
+    const int b = u * delta + (v - u - 1);
+    return (tc[b >> 5] >> (b & 31)) & 1u;
+}
+
+__device__ __forceinline__ void tc_put(unsigned *tc, int u, int v, int delta, bool on) {
+    const int b = u * delta + (v - u - 1);
+    if (on) tc[b >> 5] |= 1u << (b & 31);
+    else tc[b >> 5] &= ~(1u << (b & 31));
+}
+
+// ---------------------------------------------------------------------------
+// Persistent search kernel.
+// ---------------------------------------------------------------------------
+template <int G>
+__global__ void __launch_bounds__(1024) search_kernel(const LaunchItem *__restrict__ items, int count,
+                                                      int *__restrict__ queue, int move_cap) {
+    extern __shared__ __align__(16) int sm[];
+    __shared__ int s_item, s_nmoves, s_C, s_Cbest, s_widx, s_it, s_improved, s_err;
+    __shared__ unsigned long long s_best;
+    __shared__ long long s_eval, s_work;
+
+    constexpr int NG = 32 / G;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int warp = tid >> 5, wl = tid & 31;
+    const int ngroups = (nthr >> 5) * NG;
+    const int gid = warp * NG + wl / G;
+    const Group<G> g;
+
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(queue, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= count) break;
+        const LaunchItem it = items[item];
+        const InstHeader &h = it.h;
+        const int n = h.n, mode = it.mode, delta = it.delta, tl = it.tabu_len;
+        const int pw = profile_words(mode, h.wps, h.ub, h.sum_cap);
+        const StateLayout S = state_layout(h.inst_words, n, tl, delta, move_cap, pw, ngroups);
+        stage_instance(sm, it.record, h.inst_words);
+        const SInst I = bind_instance(sm, h);
+        int *W = sm + S.W;
+        int *pos = sm + S.pos;
+        int *Wbest = sm + S.Wbest;
+        int *fsp = sm + S.fsp;
+        int *lpp = sm + S.lpp;
+        int *stl = sm + S.stl;
+        unsigned *tc = reinterpret_cast<unsigned *>(sm + S.tc);
+        int *moves = sm + S.moves;
+        int *area = sm + S.groups + warp * NG * S.group_words + wl / G;
+        const int32_t *W0 = it.record + h.inst_words;
+        for (int p = tid; p < n; p += nthr) {
+            const int a = W0[p];
+            W[p] = a;
+            Wbest[p] = a;
+            pos[a] = p;
+        }
+        for (int x = tid; x < tl; x += nthr) stl[x] = 0;                 // (0,0) = empty move
+        for (int x = tid; x < (n * delta + 31) / 32; x += nthr) tc[x] = 0u;
+        if (tid == 0) {
+            s_widx = 0;
+            s_it = 0;
+            s_eval = 0;
+            s_work = 0;
+            s_err = 0;
+        }
+        __syncthreads();
+        int err = 0;
+        if (gid == 0) {
+            long long w0 = 0;
+            const int c0 = decode<G>(I, mode, W, 0, 0, area, NG, g, w0, err);
+            if (g.lane == 0) {
+                s_C = c0;
+                s_Cbest = c0;
+            }
+        }
+        __syncthreads();
+        const int nslots = n > 3 ? (n - 3) * delta : 0;
+        long long my_work = 0;
+        for (;;) {
+            if (s_it >= it.iterations || (it.stop_at_cp && s_Cbest == h.cp)) break;
+            // 1. first successor / last predecessor position of every position
+            for (int p = tid; p < n; p += nthr) {
+                const int a = W[p];
+                int f = n, l = -1;
+                for (int e = I.soff[a]; e < I.soff[a + 1]; ++e) f = ::min(f, pos[I.slist[e]]);
+                for (int e = I.poff[a]; e < I.poff[a + 1]; ++e) l = ::max(l, pos[I.plist[e]]);
+                fsp[p] = f;
+                lpp[p] = l;
+            }
+            if (tid == 0) s_best = ~0ull;
+            __syncthreads();
+            const int cbest = s_Cbest;
+            unsigned long long my_key = ~0ull;
+            for (int base = 0; base < nslots; base += move_cap) {
+                const int stripe = ::min(move_cap, nslots - base);
+                if (tid == 0) s_nmoves = 0;
+                __syncthreads();
+                // 2. feasible moves of the stripe, compacted
+                for (int k0 = 0; k0 < stripe; k0 += nthr) {
+                    const int k = k0 + tid;
+                    bool ok = false;
+                    int code = 0;
+                    if (k < stripe) {
+                        const int slot = base + k;
+                        const int u = 1 + slot / delta;
+                        const int v = u + 1 + slot % delta;
+                        if (v <= n - 2 && fsp[u] > v && lpp[v] < u) {
+                            ok = true;
+                            code = u | (v << 16);
+                        }
+                    }
+                    const unsigned b = __ballot_sync(kFull, ok);
+                    int wb = 0;
+                    if (wl == 0 && b) wb = atomicAdd(&s_nmoves, __popc(b));
+                    wb = __shfl_sync(kFull, wb, 0);
+                    if (ok) moves[wb + __popc(b & ((1u << wl) - 1u))] = code;
+                }
+                __syncthreads();
+                const int nm = s_nmoves;
+                // 3. decode the neighbours
+                for (int q = gid; q < nm; q += ngroups) {
+                    const int code = moves[q];
+                    const int u = code & 0xffff, v = code >> 16;
+                    const int c = decode<G>(I, mode, W, u, v, area, NG, g, my_work, err);
+                    if (!tc_get(tc, u, v, delta) || c < cbest) {
+                        const unsigned long long key =
+                            (static_cast<unsigned long long>(c) << 32) | static_cast<unsigned>(code & 0xffff) << 16 |
+                            static_cast<unsigned>(v);
+                        my_key = key < my_key ? key : my_key;
+                    }
+                }
+                if (tid == 0) s_eval += nm;
+                __syncthreads();
+            }
+            // 4. best admissible move of the block
+            const unsigned long long wk = warp_min_u64(my_key);
+            if (wl == 0 && wk != ~0ull) atomicMin(&s_best, wk);
+            __syncthreads();
+            // 5. apply, Alg. 3
+            if (tid == 0) {
+                const unsigned long long kb = s_best;
+                int bu = 0, bv = 0;
+                s_improved = 0;
+                if (kb != ~0ull) {
+                    const int c = static_cast<int>(kb >> 32);
+                    bu = static_cast<int>((kb >> 16) & 0xffff);
+                    bv = static_cast<int>(kb & 0xffff);
+                    const int a = W[bu], b = W[bv];
+                    W[bu] = b;
+                    W[bv] = a;
+                    pos[b] = bu;
+                    pos[a] = bv;
+                    s_C = c;
+                    if (c < s_Cbest) {
+                        s_Cbest = c;
+                        s_improved = 1;
+                    }
+                }
+                const int old = stl[s_widx];
+                if (old) tc_put(tc, old & 0xffff, old >> 16, delta, false);
+                stl[s_widx] = bu | (bv << 16);
+                if (bu | bv) tc_put(tc, bu, bv, delta, true);
+                s_widx = s_widx + 1 == tl ? 0 : s_widx + 1;
+                if (it.trace) {
+                    it.trace[3 * s_it + 0] = bu;
+                    it.trace[3 * s_it + 1] = bv;
+                    it.trace[3 * s_it + 2] = s_C;
+                }
+                s_it = s_it + 1;
+            }
+            __syncthreads();
+            if (s_improved)
+                for (int p = tid; p < n; p += nthr) Wbest[p] = W[p];
+        }
+        // work of all groups (the lanes of a group hold the same count)
+        const long long ws = warp_sum_i64(g.lane == 0 ? my_work : 0);
+        if (wl == 0) atomicAdd(reinterpret_cast<unsigned long long *>(&s_work), static_cast<unsigned long long>(ws));
+        if (err) atomicOr(&s_err, err);
+        __syncthreads();
+        // outputs: W*, its schedule S*, statistics
+        int32_t *out = it.out;
+        if (gid == 0) {
+            long long w1 = 0;
+            int e1 = 0;
+            const int cb = decode<G>(I, mode, Wbest, 0, 0, area, NG, g, w1, e1);
+            const int *fin = area + pw * NG;
+            for (int i = g.lane; i < n; i += G) out[n + i] = fin[i * NG] - I.dur[i];
+            if (g.lane == 0) {
+                out[2 * n + kOutCmax] = cb;
+                if (e1 || cb != s_Cbest) atomicOr(&s_err, 2);
+            }
+        }
+        for (int p = tid; p < n; p += nthr) out[p] = Wbest[p];
+        __syncthreads();
+        if (tid == 0) {
+            int32_t *st = out + 2 * n;
+            st[kOutEvalLo] = static_cast<int32_t>(s_eval & 0xffffffffll);
+            st[kOutEvalHi] = static_cast<int32_t>(s_eval >> 32);
+            st[kOutWorkLo] = static_cast<int32_t>(s_work & 0xffffffffll);
+            st[kOutWorkHi] = static_cast<int32_t>(s_work >> 32);
+            st[kOutIters] = s_it;
+            st[kOutMode] = mode;
+            st[kOutStatus] = s_err ? RCPSP_E_DEVICE : 0;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Decoding of caller-given lists (rcpsp_evaluate_lists).
+// ---------------------------------------------------------------------------
+template <int G>
+__global__ void __launch_bounds__(1024) evaluate_kernel(LaunchItem item, const int32_t *__restrict__ lists,
+                                                        int count, int32_t *__restrict__ start,
+                                                        int32_t *__restrict__ cmax_out,
+                                                        long long *__restrict__ work_out,
+                                                        int *__restrict__ err_out) {
+    extern __shared__ __align__(16) int sm[];
+    constexpr int NG = 32 / G;
+    const int tid = threadIdx.x, warp = tid >> 5, wl = tid & 31;
+    const int ngroups = (blockDim.x >> 5) * NG;
+    const int gid = warp * NG + wl / G;
+    const Group<G> g;
+    const InstHeader &h = item.h;
+    const int n = h.n, mode = item.mode;
+    const int pw = profile_words(mode, h.wps, h.ub, h.sum_cap);
+    // per-group list buffers take the place of the move buffer
+    const StateLayout S = state_layout(h.inst_words, n, 0, 0, ngroups * align4(n), pw, ngroups);
+    stage_instance(sm, item.record, h.inst_words);
+    __syncthreads();
+    const SInst I = bind_instance(sm, h);
+    int *myW = sm + S.moves + gid * align4(n);
+    int *area = sm + S.groups + warp * NG * S.group_words + wl / G;
+    int err = 0;
+    for (int l = blockIdx.x * ngroups + gid; l < count; l += gridDim.x * ngroups) {
+        for (int p = g.lane; p < n; p += G) myW[p] = lists[static_cast<long long>(l) * n + p];
+        g.sync();
+        long long wk = 0;
+        const int c = decode<G>(I, mode, myW, 0, 0, area, NG, g, wk, err);
+        const int *fin = area + pw * NG;
+        for (int i = g.lane; i < n; i += G) start[static_cast<long long>(l) * n + i] = fin[i * NG] - I.dur[i];
+        if (g.lane == 0) {
+            cmax_out[l] = c;
+            work_out[l] = wk;
+        }
+        g.sync();
+    }
+    if (err) atomicOr(err_out, err);
+}
+
+template <int G>
+cudaError_t prepare_search_g(size_t smem) {
+    return cudaFuncSetAttribute(search_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(smem));
+}
+
+template <int G>
+cudaError_t occupancy_g(int threads, size_t smem, int *ctas) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, search_kernel<G>, threads, smem);
+}
+
+template <int G>
+cudaError_t launch_search_g(const LaunchItem *items, int count, int *queue, int move_cap, int blocks,
+                            int threads, size_t smem, cudaStream_t st) {
+    search_kernel<G><<<blocks, threads, smem, st>>>(items, count, queue, move_cap);
+    return cudaGetLastError();
+}
+
+template <int G>
+cudaError_t launch_eval_g(const LaunchItem &item, const int32_t *lists, int count, int32_t *start,
+                          int32_t *cmax, long long *work, int *err, int blocks, int threads, size_t smem,
+                          cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(evaluate_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    evaluate_kernel<G><<<blocks, threads, smem, st>>>(item, lists, count, start, cmax, work, err);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+#define RCPSP_DISPATCH_G(G_, CALL)                 \
+    switch (G_) {                                  \
+        case 1: { constexpr int GG = 1; CALL; }    \
+        case 2: { constexpr int GG = 2; CALL; }    \
+        case 4: { constexpr int GG = 4; CALL; }    \
+        case 8: { constexpr int GG = 8; CALL; }    \
+        case 16: { constexpr int GG = 16; CALL; }  \
+        case 32: { constexpr int GG = 32; CALL; }  \
+        default: return cudaErrorInvalidValue;     \
+    }
+
+cudaError_t prepare_search(int group_size, size_t smem) {
+    RCPSP_DISPATCH_G(group_size, return prepare_search_g<GG>(smem))
+}
+
+cudaError_t search_occupancy(int group_size, int threads, size_t smem, int *ctas) {
+    RCPSP_DISPATCH_G(group_size, return occupancy_g<GG>(threads, smem, ctas))
+}
+
+cudaError_t launch_search(int group_size, const LaunchItem *items, int count, int *queue, int move_cap,
+                          int blocks, int threads, size_t smem, cudaStream_t st) {
+    switch (group_size) {
+        case 1: return launch_search_g<1>(items, count, queue, move_cap, blocks, threads, smem, st);
+        case 2: return launch_search_g<2>(items, count, queue, move_cap, blocks, threads, smem, st);
+        case 4: return launch_search_g<4>(items, count, queue, move_cap, blocks, threads, smem, st);
+        case 8: return launch_search_g<8>(items, count, queue, move_cap, blocks, threads, smem, st);
+        case 16: return launch_search_g<16>(items, count, queue, move_cap, blocks, threads, smem, st);
+        case 32: return launch_search_g<32>(items, count, queue, move_cap, blocks, threads, smem, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_evaluate(int group_size, const LaunchItem &item, const int32_t *lists, int count,
+                            int32_t *start, int32_t *cmax, long long *work, int *err, int blocks, int threads,
+                            size_t smem, cudaStream_t st) {
+    switch (group_size) {
+        case 1: return launch_eval_g<1>(item, lists, count, start, cmax, work, err, blocks, threads, smem, st);
+        case 2: return launch_eval_g<2>(item, lists, count, start, cmax, work, err, blocks, threads, smem, st);
+        case 4: return launch_eval_g<4>(item, lists, count, start, cmax, work, err, blocks, threads, smem, st);
+        case 8: return launch_eval_g<8>(item, lists, count, start, cmax, work, err, blocks, threads, smem, st);
+        case 16: return launch_eval_g<16>(item, lists, count, start, cmax, work, err, blocks, threads, smem, st);
+        case 32: return launch_eval_g<32>(item, lists, count, start, cmax, work, err, blocks, threads, smem, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace rcpsp

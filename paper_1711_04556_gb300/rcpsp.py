@@ -1,0 +1,246 @@
+"""Python binding of the C interface in include/rcpsp.h (argument marshalling only).
+
+Every step of the search runs in the CUDA library; this module converts
+numpy arrays to the C structs, hands PyTorch's CUDA caching allocator and
+streams to the library, and converts results back.  There is no CPU path:
+without the built library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librcpsp_gb300.so")
+
+EVAL_AUTO, EVAL_TIME, EVAL_CAPACITY = 0, 1, 2
+ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "CYCLE", -3: "DUMMY", -4: "DEMAND_EXCEEDS_CAP",
+          -5: "TOO_LARGE", -6: "CUDA", -7: "TIMEOUT", -8: "NOT_FOUND", -9: "DEVICE"}
+EXPORTS = ("rcpsp_create", "rcpsp_destroy", "rcpsp_load_instances", "rcpsp_free_instances",
+           "rcpsp_tabu_search", "rcpsp_get_schedules", "rcpsp_get_trace", "rcpsp_evaluate_lists",
+           "rcpsp_prepare_instance", "rcpsp_last_error")
+
+
+class RcpspError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Instance(C.Structure):
+    _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("dur", C.POINTER(C.c_int32)),
+                ("cap", C.POINTER(C.c_int32)), ("req", C.POINTER(C.c_int32)),
+                ("succ_off", C.POINTER(C.c_int32)), ("succ", C.POINTER(C.c_int32)),
+                ("level_key", C.POINTER(C.c_int32))]
+
+
+class Params(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("max_swap_dist", C.c_int32), ("tabu_len", C.c_int32),
+                ("eval_mode", C.c_int32), ("stop_at_cp", C.c_int32), ("group_size", C.c_int32),
+                ("warps_per_cta", C.c_int32), ("record_trace", C.c_int32), ("use_graph", C.c_int32)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("evaluated", C.c_int64), ("work", C.c_int64), ("iterations", C.c_int32),
+                ("eval_mode", C.c_int32), ("critical_path", C.c_int32), ("status", C.c_int32)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class Allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("release", FREE_FN), ("user", C.c_void_p)]
+
+
+_lib_handle = None
+
+
+def library(path: Optional[str] = None):
+    """Loads the CUDA library; raises if it has not been built."""
+    global _lib_handle
+    if _lib_handle is not None and path is None:
+        return _lib_handle
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"CUDA library {p} is missing: build it with paper_1711_04556_gb300.build.build()")
+    h = C.CDLL(p)
+    P = C.POINTER
+    sig = {
+        "rcpsp_create": (C.c_int, [P(C.c_void_p), C.c_int, P(Allocator)]),
+        "rcpsp_destroy": (C.c_int, [C.c_void_p]),
+        "rcpsp_load_instances": (C.c_int, [C.c_void_p, P(Instance), C.c_int32, P(C.c_int32)]),
+        "rcpsp_free_instances": (C.c_int, [C.c_void_p, P(C.c_int32), C.c_int32]),
+        "rcpsp_tabu_search": (C.c_int, [C.c_void_p, P(C.c_int32), C.c_int32, P(Params), C.c_void_p]),
+        "rcpsp_get_schedules": (C.c_int, [C.c_void_p, P(C.c_int32), C.c_int32, P(C.c_int32), P(C.c_int32),
+                                          P(C.c_int32), P(Stats)]),
+        "rcpsp_get_trace": (C.c_int, [C.c_void_p, C.c_int32, P(C.c_int32), C.c_int32, P(C.c_int32)]),
+        "rcpsp_evaluate_lists": (C.c_int, [C.c_void_p, C.c_int32, P(C.c_int32), C.c_int32, C.c_int32,
+                                           P(C.c_int32), P(C.c_int32), P(C.c_int64), C.c_void_p]),
+        "rcpsp_prepare_instance": (C.c_int, [P(Instance), P(C.c_int32), P(C.c_int32), P(C.c_int32),
+                                             P(C.c_int32), C.c_char_p, C.c_int32]),
+        "rcpsp_last_error": (C.c_char_p, [C.c_void_p]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(h, name)
+        f.restype, f.argtypes = res, args
+    if path is None:
+        _lib_handle = h
+    return h
+
+
+def _i32(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _ptr(a: np.ndarray, ty=C.c_int32):
+    return a.ctypes.data_as(C.POINTER(ty))
+
+
+class _Marshalled:
+    def __init__(self, inst, level_key=None):
+        self.arrs = [_i32(x) for x in (inst.dur, inst.cap, inst.req, inst.succ_off, inst.succ)]
+        self.key = None if level_key is None else _i32(level_key)
+        self.s = Instance(inst.n, inst.m, *[_ptr(a) for a in self.arrs],
+                          _ptr(self.key) if self.key is not None else None)
+
+
+def _torch_allocator():
+    """Device memory from PyTorch's caching allocator."""
+    import torch
+
+    live = {}
+
+    def alloc(nbytes, stream, user):
+        try:
+            dev = torch.cuda.current_device()
+            p = torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream or 0)
+            live[p] = nbytes
+            return p
+        except Exception:  # the library reports the failure as RCPSP_E_CUDA
+            return None
+
+    def release(ptr, nbytes, stream, user):
+        if ptr in live:
+            del live[ptr]
+            torch.cuda.caching_allocator_delete(ptr)
+
+    return ALLOC_FN(alloc), FREE_FN(release)
+
+
+def prepare(inst, level_key=None, lib_path: Optional[str] = None) -> dict:
+    """Host preparation of one instance without a GPU (rcpsp_prepare_instance)."""
+    lib = library(lib_path)
+    m = _Marshalled(inst, level_key)
+    cp, ub, mode = C.c_int32(0), C.c_int32(0), C.c_int32(0)
+    W = np.zeros(inst.n, np.int32)
+    msg = C.create_string_buffer(256)
+    rc = lib.rcpsp_prepare_instance(C.byref(m.s), C.byref(cp), C.byref(ub), _ptr(W), C.byref(mode), msg, 256)
+    if rc != 0:
+        raise RcpspError(rc, msg.value.decode())
+    return dict(cp=cp.value, ub=ub.value, initial=W, mode=mode.value)
+
+
+class Solver:
+    """One library context on one CUDA device."""
+
+    def __init__(self, device: int = 0, torch_memory: bool = True, lib_path: Optional[str] = None):
+        self.lib = library(lib_path)
+        self.ctx = C.c_void_p()
+        self._cbs = None
+        alloc = None
+        if torch_memory:
+            import torch
+            torch.cuda.set_device(device)
+            self._cbs = _torch_allocator()
+            alloc = Allocator(self._cbs[0], self._cbs[1], None)
+        self._check(self.lib.rcpsp_create(C.byref(self.ctx), device, C.byref(alloc) if alloc else None))
+        self.n_of = {}
+
+    def _check(self, rc: int):
+        if rc != 0:
+            msg = self.lib.rcpsp_last_error(self.ctx).decode() if self.ctx else ""
+            raise RcpspError(rc, msg)
+
+    def close(self):
+        if self.ctx:
+            self.lib.rcpsp_destroy(self.ctx)
+            self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ------------------------------------------------------------------ calls
+    def load(self, instances: Sequence, level_keys: Optional[Sequence] = None) -> np.ndarray:
+        ms = [_Marshalled(x, None if level_keys is None else level_keys[k]) for k, x in enumerate(instances)]
+        arr = (Instance * len(ms))(*[m.s for m in ms])
+        ids = np.zeros(len(ms), np.int32)
+        self._check(self.lib.rcpsp_load_instances(self.ctx, arr, len(ms), _ptr(ids)))
+        for i, x in zip(ids, instances):
+            self.n_of[int(i)] = x.n
+        return ids
+
+    def free(self, ids):
+        ids = _i32(ids)
+        self._check(self.lib.rcpsp_free_instances(self.ctx, _ptr(ids), len(ids)))
+        for i in ids:
+            self.n_of.pop(int(i), None)
+
+    def search(self, ids, iterations: int = 100, delta: int = 0, tabu_len: int = 0, mode: int = EVAL_AUTO,
+               stop_at_cp: bool = True, group_size: int = 0, warps_per_cta: int = 0, trace: bool = False,
+               use_graph: bool = False, stream=None):
+        """Asynchronous search on ``stream`` (a torch.cuda.Stream, a raw handle or None)."""
+        ids = _i32(ids)
+        p = Params(iterations, delta, tabu_len, mode, int(stop_at_cp), group_size, warps_per_cta,
+                   int(trace), int(use_graph))
+        handle = getattr(stream, "cuda_stream", stream) or None
+        self._check(self.lib.rcpsp_tabu_search(self.ctx, _ptr(ids), len(ids), C.byref(p), handle))
+
+    def results(self, ids) -> List[dict]:
+        ids = _i32(ids)
+        ns = [self.n_of[int(i)] for i in ids]
+        tot = int(sum(ns))
+        order = np.zeros(tot, np.int32)
+        start = np.zeros(tot, np.int32)
+        cmax = np.zeros(len(ids), np.int32)
+        stats = (Stats * len(ids))()
+        self._check(self.lib.rcpsp_get_schedules(self.ctx, _ptr(ids), len(ids), _ptr(order), _ptr(start),
+                                                 _ptr(cmax), stats))
+        out, at = [], 0
+        for k, n in enumerate(ns):
+            s = stats[k]
+            out.append(dict(best_W=order[at:at + n], best_S=start[at:at + n], best_cmax=int(cmax[k]),
+                            evaluated=int(s.evaluated), work=int(s.work), iterations=int(s.iterations),
+                            mode=int(s.eval_mode), cp=int(s.critical_path), status=int(s.status)))
+            at += n
+        return out
+
+    def trace(self, id_: int, iterations: int) -> np.ndarray:
+        buf = np.zeros(max(1, 3 * iterations), np.int32)
+        written = C.c_int32(0)
+        self._check(self.lib.rcpsp_get_trace(self.ctx, int(id_), _ptr(buf), buf.size, C.byref(written)))
+        return buf[:3 * written.value].reshape(-1, 3)
+
+    def evaluate_lists(self, id_: int, lists, mode: int = EVAL_AUTO, stream=None):
+        lists = _i32(lists)
+        n = self.n_of[int(id_)]
+        cnt = lists.size // n
+        start = np.zeros(cnt * n, np.int32)
+        cmax = np.zeros(cnt, np.int32)
+        work = np.zeros(cnt, np.int64)
+        handle = getattr(stream, "cuda_stream", stream) or None
+        self._check(self.lib.rcpsp_evaluate_lists(self.ctx, int(id_), _ptr(lists), cnt, mode, _ptr(start),
+                                                  _ptr(cmax), _ptr(work, C.c_int64), handle))
+        return cmax, start.reshape(cnt, n), work

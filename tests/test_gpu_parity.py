@@ -1,0 +1,168 @@
+"""GPU parity: the CUDA path against the CPU reference, bit-exact.
+
+Integer results must be identical: every decoded start time and makespan,
+the work counters, the whole tabu trajectory (u, v, C per iteration), the
+best list, its schedule, the makespan and the number of evaluated
+neighbours.  Sizes span several CTAs, group shapes and ragged stripes.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_1711_04556_gb300 import instances as I
+from paper_1711_04556_gb300 import rcpsp as R
+from test_oracle_pins import medium_instances, random_feasible_list
+
+pytestmark = pytest.mark.gpu
+
+NPROC = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module")
+def solver():
+    from paper_1711_04556_gb300 import build as B
+    B.build()
+    s = R.Solver(0)
+    yield s
+    s.close()
+
+
+def compare_search(oracle, gpu, ref, trace_gpu=None):
+    assert gpu["status"] == 0
+    assert gpu["best_cmax"] == ref["best_cmax"]
+    assert gpu["iterations"] == ref["iterations"]
+    assert gpu["evaluated"] == ref["evaluated"]
+    assert gpu["work"] == ref["work"]
+    assert gpu["best_W"].tolist() == ref["best_W"].tolist()
+    assert gpu["best_S"].tolist() == ref["best_S"].tolist()
+    assert gpu["cp"] == ref["cp"] and gpu["mode"] == ref["mode"]
+    if trace_gpu is not None:
+        assert trace_gpu.tolist() == ref["trace"].tolist()
+
+
+# ----------------------------------------------------------------- decoders
+def test_table1_decode(solver, oracle):
+    from golden import fixtures
+    text, vals = fixtures.read("table1_instance.txt")
+    inst = I.Instance.from_text(text)
+    ids = solver.load([inst])
+    for mode in (R.EVAL_TIME, R.EVAL_CAPACITY):
+        cmax, S, work = solver.evaluate_lists(ids[0], np.array([vals["W"]], np.int32), mode)
+        ref = oracle.decode(inst, vals["W"], mode)
+        assert cmax[0] == 22 and S[0].tolist() == ref[1].tolist() and work[0] == ref[2]
+    solver.free(ids)
+
+
+@pytest.mark.parametrize("family", ["medium", "j30", "j120", "mixed"])
+def test_decoders_on_random_lists(solver, oracle, family):
+    rng = np.random.default_rng(17)
+    insts = {"medium": medium_instances(24, first=900),
+             "j30": I.config_batch("j30_batch", 12),
+             "j120": I.config_batch("j120_batch", 4),
+             "mixed": I.config_batch("mixed_batch", 12)}[family]
+    ids = solver.load(insts)
+    for inst, i in zip(insts, ids):
+        lists = np.stack([random_feasible_list(inst, rng) for _ in range(5)])
+        for mode in (R.EVAL_TIME, R.EVAL_CAPACITY):
+            cmax, S, work = solver.evaluate_lists(i, lists, mode)
+            for k in range(len(lists)):
+                c, s, w = oracle.decode(inst, lists[k], mode)
+                assert cmax[k] == c and S[k].tolist() == s.tolist() and work[k] == w
+    solver.free(ids)
+
+
+# ---------------------------------------------------------------- searches
+@pytest.mark.parametrize("G", [1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("mode", [R.EVAL_TIME, R.EVAL_CAPACITY])
+def test_single_instance_search_all_group_sizes(solver, oracle, G, mode):
+    inst = I.config_batch("j30_single")[0]
+    ref = oracle.tabu_search(inst, 100, 20, 60, mode, 1, trace=True)
+    ids = solver.load([inst])
+    for warps in ((1, 2, 4) if G <= 2 else (1, 3, 8)):
+        solver.search(ids, iterations=100, delta=20, tabu_len=60, mode=mode, group_size=G,
+                      warps_per_cta=warps, trace=True)
+        res = solver.results(ids)[0]
+        compare_search(oracle, res, ref, solver.trace(ids[0], 100))
+    solver.free(ids)
+
+
+def test_j30_batch_full_size(solver, oracle):
+    """The 480-instance, 1000-iteration workload in the default launch shape."""
+    insts = I.config_batch("j30_batch")
+    ids = solver.load(insts)
+    solver.search(ids, iterations=1000, delta=20, tabu_len=60, mode=R.EVAL_AUTO)
+    got = solver.results(ids)
+    ref = oracle.tabu_search_batch(insts, [(1000, 20, 60, 0, 1)] * len(insts), NPROC)
+    for g, r in zip(got, ref):
+        compare_search(oracle, g, r)
+    solver.free(ids)
+
+
+@pytest.mark.parametrize("mode", [R.EVAL_TIME, R.EVAL_CAPACITY])
+def test_j120_sample(solver, oracle, mode):
+    insts = I.config_batch("j120_batch", 10)
+    ids = solver.load(insts)
+    solver.search(ids, iterations=60, delta=60, tabu_len=800, mode=mode, trace=True)
+    got = solver.results(ids)
+    ref = oracle.tabu_search_batch(insts, [(60, 60, 800, mode, 1)] * len(insts), NPROC, trace=True)
+    for k, (g, r) in enumerate(zip(got, ref)):
+        compare_search(oracle, g, r, solver.trace(ids[k], 60))
+    solver.free(ids)
+
+
+def test_mixed_sample_auto(solver, oracle):
+    insts = I.config_batch("mixed_batch", 20)
+    ids = solver.load(insts)
+    solver.search(ids, iterations=12, delta=0, tabu_len=0, mode=R.EVAL_AUTO)
+    got = solver.results(ids)
+    params = []
+    for x in insts:
+        a = x.n - 2
+        params.append((12,) + ((20, 60) if a <= 45 else (60, 250) if a <= 75 else (60, 600) if a <= 105
+                               else (60, 800)) + (0, 1))
+    ref = oracle.tabu_search_batch(insts, params, NPROC)
+    for g, r in zip(got, ref):
+        compare_search(oracle, g, r)
+    solver.free(ids)
+
+
+# -------------------------------------------------------------- edge cases
+def test_edge_cases(solver, oracle):
+    base = medium_instances(1, first=1000)[0]
+    big = np.array([base.req[k::base.m].sum() + 1 for k in range(base.m)], np.int32)
+    free = I.Instance(base.n, base.m, base.dur, big, base.req, base.succ_off, base.succ)
+    n = 5
+    succ_sets = [[1]] + [[i + 1] for i in range(1, n + 1)] + [[]]
+    off = np.r_[0, np.cumsum([len(s) for s in succ_sets])].astype(np.int32)
+    chain = I.Instance(n + 2, 1, np.r_[0, np.full(n, 2), 0].astype(np.int32), np.array([1], np.int32),
+                       np.r_[0, np.ones(n), 0].astype(np.int32), off,
+                       np.array([x for s in succ_sets for x in s], np.int32))
+    one = I.generate(2, 1, 2, 150, 50, stream=11)            # N = 3: no moves at all
+    relab = I.generate(5, 14, 3, 210, 20, relabel=True, stream=11)
+    cases = [(free, (40, 6, 5, 1, 1)), (chain, (7, 4, 3, 1, 0)), (one, (5, 3, 2, 2, 0)),
+             (relab, (25, 1, 1, 1, 0)), (relab, (25, 50, 1, 2, 0)), (base, (0, 5, 5, 1, 1)),
+             (base, (30, 3, 200, 2, 0))]
+    for inst, (it, dl, tl, mode, stop) in cases:
+        ids = solver.load([inst])
+        solver.search(ids, iterations=it, delta=dl, tabu_len=tl, mode=mode, stop_at_cp=bool(stop), trace=True)
+        ref = oracle.tabu_search(inst, it, dl, tl, mode, stop, trace=True)
+        compare_search(oracle, solver.results(ids)[0], ref, solver.trace(ids[0], max(it, 1)))
+        solver.free(ids)
+
+
+def test_level_keys_and_repeat_with_graph(solver, oracle):
+    import torch
+    insts = I.config_batch("j30_batch", 40, first=100)
+    keys = [I.level_keys(x, k) for k, x in enumerate(insts)]
+    ids = solver.load(insts, keys)
+    st = torch.cuda.Stream()
+    outs = []
+    for _ in range(3):
+        solver.search(ids, iterations=50, delta=20, tabu_len=60, use_graph=True, stream=st)
+        outs.append(solver.results(ids))
+    ref = oracle.tabu_search_batch(insts, [(50, 20, 60, 0, 1)] * len(insts), NPROC, level_keys=keys)
+    for o in outs:
+        for g, r in zip(o, ref):
+            compare_search(oracle, g, r)
+    solver.free(ids)
