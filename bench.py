@@ -1,0 +1,397 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 tabu search: evaluated neighbour schedules per second.
+
+One step = one pass of the whole search path over a batch of synthetic
+instances: 480 instances of 30 non-dummy activities (4 resources, network
+complexity 1.5/1.8/2.1, resource strength 0.2/0.5/0.7/1.0), 1000 tabu
+iterations each (swap distance 20, tabu list 60, evaluator by the selection
+rule), all in one persistent launch replayed from a CUDA graph.  ``value``
+counts the neighbour schedules the searches decoded (the paper's Sched_sec)
+per second of device time with the instances resident in HBM; ``e2e`` is
+the same count through the C interface with host buffers (instance upload,
+host preparation, search, result download).
+
+Run: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun each rank solves its own 480 instances (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(family="j30_batch", count=480, iterations=1000, delta=20, tabu_len=60)
+METRIC = "neighbour schedules evaluated/sec on 1 GB300 (bit-exact) + p50/p99 solve latency"
+UNIT = "schedules/s"
+KERNEL_SOURCES = ["paper_1711_04556_gb300/csrc/search_kernel.cu", "paper_1711_04556_gb300/csrc/rcpsp_internal.h"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "search_kernel_j30_batch.traffic.json")
+
+
+def workload_config(extra=None):
+    cfg = {"workload": "j30_batch: 480 synthetic RCPSP instances, n=30 (+2 dummies), M=4, durations 1-10, "
+                       "demands 1-10 w.p. 0.5, NC in {1.5,1.8,2.1}, RS in {0.2,0.5,0.7,1.0}; 1000 tabu "
+                       "iterations each, swap distance 20, tabu list 60, evaluator by the selection rule; "
+                       "one persistent CUDA-graph launch per step",
+           "instances": WORKLOAD["count"], "iterations": WORKLOAD["iterations"],
+           "delta": WORKLOAD["delta"], "tabu_len": WORKLOAD["tabu_len"],
+           "l2": "flushed between timed steps (256 MiB write); inputs are a few hundred KB"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = None
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_ops(insts, results):
+    """Resource-cell operations of the decodes the searches performed.
+
+    Time-indexed (Algs. 5-7): every loop step of Alg. 5 tests M cells, Alg. 6
+    updates M cells on each of the d_i steps of every activity (M * UB per
+    schedule) and Alg. 7 reads |E| predecessor finish times.  Capacity-indexed
+    (Eq. 7, Alg. 4): one read per used resource of every activity, one cell per
+    Alg. 4 loop step, |E| predecessor reads.  ``work`` is the exact Alg. 5 or
+    Alg. 4 step count the kernel reports (bit-exact with the CPU reference).
+    """
+    ops = 0
+    for inst, r in zip(insts, results):
+        ev = r["evaluated"]
+        arcs = int(inst.succ_off[-1])
+        if r["mode"] == 1:
+            ops += inst.m * (r["work"] + ev * int(inst.dur.sum())) + ev * arcs
+        else:
+            used = int(np.count_nonzero(inst.req))
+            ops += r["work"] + ev * (used + arcs)
+    return ops
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic():
+    try:
+        d = json.load(open(TRAFFIC_FILE))
+        if d.get("kernel_hash") == kernel_hash():
+            return d.get("dram_bytes_per_launch")
+    except Exception:
+        pass
+    return None
+
+
+def cpu_baseline(sample: int):
+    """The CPU reference, as it stands, on a bounded sample of the workload."""
+    from oracle import oracle as O
+    from paper_1711_04556_gb300 import instances as I
+    O.build()
+    insts = I.config_batch(WORKLOAD["family"], sample)
+    cores = os.cpu_count() or 1
+    p = (WORKLOAD["iterations"], WORKLOAD["delta"], WORKLOAD["tabu_len"], O.AUTO, 1)
+    t0 = time.perf_counter()
+    res = O.tabu_search_batch(insts, [p] * len(insts), cores)
+    dt = time.perf_counter() - t0
+    ev = sum(r["evaluated"] for r in res)
+    return {"value": ev / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {sample} of the {WORKLOAD['count']} instances, {WORKLOAD['iterations']} "
+                      f"iterations each, one search per host thread ({ev} schedules in {dt:.2f} s)"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    from paper_1711_04556_gb300 import instances as I
+    O.build()
+    sample = args.reference_sample
+    insts = I.config_batch(WORKLOAD["family"], sample)
+    cores = os.cpu_count() or 1
+    p = (WORKLOAD["iterations"], WORKLOAD["delta"], WORKLOAD["tabu_len"], O.AUTO, 1)
+    for _ in range(args.warmup):
+        O.tabu_search_batch(insts[:max(1, cores)], [p] * min(len(insts), max(1, cores)), cores)
+    ev_total, t_total = 0, 0.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        res = O.tabu_search_batch(insts, [p] * len(insts), cores)
+        t_total += time.perf_counter() - t0
+        ev_total += sum(r["evaluated"] for r in res)
+    value = ev_total / t_total
+    sample_txt = (f"each step: first {sample} of the {WORKLOAD['count']} instances, {WORKLOAD['iterations']} "
+                  f"iterations each, one search per host thread")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * t_total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "impl": "reference", "config": workload_config({"reference_sample": sample}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample_txt},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def percentiles(xs):
+    xs = np.asarray(xs, dtype=np.float64)
+    return float(np.percentile(xs, 50)), float(np.percentile(xs, 99))
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world, rank, local = dist_env()
+    if world > 1:
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
+    if not torch.cuda.is_available():
+        raise RuntimeError("no CUDA device: the benchmark needs a GPU")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1711_04556_gb300 import build as B
+    from paper_1711_04556_gb300 import instances as I
+    from paper_1711_04556_gb300 import rcpsp as R
+    B.build()
+    insts = I.config_batch(WORKLOAD["family"], WORKLOAD["count"], first=rank * WORKLOAD["count"])
+    solver = R.Solver(local)
+    st = torch.cuda.Stream(device=dev)
+    kw = dict(iterations=WORKLOAD["iterations"], delta=WORKLOAD["delta"], tabu_len=WORKLOAD["tabu_len"],
+              mode=R.EVAL_AUTO, group_size=args.group_size, warps_per_cta=args.warps)
+    ids = solver.load(insts)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)   # 256 MiB > L2
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        solver.search(ids, use_graph=True, stream=st, **kw)
+        solver.results(ids)
+    ref_res = solver.results(ids)
+    assert all(r["status"] == 0 for r in ref_res), "a search reported an error"
+    ev_step = sum(r["evaluated"] for r in ref_res)
+    ops_step = algorithmic_ops(insts, ref_res)
+
+    # ---------------- timed region: K steps, device time by CUDA events
+    barrier()
+    sampler = ClockSampler(local)
+    time.sleep(0.3)
+    events = []
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        with torch.cuda.stream(st):
+            flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        solver.search(ids, use_graph=True, stream=st, **kw)
+        e1.record(st)
+        events.append((e0, e1))
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in events]
+    res = solver.results(ids)
+    for a, b in zip(res, ref_res):   # every step reproduces the same searches
+        assert a["best_cmax"] == b["best_cmax"] and a["evaluated"] == b["evaluated"]
+    dev_s = sum(step_ms) / 1000.0
+    if world > 1:
+        t = torch.tensor([dev_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_s = float(t.item())
+        e = torch.tensor([ev_step], dtype=torch.float64, device=dev)
+        dist.all_reduce(e, op=dist.ReduceOp.SUM)
+        ev_all = float(e.item())
+    else:
+        ev_all = float(ev_step)
+    value = ev_all * args.steps / dev_s
+
+    # in-batch solve latency from the device timestamps of the last step
+    t0 = min(r["t_start_ns"] for r in res)
+    done_ms = [(r["t_end_ns"] - t0) / 1e6 for r in res]
+    service_ms = [(r["t_end_ns"] - r["t_start_ns"]) / 1e6 for r in res]
+
+    # ---------------- end to end through the C interface, host buffers
+    h0, d0 = solver.transfer_bytes()
+    e2e_steps = max(1, min(args.steps, 5))
+    barrier()
+    t_e2e = time.perf_counter()
+    ev_e2e = 0
+    for _ in range(e2e_steps):
+        ids2 = solver.load(insts)
+        solver.search(ids2, use_graph=False, stream=st, **kw)
+        out = solver.results(ids2)
+        ev_e2e += sum(r["evaluated"] for r in out)
+        solver.free(ids2)
+    barrier()
+    t_e2e = time.perf_counter() - t_e2e
+    h1, d1 = solver.transfer_bytes()
+    e2e_val = ev_e2e / t_e2e
+    if world > 1:
+        t = torch.tensor([t_e2e, ev_e2e], dtype=torch.float64, device=dev)
+        tm = t.clone()
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        e2e_val = float(t[1].item()) / float(tm[0].item())
+
+    extra = {}
+    if rank == 0:
+        # plain form: one instance per launch, sequential, on a sample
+        sample = insts[:args.plain_sample]
+        sid = ids[:args.plain_sample]
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        ev_plain = 0
+        for i in sid:
+            solver.search([i], use_graph=False, stream=st, **kw)
+        e1.record(st)
+        barrier()
+        ev_plain = sum(r["evaluated"] for r in solver.results(sid))
+        plain = ev_plain / (e0.elapsed_time(e1) / 1000.0)
+        extra["plain_per_instance_launch"] = {"value": plain, "unit": UNIT,
+                                              "sample": f"first {len(sid)} instances, one launch each",
+                                              "batched_over_plain": value / world / plain}
+        # single-instance solve latency (one instance, 100 iterations), repeated
+        one = I.config_batch("j30_single")
+        lat = []
+        for _ in range(args.latency_reps):
+            t0h = time.perf_counter()
+            i1 = solver.load(one)
+            solver.search(i1, iterations=100, delta=20, tabu_len=60, mode=R.EVAL_AUTO, stream=st)
+            solver.results(i1)
+            solver.free(i1)
+            lat.append((time.perf_counter() - t0h) * 1000)
+        p50, p99 = percentiles(lat)
+        b50, b99 = percentiles(done_ms)
+        s50, s99 = percentiles(service_ms)
+        extra["latency_ms"] = {
+            "single_instance_e2e": {"p50": p50, "p99": p99, "reps": args.latency_reps,
+                                    "what": "1 instance, 100 iterations, load+search+results through the C API"},
+            "in_batch_completion": {"p50": b50, "p99": b99, "what": "device time from the first search start to each instance's results, one batched step"},
+            "in_batch_service": {"p50": s50, "p99": s99, "what": "device time from each search start to its results"}}
+
+    if rank != 0:
+        solver.close()
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    max_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak = sms * 128 * max_mhz * 1e6 / 1e9            # INT32 lane-ops/s, in Gop/s
+    per_launch_s = dev_s / args.steps if world == 1 else sum(step_ms) / 1000.0 / args.steps
+    achieved = ops_step / per_launch_s / 1e9
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_sample)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sum(step_ms) / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": workload_config({"parallelism": f"replicas{world}" if world > 1 else "single GPU",
+                                   "schedules_per_step": ev_step, "wall_s_timed": t_wall}),
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": (h1 - h0) // e2e_steps,
+                "d2h_bytes_per_step": (d1 - d0) // e2e_steps},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
+                     "frac": achieved / peak, "traffic": load_traffic(),
+                     "ops_per_launch": ops_step,
+                     "peak_basis": f"{sms} SMs x 128 INT32 lanes x {max_mhz:.0f} MHz (derived, not measured)"},
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+    }
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--group-size", type=int, default=0)
+    ap.add_argument("--warps", type=int, default=0)
+    ap.add_argument("--plain-sample", type=int, default=48)
+    ap.add_argument("--latency-reps", type=int, default=100)
+    ap.add_argument("--cpu-sample", type=int, default=160)
+    ap.add_argument("--reference-sample", type=int, default=48)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    return run_reference(args) if args.impl == "reference" else run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

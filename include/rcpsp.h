@@ -99,6 +99,8 @@ typedef struct {
     int32_t eval_mode;          /* evaluator used (RCPSP_EVAL_TIME / _CAPACITY)  */
     int32_t critical_path;      /* critical-path length (Sec. 2)                */
     int32_t status;             /* 0, or a negative RCPSP_E_* code              */
+    int64_t t_start_ns;         /* device global timer when the search started   */
+    int64_t t_end_ns;           /* device global timer when its results were out */
 } rcpsp_stats;
 
 /* Optional device allocator.  alloc returns device memory of `bytes` bytes
@@ -174,6 +176,10 @@ int rcpsp_evaluate_lists(rcpsp_ctx *ctx, int32_t id, const int32_t *lists, int32
  * gets the reason of a failure.  Returns the same codes as loading. */
 int rcpsp_prepare_instance(const rcpsp_instance *inst, int32_t *critical_path, int32_t *horizon,
                            int32_t *initial_order, int32_t *eval_mode, char *msg, int32_t msg_len);
+
+/* Bytes the context has copied host->device and device->host since it was
+ * created (instance records, launch plans, results, traces); host. */
+int rcpsp_transfer_bytes(const rcpsp_ctx *ctx, int64_t *h2d, int64_t *d2h);
 
 /* Text of the last error of the context (never NULL). */
 const char *rcpsp_last_error(const rcpsp_ctx *ctx);

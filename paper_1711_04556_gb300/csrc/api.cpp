@@ -65,6 +65,7 @@ struct rcpsp_ctx {
     std::vector<LaunchItem> g_items;
     int g_shape[5] = {0, 0, 0, 0, 0};
     cudaStream_t g_stream = nullptr;
+    long long h2d = 0, d2h = 0;   // bytes copied by the context
 };
 
 namespace {
@@ -188,6 +189,13 @@ int rcpsp_destroy(rcpsp_ctx *c) {
 
 const char *rcpsp_last_error(const rcpsp_ctx *c) { return c ? c->err.c_str() : "null context"; }
 
+int rcpsp_transfer_bytes(const rcpsp_ctx *c, int64_t *h2d, int64_t *d2h) {
+    if (!c) return RCPSP_E_INVALID_ARG;
+    if (h2d) *h2d = c->h2d;
+    if (d2h) *d2h = c->d2h;
+    return RCPSP_OK;
+}
+
 int rcpsp_prepare_instance(const rcpsp_instance *inst, int32_t *critical_path, int32_t *horizon,
                            int32_t *initial_order, int32_t *eval_mode, char *msg, int32_t msg_len) {
     if (!inst) return RCPSP_E_INVALID_ARG;
@@ -233,6 +241,7 @@ int rcpsp_load_instances(rcpsp_ctx *c, const rcpsp_instance *inst, int32_t count
         ro += packed[k].record.size();
     }
     cudaError_t e = cudaMemcpy(b.ptr, host.data(), rec_words * 4, cudaMemcpyHostToDevice);
+    c->h2d += static_cast<long long>(rec_words) * 4;
     if (e == cudaSuccess) e = cudaMemset(static_cast<char *>(b.ptr) + b.out_offset, 0, b.out_bytes);
     if (e != cudaSuccess) {
         dev_free(c, b.ptr, b.bytes, nullptr);
@@ -385,6 +394,7 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
         std::memcpy(c->items_host, sorted.data(), ibytes);
         e = cudaMemcpyAsync(c->items_dev, c->items_host, ibytes, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return cuda_err(c, e, "plan upload");
+        c->h2d += static_cast<long long>(ibytes);
         if (c->gexec) {
             cudaGraphExecDestroy(c->gexec);
             c->gexec = nullptr;
@@ -448,6 +458,7 @@ int rcpsp_get_schedules(rcpsp_ctx *c, const int32_t *ids, int32_t count, int32_t
         cudaError_t e = cudaMemcpy(host[b].data(), static_cast<char *>(bl.ptr) + bl.out_offset, bl.out_bytes,
                                    cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_err(c, e, "result copy");
+        c->d2h += static_cast<long long>(bl.out_bytes);
     }
     size_t at = 0;
     int status = RCPSP_OK;
@@ -468,6 +479,8 @@ int rcpsp_get_schedules(rcpsp_ctx *c, const int32_t *ids, int32_t count, int32_t
             x.eval_mode = s[rcpsp::kOutMode];
             x.critical_path = in.h.cp;
             x.status = s[rcpsp::kOutStatus];
+            x.t_start_ns = (static_cast<int64_t>(s[rcpsp::kOutT0Hi]) << 32) | static_cast<uint32_t>(s[rcpsp::kOutT0Lo]);
+            x.t_end_ns = (static_cast<int64_t>(s[rcpsp::kOutT1Hi]) << 32) | static_cast<uint32_t>(s[rcpsp::kOutT1Lo]);
         }
         if (s[rcpsp::kOutStatus] != 0) status = RCPSP_E_DEVICE;
     }
@@ -492,6 +505,7 @@ int rcpsp_get_trace(rcpsp_ctx *c, int32_t id, int32_t *trace, int32_t capacity, 
     if (iters > 0) {
         e = cudaMemcpy(trace, in.trace, static_cast<size_t>(iters) * 3 * 4, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_err(c, e, "trace copy");
+        c->d2h += static_cast<long long>(iters) * 12;
     }
     *written = iters;
     return RCPSP_OK;
@@ -569,6 +583,8 @@ int rcpsp_evaluate_lists(rcpsp_ctx *c, int32_t id, const int32_t *lists, int32_t
     dev_free(c, dl, lbytes, st);
     dev_free(c, dout, obytes, st);
     if (rc != RCPSP_OK) return rc;
+    c->h2d += static_cast<long long>(lbytes);
+    c->d2h += static_cast<long long>(obytes);
     if (start) std::memcpy(start, host.data() + o_start, lbytes);
     if (work) std::memcpy(work, host.data() + o_work, static_cast<size_t>(count) * 8);
     if (makespan) std::memcpy(makespan, host.data() + o_cmax, static_cast<size_t>(count) * 4);

@@ -53,7 +53,8 @@ static_assert(sizeof(LaunchItem) == 112, "LaunchItem is 112 bytes");
 // Statistics words after W* and S* in the output block of an instance.
 enum : int {
     kOutEvalLo = 0, kOutEvalHi, kOutWorkLo, kOutWorkHi,
-    kOutIters, kOutCmax, kOutMode, kOutStatus, kOutStats
+    kOutIters, kOutCmax, kOutMode, kOutStatus,
+    kOutT0Lo, kOutT0Hi, kOutT1Lo, kOutT1Hi, kOutStats
 };
 
 RC_HD int align4(int x) { return (x + 3) & ~3; }

@@ -260,6 +260,12 @@ __device__ __forceinline__ int decode(const SInst &I, int mode, const int *W, in
                                        : decode_time<G>(I, W, u, v, area, NG, g, work, err);
 }
 
+__device__ __forceinline__ unsigned long long global_timer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long x) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -294,7 +300,7 @@ __global__ void __launch_bounds__(1024) search_kernel(const LaunchItem *__restri
                                                       int *__restrict__ queue, int move_cap) {
     extern __shared__ __align__(16) int sm[];
     __shared__ int s_item, s_nmoves, s_C, s_Cbest, s_widx, s_it, s_improved, s_err;
-    __shared__ unsigned long long s_best;
+    __shared__ unsigned long long s_best, s_t0;
     __shared__ long long s_eval, s_work;
 
     constexpr int NG = 32 / G;
@@ -335,6 +341,7 @@ __global__ void __launch_bounds__(1024) search_kernel(const LaunchItem *__restri
         for (int x = tid; x < tl; x += nthr) stl[x] = 0;                 // (0,0) = empty move
         for (int x = tid; x < (n * delta + 31) / 32; x += nthr) tc[x] = 0u;
         if (tid == 0) {
+            s_t0 = global_timer_ns();
             s_widx = 0;
             s_it = 0;
             s_eval = 0;
@@ -479,6 +486,11 @@ __global__ void __launch_bounds__(1024) search_kernel(const LaunchItem *__restri
             st[kOutIters] = s_it;
             st[kOutMode] = mode;
             st[kOutStatus] = s_err ? RCPSP_E_DEVICE : 0;
+            const unsigned long long t1 = global_timer_ns();
+            st[kOutT0Lo] = static_cast<int32_t>(s_t0 & 0xffffffffull);
+            st[kOutT0Hi] = static_cast<int32_t>(s_t0 >> 32);
+            st[kOutT1Lo] = static_cast<int32_t>(t1 & 0xffffffffull);
+            st[kOutT1Hi] = static_cast<int32_t>(t1 >> 32);
         }
         __syncthreads();
     }

@@ -21,7 +21,7 @@ ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "CYCLE", -3: "DUMMY", -4: "DEMAND_EXCE
           -5: "TOO_LARGE", -6: "CUDA", -7: "TIMEOUT", -8: "NOT_FOUND", -9: "DEVICE"}
 EXPORTS = ("rcpsp_create", "rcpsp_destroy", "rcpsp_load_instances", "rcpsp_free_instances",
            "rcpsp_tabu_search", "rcpsp_get_schedules", "rcpsp_get_trace", "rcpsp_evaluate_lists",
-           "rcpsp_prepare_instance", "rcpsp_last_error")
+           "rcpsp_prepare_instance", "rcpsp_transfer_bytes", "rcpsp_last_error")
 
 
 class RcpspError(RuntimeError):
@@ -45,7 +45,8 @@ class Params(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("evaluated", C.c_int64), ("work", C.c_int64), ("iterations", C.c_int32),
-                ("eval_mode", C.c_int32), ("critical_path", C.c_int32), ("status", C.c_int32)]
+                ("eval_mode", C.c_int32), ("critical_path", C.c_int32), ("status", C.c_int32),
+                ("t_start_ns", C.c_int64), ("t_end_ns", C.c_int64)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -82,6 +83,7 @@ def library(path: Optional[str] = None):
                                            P(C.c_int32), P(C.c_int32), P(C.c_int64), C.c_void_p]),
         "rcpsp_prepare_instance": (C.c_int, [P(Instance), P(C.c_int32), P(C.c_int32), P(C.c_int32),
                                              P(C.c_int32), C.c_char_p, C.c_int32]),
+        "rcpsp_transfer_bytes": (C.c_int, [C.c_void_p, P(C.c_int64), P(C.c_int64)]),
         "rcpsp_last_error": (C.c_char_p, [C.c_void_p]),
     }
     for name, (res, args) in sig.items():
@@ -223,9 +225,15 @@ class Solver:
             s = stats[k]
             out.append(dict(best_W=order[at:at + n], best_S=start[at:at + n], best_cmax=int(cmax[k]),
                             evaluated=int(s.evaluated), work=int(s.work), iterations=int(s.iterations),
-                            mode=int(s.eval_mode), cp=int(s.critical_path), status=int(s.status)))
+                            mode=int(s.eval_mode), cp=int(s.critical_path), status=int(s.status),
+                            t_start_ns=int(s.t_start_ns), t_end_ns=int(s.t_end_ns)))
             at += n
         return out
+
+    def transfer_bytes(self):
+        h2d, d2h = C.c_int64(0), C.c_int64(0)
+        self._check(self.lib.rcpsp_transfer_bytes(self.ctx, C.byref(h2d), C.byref(d2h)))
+        return h2d.value, d2h.value
 
     def trace(self, id_: int, iterations: int) -> np.ndarray:
         buf = np.zeros(max(1, 3 * iterations), np.int32)
