@@ -84,7 +84,7 @@ typedef struct {
     int32_t stop_at_cp;         /* 1: stop once C*_max equals the critical path  */
     int32_t group_size;         /* lanes per neighbour decode: 1,2,4,8,16,32;
                                    0 = choose automatically                      */
-    int32_t warps_per_cta;      /* 1..32; 0 = choose automatically               */
+    int32_t warps_per_cta;      /* 1..16; 0 = choose automatically               */
     int32_t record_trace;       /* 1: keep (u, v, C) of every iteration          */
     int32_t use_graph;          /* 1: capture the launch in a CUDA graph and
                                    replay it on later identical calls            */
@@ -161,8 +161,9 @@ int rcpsp_get_trace(rcpsp_ctx *ctx, int32_t id, int32_t *trace, int32_t capacity
 
 /* Decodes `count` activity lists of one loaded instance on the device with
  * the serial SGS of Alg. 7 and the given evaluator (TIME or CAPACITY; AUTO =
- * the instance's selected one).  lists [count*N] (host) must be
- * precedence-feasible.  Writes start [count*N], makespan [count] and work
+ * the instance's selected one).  lists [count*N] (host): each a permutation
+ * of 0..N-1 with 0 first, N-1 last and every arc pointing forward, else
+ * RCPSP_E_INVALID_ARG.  Writes start [count*N], makespan [count] and work
  * [count] (Alg. 5 or Alg. 4 loop steps; any may be NULL).  Synchronous. */
 int rcpsp_evaluate_lists(rcpsp_ctx *ctx, int32_t id, const int32_t *lists, int32_t count,
                          int32_t eval_mode, int32_t *start, int32_t *makespan,

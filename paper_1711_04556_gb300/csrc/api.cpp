@@ -40,6 +40,7 @@ struct Inst {
     size_t trace_bytes = 0;
     int trace_iters = -1;    // iterations recorded by the last traced search, -1 = none
     bool alive = false;
+    std::vector<int32_t> succ_off, succ;   // host copy of the arcs, to check caller lists
 };
 
 int out_words(int n) { return rcpsp::align4(2 * n + rcpsp::kOutStats); }
@@ -261,6 +262,8 @@ int rcpsp_load_instances(rcpsp_ctx *c, const rcpsp_instance *inst, int32_t count
         in.out_word = oo;
         in.out = base + rec_words + oo;
         in.alive = true;
+        in.succ_off.assign(inst[k].succ_off, inst[k].succ_off + inst[k].n + 1);
+        in.succ.assign(inst[k].succ, inst[k].succ + inst[k].succ_off[inst[k].n]);
         ro += packed[k].record.size();
         oo += out_words(in.h.n);
         out_ids[k] = static_cast<int32_t>(c->insts.size());
@@ -296,7 +299,7 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
     if (!c) return RCPSP_E_INVALID_ARG;
     if (!p || count < 0 || (count > 0 && !ids)) return set_err(c, RCPSP_E_INVALID_ARG, "bad arguments");
     if (p->iterations < 0 || p->max_swap_dist < 0 || p->tabu_len < 0 || p->tabu_len > RCPSP_MAX_TABU ||
-        p->eval_mode < 0 || p->eval_mode > 2 || p->warps_per_cta < 0 || p->warps_per_cta > 32)
+        p->eval_mode < 0 || p->eval_mode > 2 || p->warps_per_cta < 0 || p->warps_per_cta > 16)
         return set_err(c, RCPSP_E_INVALID_ARG, "bad search parameters");
     const int gs = p->group_size;
     if (gs != 0 && gs != 1 && gs != 2 && gs != 4 && gs != 8 && gs != 16 && gs != 32)
@@ -522,8 +525,25 @@ int rcpsp_evaluate_lists(rcpsp_ctx *c, int32_t id, const int32_t *lists, int32_t
     if (count == 0) return RCPSP_OK;
     const Inst &in = c->insts[id];
     const int n = in.h.n;
-    for (long long x = 0; x < static_cast<long long>(count) * n; ++x)
-        if (lists[x] < 0 || lists[x] >= n) return set_err(c, RCPSP_E_INVALID_ARG, "list entry out of range");
+    // every list must be a precedence-feasible permutation with the dummies fixed
+    {
+        std::vector<int> pos(n);
+        for (int l = 0; l < count; ++l) {
+            const int32_t *L = lists + static_cast<size_t>(l) * n;
+            std::fill(pos.begin(), pos.end(), -1);
+            for (int p = 0; p < n; ++p) {
+                if (L[p] < 0 || L[p] >= n || pos[L[p]] >= 0)
+                    return set_err(c, RCPSP_E_INVALID_ARG, "list " + std::to_string(l) + " is not a permutation");
+                pos[L[p]] = p;
+            }
+            if (L[0] != 0 || L[n - 1] != n - 1)
+                return set_err(c, RCPSP_E_INVALID_ARG, "list " + std::to_string(l) + " moves a dummy activity");
+            for (int i = 0; i < n; ++i)
+                for (int e = in.succ_off[i]; e < in.succ_off[i + 1]; ++e)
+                    if (pos[i] > pos[in.succ[e]])
+                        return set_err(c, RCPSP_E_INVALID_ARG, "list " + std::to_string(l) + " violates a precedence");
+        }
+    }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     LaunchItem it;
     std::memset(&it, 0, sizeof(it));

@@ -38,27 +38,29 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kErrHorizon = 1;     // a profile window ran past UB
 
+// G lanes of a warp that decode one neighbour.  All groups of a warp run in
+// lockstep: a loop whose trip count may differ between groups is driven by a
+// warp-wide vote and every warp-synchronous primitive names all 32 lanes, so
+// one instruction serves the 32/G neighbours of the warp at once.
 template <int G>
 struct Group {
     int lane;        // lane inside the group
     int gbase;       // first warp lane of the group
-    unsigned mask;   // warp lanes of the group
     __device__ Group() {
-        int wl = threadIdx.x & 31;
+        const int wl = threadIdx.x & 31;
         lane = wl & (G - 1);
         gbase = wl & ~(G - 1);
-        mask = G == 32 ? kFull : (((1u << G) - 1u) << gbase);
     }
-    __device__ unsigned ballot(bool p) const {
-        unsigned b = __ballot_sync(mask, p);
-        return G == 32 ? b : (b >> gbase) & ((1u << G) - 1u);
+    // the group's G bits of a warp-wide ballot
+    __device__ unsigned bits(unsigned warp_ballot) const {
+        return G == 32 ? warp_ballot : (warp_ballot >> gbase) & ((1u << G) - 1u);
     }
+    // maximum over the group; every lane of the warp calls it
     __device__ int max(int x) const {
 #pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) x = ::max(x, __shfl_xor_sync(mask, x, o, G));
+        for (int o = G / 2; o > 0; o >>= 1) x = ::max(x, __shfl_xor_sync(kFull, x, o));
         return x;
     }
-    __device__ void sync() const { __syncwarp(mask); }
 };
 
 // Shared-memory view of one instance.
@@ -108,130 +110,163 @@ __device__ void stage_instance(int *sm, const int32_t *record, int words) {
 
 // ---------------------------------------------------------------------------
 // Serial SGS (Alg. 7) of the list W with positions u and v swapped
-// (u == v leaves W unchanged), decoded by one group.  `area` is the group's
-// interleaved scratch: profile element e at area[e*NG], finish time of
-// activity i at area[(prof_words + i)*NG].  Returns C_max; `work` gets the
-// Alg. 5 (time-indexed) or Alg. 4 (capacity-indexed) loop steps.
+// (u == v leaves W unchanged), decoded by one group in lockstep with the
+// other groups of its warp.  A group with active == false follows the loops
+// without reading or writing its scratch.  `area` is the group's interleaved
+// scratch: element e at area[e*NG]; the profile (or capacity state) comes
+// first, then the finish time of every activity.  Returns C_max; `work` gets
+// the Alg. 5 (time-indexed) or Alg. 4 (capacity-indexed) loop steps.
 // ---------------------------------------------------------------------------
 template <int G>
-__device__ int decode_time(const SInst &I, const int *W, int u, int v, int *area, int NG,
-                           const Group<G> &g, long long &work, int &err) {
-    const int n = I.n, ub = I.ub, wps = I.wps;
+__device__ __forceinline__ int activity_at(const int *W, int p, int u, int v) {
+    return p == u ? W[v] : (p == v ? W[u] : W[p]);
+}
+
+// precedence earliest start (Alg. 7): max over predecessors j of s_j + d_j
+template <int G>
+__device__ __forceinline__ int precedence_start(const SInst &I, int i, const int *fin, int NG,
+                                                const Group<G> &g) {
+    const int e0 = I.poff[i], np = I.poff[i + 1] - e0;
+    const int npmax = __reduce_max_sync(kFull, np);
+    int es = 0;
+    for (int b = g.lane; b < npmax; b += G)
+        if (b < np) es = ::max(es, fin[I.plist[e0 + b] * NG]);
+    return g.max(es);
+}
+
+// Time-indexed decode, WPS = 32-bit words per time step of the packed profile.
+template <int G, int WPS>
+__device__ int decode_time(const SInst &I, const int *W, int u, int v, bool active, int *area, int NG,
+                           const Group<G> &g, int &work, int &err) {
+    constexpr int U = G >= 32 ? 1 : (G >= 16 ? 2 : 4);   // steps a lane tests per round
+    constexpr int R = G * U;                               // steps a group tests per round (<= 32)
+    const int n = I.n, ub = I.ub;
+    const int ubs = ub > 0 ? ub : 1;              // stride of one resource-word plane
     uint32_t *prof = reinterpret_cast<uint32_t *>(area);
-    int *fin = area + wps * (ub > 0 ? ub : 1) * NG;
-    // every time step starts with R_k free units of every resource (Sec. 5.2.1)
-    for (int w = 0; w < wps; ++w) {
-        const uint32_t cw = I.capw[w];
-        for (int t = g.lane; t < ub; t += G) prof[(w * ub + t) * NG] = cw;
-    }
-    g.sync();
+    int *fin = area + WPS * ubs * NG;
+    const uint32_t hi = I.hi;
+    uint32_t capw[WPS];
+#pragma unroll
+    for (int w = 0; w < WPS; ++w) capw[w] = I.capw[w];
+    // Every step starts with R_k free units (Sec. 5.2.1).  Steps at or after
+    // the frontier F have not been touched by this decode, so they are not
+    // stored: they are written the first time an activity covers them.
+    int F = 0;
     int cmax = 0;
     for (int p = 0; p < n; ++p) {
-        int i = W[p];
-        if (p == u) i = W[v];
-        else if (p == v) i = W[u];
-        // precedence earliest start (Alg. 7): max over predecessors of s_j + d_j
-        int es = 0;
-        for (int e = I.poff[i] + g.lane; e < I.poff[i + 1]; e += G) es = ::max(es, fin[I.plist[e] * NG]);
-        es = g.max(es);
+        const int i = activity_at<G>(W, p, u, v);
+        const int es = precedence_start<G>(I, i, fin, NG, g);
         const int d = I.dur[i];
-        int s = es;
-        if (d > 0) {
-            uint32_t rq[4];
+        uint32_t rq[WPS];
 #pragma unroll
-            for (int w = 0; w < 4; ++w) rq[w] = w < wps ? I.reqw[i * wps + w] : 0u;
-            // Alg. 5: first window of d consecutive steps that fit, from es on.
-            // The G lanes test G steps at once; a step that does not fit
-            // moves the window start past it.
-            for (;;) {
-                bool found = true;
-                for (int off = 0; off < d; off += G) {
-                    const int t = s + off + g.lane;
-                    bool fit = true;
-                    if (off + g.lane < d) {
-                        if (t < ub) {
+        for (int w = 0; w < WPS; ++w) rq[w] = I.reqw[i * WPS + w];
+        // Alg. 5: the first window [s, s+d), s >= es, whose steps all fit.
+        // A round tests R window offsets k..k+R-1 (offset k + lane + G*j in
+        // lane `lane`); a step that does not fit moves s past it; steps at or
+        // after F always fit.
+        int s = es, k = 0;
+        bool done = !active || d == 0;
+        while (__any_sync(kFull, !done)) {
+            if (!done && s + k >= F) done = true;
+            bool fit[U];
 #pragma unroll
-                            for (int w = 0; w < 4; ++w)
-                                if (w < wps) {
-                                    const uint32_t x = prof[(w * ub + t) * NG];
-                                    fit = fit && (((x | I.hi) - rq[w]) & I.hi) == I.hi;
-                                }
-                        } else {
-                            err |= kErrHorizon;
-                        }
-                    }
-                    const unsigned bad = g.ballot(!fit);
-                    if (bad) {
-                        s += off + (31 - __clz(bad)) + 1;
-                        found = false;
-                        break;
+            for (int j = 0; j < U; ++j) {
+                const int o = k + g.lane + G * j;
+                const int t = s + o;
+                fit[j] = true;
+                if (!done && o < d && t < F && t < ub) {
+#pragma unroll
+                    for (int w = 0; w < WPS; ++w) {
+                        const uint32_t x = prof[(w * ubs + t) * NG];
+                        fit[j] = fit[j] && (((x | hi) - rq[w]) & hi) == hi;
                     }
                 }
-                if (found) break;
             }
-            // Alg. 6: take r_{i,k} units over [s, s+d); fields never borrow
-            for (int t = s + g.lane; t < s + d; t += G) {
-                if (t < ub) {
+            unsigned bad = 0;
 #pragma unroll
-                    for (int w = 0; w < 4; ++w)
-                        if (w < wps) prof[(w * ub + t) * NG] -= rq[w];
+            for (int j = 0; j < U; ++j) bad |= g.bits(__ballot_sync(kFull, !fit[j])) << (G * j);
+            if (!done) {
+                if (bad) {
+                    s += k + (31 - __clz(bad)) + 1;
+                    k = 0;
+                } else {
+                    k += R;
+                    if (k >= d) done = true;
                 }
             }
         }
-        if (g.lane == 0) fin[i * NG] = s + d;
-        work += s + d - es;
-        cmax = ::max(cmax, s + d);
-        g.sync();
+        // Alg. 6: take r_{i,k} units over [s, s+d) (fields never borrow);
+        // untouched steps in [F, s+d) first get R_k.
+        if (active && d > 0) {
+            const int fend = s + d;
+#pragma unroll 2
+            for (int t = ::min(s, F) + g.lane; t < fend; t += G) {
+                if (t >= ub) {
+                    err |= kErrHorizon;
+                    break;
+                }
+#pragma unroll
+                for (int w = 0; w < WPS; ++w) {
+                    uint32_t *x = prof + (w * ubs + t) * NG;
+                    if (t < s) *x = capw[w];                       // gap between old frontier and s
+                    else *x = (t >= F ? capw[w] : *x) - rq[w];
+                }
+            }
+            F = ::max(F, fend);
+        }
+        if (active) {
+            if (g.lane == 0) fin[i * NG] = s + d;
+            work += s + d - es;
+            cmax = ::max(cmax, s + d);
+        }
+        __syncwarp();
     }
     return cmax;
 }
 
 template <int G>
-__device__ int decode_capacity(const SInst &I, const int *W, int u, int v, int *area, int NG,
-                               const Group<G> &g, long long &work, int &err) {
+__device__ int decode_capacity(const SInst &I, const int *W, int u, int v, bool active, int *area, int NG,
+                               const Group<G> &g, int &work, int &err) {
     const int n = I.n, m = I.m;
     int *cst = area;                                   // c_k, concatenated
     int *fin = area + I.sum_cap * NG;
-    for (int j = g.lane; j < I.sum_cap; j += G) cst[j * NG] = 0;   // Sec. 5.1.1
-    g.sync();
+    if (active)
+        for (int j = g.lane; j < I.sum_cap; j += G) cst[j * NG] = 0;   // Sec. 5.1.1
+    __syncwarp();
     int cmax = 0;
     for (int p = 0; p < n; ++p) {
-        int i = W[p];
-        if (p == u) i = W[v];
-        else if (p == v) i = W[u];
-        int es = 0;
-        for (int e = I.poff[i] + g.lane; e < I.poff[i + 1]; e += G) es = ::max(es, fin[I.plist[e] * NG]);
-        es = g.max(es);
+        const int i = activity_at<G>(W, p, u, v);
+        const int es = precedence_start<G>(I, i, fin, NG, g);
         // Eq. 7: es_res = max over used resources of c_k[R_k - r_{i,k}]
         int er = 0;
-        for (int k = g.lane; k < m; k += G) {
-            const int r = I.reqk[i * m + k];
-            if (r > 0) er = ::max(er, cst[(I.cbase[k] + I.cap[k] - r) * NG]);
-        }
+        if (active)
+            for (int k = g.lane; k < m; k += G) {
+                const int r = I.reqk[i * m + k];
+                if (r > 0) er = ::max(er, cst[(I.cbase[k] + I.cap[k] - r) * NG]);
+            }
         er = g.max(er);
         const int s = ::max(es, er);
         const int d = I.dur[i];
-        if (d > 0) {
-            for (int k = 0; k < m; ++k) {
-                const int r = I.reqk[i * m + k];
-                if (r == 0) continue;
+        for (int k = 0; k < m; ++k) {
+            const int r = I.reqk[i * m + k];
+            const bool upd = active && d > 0 && r > 0;
+            int last = -1;
+            if (__any_sync(kFull, upd)) {
                 // Alg. 4 as a per-index closed form of its result:
                 //   j <  r : c'[j] = max(c[j], s+d)
                 //   j >= r : c'[j] = c[j-r] <= s ? c[j] : max(c[j], min(c[j-r], s+d))
-                // Chunks are processed from the top so that c[j-r] is still
-                // the old value when it is read.
+                // Chunks go from the top so that c[j-r] is still old when read.
                 const int R = I.cap[k];
                 int *ck = cst + I.cbase[k] * NG;
-                int last = -1;
                 for (int J = ((R - 1) / G) * G; J >= 0; J -= G) {
                     const int j = J + g.lane;
                     int old = 0, prev = 0;
-                    if (j < R) {
+                    if (upd && j < R) {
                         old = ck[j * NG];
                         if (j >= r) prev = ck[(j - r) * NG];
                     }
-                    g.sync();
-                    if (j < R) {
+                    __syncwarp();
+                    if (upd && j < R) {
                         const int nv = j < r ? ::max(old, s + d)
                                              : (prev <= s ? old : ::max(old, ::min(prev, s + d)));
                         if (nv != old) {
@@ -239,25 +274,32 @@ __device__ int decode_capacity(const SInst &I, const int *W, int u, int v, int *
                             last = ::max(last, j);
                         }
                     }
-                    g.sync();
+                    __syncwarp();
                 }
-                // Alg. 4 stops right after its last change
-                work += g.max(last) + 1;
             }
+            last = g.max(last);
+            if (upd) work += last + 1;                 // Alg. 4 stops after its last change
         }
-        if (g.lane == 0) fin[i * NG] = s + d;
-        cmax = ::max(cmax, s + d);
-        g.sync();
+        if (active) {
+            if (g.lane == 0) fin[i * NG] = s + d;
+            cmax = ::max(cmax, s + d);
+        }
+        __syncwarp();
     }
     (void)err;
     return cmax;
 }
 
 template <int G>
-__device__ __forceinline__ int decode(const SInst &I, int mode, const int *W, int u, int v, int *area,
-                                      int NG, const Group<G> &g, long long &work, int &err) {
-    return mode == RCPSP_EVAL_CAPACITY ? decode_capacity<G>(I, W, u, v, area, NG, g, work, err)
-                                       : decode_time<G>(I, W, u, v, area, NG, g, work, err);
+__device__ __forceinline__ int decode(const SInst &I, int mode, const int *W, int u, int v, bool active,
+                                      int *area, int NG, const Group<G> &g, long long &work, int &err) {
+    int wk = 0, c;
+    if (mode == RCPSP_EVAL_CAPACITY) c = decode_capacity<G>(I, W, u, v, active, area, NG, g, wk, err);
+    else if (I.wps == 1) c = decode_time<G, 1>(I, W, u, v, active, area, NG, g, wk, err);
+    else if (I.wps == 2) c = decode_time<G, 2>(I, W, u, v, active, area, NG, g, wk, err);
+    else c = decode_time<G, 4>(I, W, u, v, active, area, NG, g, wk, err);
+    work += wk;
+    return c;
 }
 
 __device__ __forceinline__ unsigned long long global_timer_ns() {
@@ -296,7 +338,7 @@ __device__ __forceinline__ void tc_put(unsigned *tc, int u, int v, int delta, bo
 // Persistent search kernel.
 // ---------------------------------------------------------------------------
 template <int G>
-__global__ void __launch_bounds__(1024) search_kernel(const LaunchItem *__restrict__ items, int count,
+__global__ void __launch_bounds__(512) search_kernel(const LaunchItem *__restrict__ items, int count,
                                                       int *__restrict__ queue, int move_cap) {
     extern __shared__ __align__(16) int sm[];
     __shared__ int s_item, s_nmoves, s_C, s_Cbest, s_widx, s_it, s_improved, s_err;
@@ -307,7 +349,7 @@ __global__ void __launch_bounds__(1024) search_kernel(const LaunchItem *__restri
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int warp = tid >> 5, wl = tid & 31;
     const int ngroups = (nthr >> 5) * NG;
-    const int gid = warp * NG + wl / G;
+    const int gw = wl / G;                     // group inside the warp
     const Group<G> g;
 
     for (;;) {
@@ -350,10 +392,10 @@ __global__ void __launch_bounds__(1024) search_kernel(const LaunchItem *__restri
         }
         __syncthreads();
         int err = 0;
-        if (gid == 0) {
+        if (warp == 0) {
             long long w0 = 0;
-            const int c0 = decode<G>(I, mode, W, 0, 0, area, NG, g, w0, err);
-            if (g.lane == 0) {
+            const int c0 = decode<G>(I, mode, W, 0, 0, gw == 0, area, NG, g, w0, err);
+            if (gw == 0 && g.lane == 0) {
                 s_C = c0;
                 s_Cbest = c0;
             }
@@ -403,11 +445,14 @@ __global__ void __launch_bounds__(1024) search_kernel(const LaunchItem *__restri
                 __syncthreads();
                 const int nm = s_nmoves;
                 // 3. decode the neighbours
-                for (int q = gid; q < nm; q += ngroups) {
-                    const int code = moves[q];
+                // (the groups of a warp take consecutive moves and decode them in lockstep)
+                for (int q0 = warp * NG; q0 < nm; q0 += ngroups) {
+                    const int q = q0 + gw;
+                    const bool act = q < nm;
+                    const int code = act ? moves[q] : 0;
                     const int u = code & 0xffff, v = code >> 16;
-                    const int c = decode<G>(I, mode, W, u, v, area, NG, g, my_work, err);
-                    if (!tc_get(tc, u, v, delta) || c < cbest) {
+                    const int c = decode<G>(I, mode, W, u, v, act, area, NG, g, my_work, err);
+                    if (act && (!tc_get(tc, u, v, delta) || c < cbest)) {
                         const unsigned long long key =
                             (static_cast<unsigned long long>(c) << 32) | static_cast<unsigned>(code & 0xffff) << 16 |
                             static_cast<unsigned>(v);
@@ -464,15 +509,17 @@ __global__ void __launch_bounds__(1024) search_kernel(const LaunchItem *__restri
         __syncthreads();
         // outputs: W*, its schedule S*, statistics
         int32_t *out = it.out;
-        if (gid == 0) {
+        if (warp == 0) {
             long long w1 = 0;
             int e1 = 0;
-            const int cb = decode<G>(I, mode, Wbest, 0, 0, area, NG, g, w1, e1);
-            const int *fin = area + pw * NG;
-            for (int i = g.lane; i < n; i += G) out[n + i] = fin[i * NG] - I.dur[i];
-            if (g.lane == 0) {
-                out[2 * n + kOutCmax] = cb;
-                if (e1 || cb != s_Cbest) atomicOr(&s_err, 2);
+            const int cb = decode<G>(I, mode, Wbest, 0, 0, gw == 0, area, NG, g, w1, e1);
+            if (gw == 0) {
+                const int *fin = area + pw * NG;
+                for (int i = g.lane; i < n; i += G) out[n + i] = fin[i * NG] - I.dur[i];
+                if (g.lane == 0) {
+                    out[2 * n + kOutCmax] = cb;
+                    if (e1 || cb != s_Cbest) atomicOr(&s_err, 2);
+                }
             }
         }
         for (int p = tid; p < n; p += nthr) out[p] = Wbest[p];
@@ -500,7 +547,7 @@ __global__ void __launch_bounds__(1024) search_kernel(const LaunchItem *__restri
 // Decoding of caller-given lists (rcpsp_evaluate_lists).
 // ---------------------------------------------------------------------------
 template <int G>
-__global__ void __launch_bounds__(1024) evaluate_kernel(LaunchItem item, const int32_t *__restrict__ lists,
+__global__ void __launch_bounds__(512) evaluate_kernel(LaunchItem item, const int32_t *__restrict__ lists,
                                                         int count, int32_t *__restrict__ start,
                                                         int32_t *__restrict__ cmax_out,
                                                         long long *__restrict__ work_out,
@@ -509,7 +556,8 @@ __global__ void __launch_bounds__(1024) evaluate_kernel(LaunchItem item, const i
     constexpr int NG = 32 / G;
     const int tid = threadIdx.x, warp = tid >> 5, wl = tid & 31;
     const int ngroups = (blockDim.x >> 5) * NG;
-    const int gid = warp * NG + wl / G;
+    const int gw = wl / G;
+    const int gid = warp * NG + gw;
     const Group<G> g;
     const InstHeader &h = item.h;
     const int n = h.n, mode = item.mode;
@@ -522,18 +570,23 @@ __global__ void __launch_bounds__(1024) evaluate_kernel(LaunchItem item, const i
     int *myW = sm + S.moves + gid * align4(n);
     int *area = sm + S.groups + warp * NG * S.group_words + wl / G;
     int err = 0;
-    for (int l = blockIdx.x * ngroups + gid; l < count; l += gridDim.x * ngroups) {
-        for (int p = g.lane; p < n; p += G) myW[p] = lists[static_cast<long long>(l) * n + p];
-        g.sync();
+    for (int l0 = (blockIdx.x * (blockDim.x >> 5) + warp) * NG; l0 < count; l0 += gridDim.x * ngroups) {
+        const int l = l0 + gw;
+        const bool act = l < count;
+        // an idle group follows the lockstep on the identity list, reading only
+        for (int p = g.lane; p < n; p += G) myW[p] = act ? lists[static_cast<long long>(l) * n + p] : p;
+        __syncwarp();
         long long wk = 0;
-        const int c = decode<G>(I, mode, myW, 0, 0, area, NG, g, wk, err);
-        const int *fin = area + pw * NG;
-        for (int i = g.lane; i < n; i += G) start[static_cast<long long>(l) * n + i] = fin[i * NG] - I.dur[i];
-        if (g.lane == 0) {
-            cmax_out[l] = c;
-            work_out[l] = wk;
+        const int c = decode<G>(I, mode, myW, 0, 0, act, area, NG, g, wk, err);
+        if (act) {
+            const int *fin = area + pw * NG;
+            for (int i = g.lane; i < n; i += G) start[static_cast<long long>(l) * n + i] = fin[i * NG] - I.dur[i];
+            if (g.lane == 0) {
+                cmax_out[l] = c;
+                work_out[l] = wk;
+            }
         }
-        g.sync();
+        __syncwarp();
     }
     if (err) atomicOr(err_out, err);
 }
