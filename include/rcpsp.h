@@ -143,6 +143,26 @@ int rcpsp_free_instances(rcpsp_ctx *ctx, const int32_t *ids, int32_t count);
 int rcpsp_tabu_search(rcpsp_ctx *ctx, const int32_t *ids, int32_t count,
                       const rcpsp_params *params, void *cuda_stream);
 
+/* The same search as rcpsp_tabu_search, for callers that cannot allocate
+ * device memory when they search: for example a serving process whose
+ * device memory is owned by another allocator with a fixed budget, or a
+ * host thread that must not block on the implicit device synchronisation
+ * of cudaMalloc / cudaFree.  This call allocates nothing: the launch plan
+ * and the work-queue counter live in a fixed 1 MiB array in the library's
+ * device image, which every GPU that loads the library keeps until the
+ * process exits.  Instances must already be loaded (rcpsp_load_instances
+ * is where device memory is taken); results are read as usual with
+ * rcpsp_get_schedules.  Limits: at most as many instances per call as the
+ * array holds (9360; more gives RCPSP_E_TOO_LARGE), no trace and no graph
+ * capture (record_trace or use_graph = 1 gives RCPSP_E_INVALID_ARG).  The
+ * first call on a device also looks up the array's device address with
+ * that device current; make that first call before any stream capture.
+ * Every call shares the one array and resets its counter: calls whose
+ * searches overlap on the GPU (several contexts, or several streams, on
+ * one device) race.  The paper has no counterpart of this call. */
+int rcpsp_tabu_search_noalloc(rcpsp_ctx *ctx, const int32_t *ids, int32_t count,
+                              const rcpsp_params *params, void *cuda_stream);
+
 /* Waits for the last search of the context and copies results to host
  * buffers: order = best list W* and start = its start times S (both [sum of N
  * over the ids], concatenated in id order), makespan = C*_max [count].  Any

@@ -67,6 +67,7 @@ struct rcpsp_ctx {
     int g_shape[5] = {0, 0, 0, 0, 0};
     cudaStream_t g_stream = nullptr;
     long long h2d = 0, d2h = 0;   // bytes copied by the context
+    std::vector<LaunchItem> noalloc_plan;   // host copy of the last no-allocation plan
 };
 
 namespace {
@@ -431,6 +432,91 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
             e = rcpsp::launch_search(G, c->items_dev, count, c->queue_dev, move_cap, blocks, threads, smem, st);
         if (e != cudaSuccess) return cuda_err(c, e, "search launch");
     }
+    e = cudaEventRecord(c->done, st);
+    if (e != cudaSuccess) return cuda_err(c, e, "event record");
+    c->pending = true;
+    return RCPSP_OK;
+}
+
+int rcpsp_tabu_search_noalloc(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcpsp_params *p,
+                              void *stream) {
+    if (!c) return RCPSP_E_INVALID_ARG;
+    if (!p || count < 0 || (count > 0 && !ids)) return set_err(c, RCPSP_E_INVALID_ARG, "bad arguments");
+    if (p->iterations < 0 || p->max_swap_dist < 0 || p->tabu_len < 0 || p->tabu_len > RCPSP_MAX_TABU ||
+        p->eval_mode < 0 || p->eval_mode > 2 || p->warps_per_cta < 0 || p->warps_per_cta > 16)
+        return set_err(c, RCPSP_E_INVALID_ARG, "bad search parameters");
+    const int gs = p->group_size;
+    if (gs != 0 && gs != 1 && gs != 2 && gs != 4 && gs != 8 && gs != 16 && gs != 32)
+        return set_err(c, RCPSP_E_INVALID_ARG, "group_size must be 0, 1, 2, 4, 8, 16 or 32");
+    if (p->record_trace || p->use_graph)
+        return set_err(c, RCPSP_E_INVALID_ARG, "the no-allocation search keeps no trace and captures no graph");
+    if (count > rcpsp::noalloc_max_items())
+        return set_err(c, RCPSP_E_TOO_LARGE, "the no-allocation search takes at most " +
+                                                 std::to_string(rcpsp::noalloc_max_items()) + " instances per call");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaSetDevice(c->device);
+    int rc = wait_done(c);
+    if (rc != RCPSP_OK) return rc;
+    if (count == 0) return RCPSP_OK;
+    std::vector<LaunchItem> items(count);
+    std::vector<double> cost(count);
+    for (int k = 0; k < count; ++k) {
+        const int id = ids[k];
+        if (id < 0 || id >= static_cast<int>(c->insts.size()) || !c->insts[id].alive)
+            return set_err(c, RCPSP_E_NOT_FOUND, "unknown instance id");
+        Inst &in = c->insts[id];
+        LaunchItem &it = items[k];
+        std::memset(&it, 0, sizeof(it));
+        it.h = in.h;
+        it.record = in.record;
+        it.out = in.out;
+        it.mode = p->eval_mode == RCPSP_EVAL_AUTO ? in.h.sel_mode : p->eval_mode;
+        int dd, tl;
+        rcpsp::default_search_params(in.h.n, &dd, &tl);
+        it.delta = p->max_swap_dist ? p->max_swap_dist : dd;
+        it.tabu_len = p->tabu_len ? p->tabu_len : tl;
+        it.iterations = p->iterations;
+        it.stop_at_cp = p->stop_at_cp ? 1 : 0;
+        in.trace_iters = -1;
+        cost[k] = rcpsp::estimate_cost(in.h, it.mode, it.iterations, it.delta);
+    }
+    std::vector<int> order(count);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    c->noalloc_plan.resize(count);
+    for (int k = 0; k < count; ++k) c->noalloc_plan[k] = items[order[k]];
+    int G = gs, warps = p->warps_per_cta;
+    int dG, dW;
+    default_shape(c->noalloc_plan, &dG, &dW);
+    if (!G) G = dG;
+    if (!warps) warps = std::max(dW, (G + 31) / 32);
+    const int move_cap = rcpsp::kDefaultMoveCap;
+    const size_t smem_limit = c->prop.sharedMemPerBlockOptin > 1024 ? c->prop.sharedMemPerBlockOptin - 1024 : 0;
+    size_t smem = smem_bytes(c->noalloc_plan, warps * (32 / G), move_cap);
+    while (smem > smem_limit && p->warps_per_cta == 0 && warps > 1) {
+        --warps;
+        smem = smem_bytes(c->noalloc_plan, warps * (32 / G), move_cap);
+    }
+    if (smem > smem_limit)
+        return set_err(c, RCPSP_E_TOO_LARGE, "instance state does not fit in shared memory at this launch shape");
+    const int threads = warps * 32;
+    int *queue = nullptr;
+    LaunchItem *plan = nullptr;
+    cudaError_t e = rcpsp::noalloc_scratch(c->device, &queue, &plan);
+    if (e != cudaSuccess) return cuda_err(c, e, "scratch address");
+    e = rcpsp::prepare_search(G, smem);
+    if (e != cudaSuccess) return cuda_err(c, e, "kernel attributes");
+    int per_sm = 0;
+    e = rcpsp::search_occupancy(G, threads, smem, &per_sm);
+    if (e != cudaSuccess) return cuda_err(c, e, "occupancy");
+    if (per_sm < 1) return set_err(c, RCPSP_E_TOO_LARGE, "launch shape does not fit on an SM");
+    const int blocks = std::max(1, std::min(count, per_sm * c->prop.multiProcessorCount));
+    const size_t ibytes = sizeof(LaunchItem) * count;
+    e = cudaMemcpyAsync(plan, c->noalloc_plan.data(), ibytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(queue, 0, sizeof(int), st);      // the counter starts at 0
+    if (e == cudaSuccess) e = rcpsp::launch_search(G, plan, count, queue, move_cap, blocks, threads, smem, st);
+    if (e != cudaSuccess) return cuda_err(c, e, "no-allocation search launch");
+    c->h2d += static_cast<long long>(ibytes);
     e = cudaEventRecord(c->done, st);
     if (e != cudaSuccess) return cuda_err(c, e, "event record");
     c->pending = true;

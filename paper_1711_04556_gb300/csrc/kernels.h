@@ -17,4 +17,9 @@ cudaError_t launch_evaluate(int group_size, const LaunchItem &item, const int32_
                             int32_t *start, int32_t *cmax, long long *work, int *err, int blocks, int threads,
                             size_t smem, cudaStream_t st);
 
+// Fixed scratch of the no-allocation search (noalloc_scratch.cu): largest
+// plan it holds, and its device address on `device` (queue counter, plan).
+int noalloc_max_items();
+cudaError_t noalloc_scratch(int device, int **queue, LaunchItem **plan);
+
 }  // namespace rcpsp
