@@ -112,50 +112,61 @@ __device__ void stage_instance(int *sm, const int32_t *record, int words) {
 // Serial SGS (Alg. 7) of the list W with positions u and v swapped
 // (u == v leaves W unchanged), decoded by one group in lockstep with the
 // other groups of its warp.  A group with active == false follows the loops
-// without reading or writing its scratch.  `area` is the group's interleaved
-// scratch: element e at area[e*NG]; the profile (or capacity state) comes
-// first, then the finish time of every activity.  Returns C_max; `work` gets
-// the Alg. 5 (time-indexed) or Alg. 4 (capacity-indexed) loop steps.
+// without writing its scratch.  `area` is the group's interleaved scratch:
+// element e at area[e*NG]; the profile (or capacity state) comes first, then
+// es[i], the precedence earliest start of every activity.  Instead of
+// reading the finish times of i's predecessors when i is placed (Alg. 7,
+// lines 3-6), every placed activity raises es[] of its successors, so the
+// placement of i starts from one broadcast load; the value is the same
+// maximum.  Returns C_max; `work` gets the Alg. 5 (time-indexed) or Alg. 4
+// (capacity-indexed) loop steps; S_out (may be null) gets start times.
 // ---------------------------------------------------------------------------
 template <int G>
 __device__ __forceinline__ int activity_at(const int *W, int p, int u, int v) {
     return p == u ? W[v] : (p == v ? W[u] : W[p]);
 }
 
-// precedence earliest start (Alg. 7): max over predecessors j of s_j + d_j
+// es of every successor of i := max(es, f)
 template <int G>
-__device__ __forceinline__ int precedence_start(const SInst &I, int i, const int *fin, int NG,
-                                                const Group<G> &g) {
-    const int e0 = I.poff[i], np = I.poff[i + 1] - e0;
-    const int npmax = __reduce_max_sync(kFull, np);
-    int es = 0;
-    for (int b = g.lane; b < npmax; b += G)
-        if (b < np) es = ::max(es, fin[I.plist[e0 + b] * NG]);
-    return g.max(es);
+__device__ __forceinline__ void push_finish(const SInst &I, int i, int f, int *es, int NG, const Group<G> &g) {
+    const int e0 = I.soff[i], ns = I.soff[i + 1] - e0;
+    for (int b = g.lane; b < ns; b += G) {
+        int *x = es + I.slist[e0 + b] * NG;
+        *x = ::max(*x, f);
+    }
+}
+
+template <int G>
+__device__ __forceinline__ void clear_es(int *es, int n, int NG, bool active, const Group<G> &g) {
+    if (active)
+        for (int x = g.lane; x < n; x += G) es[x * NG] = 0;
+    __syncwarp();
 }
 
 // Time-indexed decode, WPS = 32-bit words per time step of the packed profile.
 template <int G, int WPS>
 __device__ int decode_time(const SInst &I, const int *W, int u, int v, bool active, int *area, int NG,
-                           const Group<G> &g, int &work, int &err) {
+                           const Group<G> &g, int &work, int &err, int *S_out) {
     constexpr int U = G >= 32 ? 1 : (G >= 16 ? 2 : 4);   // steps a lane tests per round
     constexpr int R = G * U;                               // steps a group tests per round (<= 32)
     const int n = I.n, ub = I.ub;
     const int ubs = ub > 0 ? ub : 1;              // stride of one resource-word plane
     uint32_t *prof = reinterpret_cast<uint32_t *>(area);
-    int *fin = area + WPS * ubs * NG;
+    int *esa = area + WPS * ubs * NG;
     const uint32_t hi = I.hi;
     uint32_t capw[WPS];
 #pragma unroll
     for (int w = 0; w < WPS; ++w) capw[w] = I.capw[w];
+    clear_es<G>(esa, n, NG, active, g);
     // Every step starts with R_k free units (Sec. 5.2.1).  Steps at or after
     // the frontier F have not been touched by this decode, so they are not
     // stored: they are written the first time an activity covers them.
     int F = 0;
     int cmax = 0;
+    int i = activity_at<G>(W, 0, u, v);
     for (int p = 0; p < n; ++p) {
-        const int i = activity_at<G>(W, p, u, v);
-        const int es = precedence_start<G>(I, i, fin, NG, g);
+        const int inext = activity_at<G>(W, p + 1 < n ? p + 1 : p, u, v);
+        const int es = esa[i * NG];
         const int d = I.dur[i];
         uint32_t rq[WPS];
 #pragma unroll
@@ -195,48 +206,51 @@ __device__ int decode_time(const SInst &I, const int *W, int u, int v, bool acti
                 }
             }
         }
-        // Alg. 6: take r_{i,k} units over [s, s+d) (fields never borrow);
-        // untouched steps in [F, s+d) first get R_k.
-        if (active && d > 0) {
-            const int fend = s + d;
-#pragma unroll 2
-            for (int t = ::min(s, F) + g.lane; t < fend; t += G) {
-                if (t >= ub) {
-                    err |= kErrHorizon;
-                    break;
-                }
-#pragma unroll
-                for (int w = 0; w < WPS; ++w) {
-                    uint32_t *x = prof + (w * ubs + t) * NG;
-                    if (t < s) *x = capw[w];                       // gap between old frontier and s
-                    else *x = (t >= F ? capw[w] : *x) - rq[w];
-                }
-            }
-            F = ::max(F, fend);
-        }
+        const int f = s + d;
         if (active) {
-            if (g.lane == 0) fin[i * NG] = s + d;
-            work += s + d - es;
-            cmax = ::max(cmax, s + d);
+            // Alg. 6: take r_{i,k} units over [s, s+d) (fields never borrow);
+            // untouched steps in [F, s+d) first get R_k.
+            if (d > 0) {
+#pragma unroll 2
+                for (int t = ::min(s, F) + g.lane; t < f; t += G) {
+                    if (t >= ub) {
+                        err |= kErrHorizon;
+                        break;
+                    }
+#pragma unroll
+                    for (int w = 0; w < WPS; ++w) {
+                        uint32_t *x = prof + (w * ubs + t) * NG;
+                        if (t < s) *x = capw[w];                       // gap between old frontier and s
+                        else *x = (t >= F ? capw[w] : *x) - rq[w];
+                    }
+                }
+                F = ::max(F, f);
+            }
+            push_finish<G>(I, i, f, esa, NG, g);
+            if (S_out && g.lane == 0) S_out[i] = s;
+            work += f - es;
+            cmax = ::max(cmax, f);
         }
         __syncwarp();
+        i = inext;
     }
     return cmax;
 }
 
 template <int G>
 __device__ int decode_capacity(const SInst &I, const int *W, int u, int v, bool active, int *area, int NG,
-                               const Group<G> &g, int &work, int &err) {
+                               const Group<G> &g, int &work, int &err, int *S_out) {
     const int n = I.n, m = I.m;
     int *cst = area;                                   // c_k, concatenated
-    int *fin = area + I.sum_cap * NG;
+    int *esa = area + I.sum_cap * NG;
     if (active)
         for (int j = g.lane; j < I.sum_cap; j += G) cst[j * NG] = 0;   // Sec. 5.1.1
-    __syncwarp();
+    clear_es<G>(esa, n, NG, active, g);
     int cmax = 0;
+    int i = activity_at<G>(W, 0, u, v);
     for (int p = 0; p < n; ++p) {
-        const int i = activity_at<G>(W, p, u, v);
-        const int es = precedence_start<G>(I, i, fin, NG, g);
+        const int inext = activity_at<G>(W, p + 1 < n ? p + 1 : p, u, v);
+        const int es = esa[i * NG];
         // Eq. 7: es_res = max over used resources of c_k[R_k - r_{i,k}]
         int er = 0;
         if (active)
@@ -281,10 +295,12 @@ __device__ int decode_capacity(const SInst &I, const int *W, int u, int v, bool 
             if (upd) work += last + 1;                 // Alg. 4 stops after its last change
         }
         if (active) {
-            if (g.lane == 0) fin[i * NG] = s + d;
+            push_finish<G>(I, i, s + d, esa, NG, g);
+            if (S_out && g.lane == 0) S_out[i] = s;
             cmax = ::max(cmax, s + d);
         }
         __syncwarp();
+        i = inext;
     }
     (void)err;
     return cmax;
@@ -292,12 +308,13 @@ __device__ int decode_capacity(const SInst &I, const int *W, int u, int v, bool 
 
 template <int G>
 __device__ __forceinline__ int decode(const SInst &I, int mode, const int *W, int u, int v, bool active,
-                                      int *area, int NG, const Group<G> &g, long long &work, int &err) {
+                                      int *area, int NG, const Group<G> &g, long long &work, int &err,
+                                      int *S_out = nullptr) {
     int wk = 0, c;
-    if (mode == RCPSP_EVAL_CAPACITY) c = decode_capacity<G>(I, W, u, v, active, area, NG, g, wk, err);
-    else if (I.wps == 1) c = decode_time<G, 1>(I, W, u, v, active, area, NG, g, wk, err);
-    else if (I.wps == 2) c = decode_time<G, 2>(I, W, u, v, active, area, NG, g, wk, err);
-    else c = decode_time<G, 4>(I, W, u, v, active, area, NG, g, wk, err);
+    if (mode == RCPSP_EVAL_CAPACITY) c = decode_capacity<G>(I, W, u, v, active, area, NG, g, wk, err, S_out);
+    else if (I.wps == 1) c = decode_time<G, 1>(I, W, u, v, active, area, NG, g, wk, err, S_out);
+    else if (I.wps == 2) c = decode_time<G, 2>(I, W, u, v, active, area, NG, g, wk, err, S_out);
+    else c = decode_time<G, 4>(I, W, u, v, active, area, NG, g, wk, err, S_out);
     work += wk;
     return c;
 }
@@ -338,7 +355,7 @@ __device__ __forceinline__ void tc_put(unsigned *tc, int u, int v, int delta, bo
 // Persistent search kernel.
 // ---------------------------------------------------------------------------
 template <int G>
-__global__ void __launch_bounds__(512) search_kernel(const LaunchItem *__restrict__ items, int count,
+__global__ void __launch_bounds__(512, 2) search_kernel(const LaunchItem *__restrict__ items, int count,
                                                       int *__restrict__ queue, int move_cap) {
     extern __shared__ __align__(16) int sm[];
     __shared__ int s_item, s_nmoves, s_C, s_Cbest, s_widx, s_it, s_improved, s_err;
@@ -512,10 +529,8 @@ __global__ void __launch_bounds__(512) search_kernel(const LaunchItem *__restric
         if (warp == 0) {
             long long w1 = 0;
             int e1 = 0;
-            const int cb = decode<G>(I, mode, Wbest, 0, 0, gw == 0, area, NG, g, w1, e1);
+            const int cb = decode<G>(I, mode, Wbest, 0, 0, gw == 0, area, NG, g, w1, e1, out + n);
             if (gw == 0) {
-                const int *fin = area + pw * NG;
-                for (int i = g.lane; i < n; i += G) out[n + i] = fin[i * NG] - I.dur[i];
                 if (g.lane == 0) {
                     out[2 * n + kOutCmax] = cb;
                     if (e1 || cb != s_Cbest) atomicOr(&s_err, 2);
@@ -547,7 +562,7 @@ __global__ void __launch_bounds__(512) search_kernel(const LaunchItem *__restric
 // Decoding of caller-given lists (rcpsp_evaluate_lists).
 // ---------------------------------------------------------------------------
 template <int G>
-__global__ void __launch_bounds__(512) evaluate_kernel(LaunchItem item, const int32_t *__restrict__ lists,
+__global__ void __launch_bounds__(512, 2) evaluate_kernel(LaunchItem item, const int32_t *__restrict__ lists,
                                                         int count, int32_t *__restrict__ start,
                                                         int32_t *__restrict__ cmax_out,
                                                         long long *__restrict__ work_out,
@@ -577,10 +592,9 @@ __global__ void __launch_bounds__(512) evaluate_kernel(LaunchItem item, const in
         for (int p = g.lane; p < n; p += G) myW[p] = act ? lists[static_cast<long long>(l) * n + p] : p;
         __syncwarp();
         long long wk = 0;
-        const int c = decode<G>(I, mode, myW, 0, 0, act, area, NG, g, wk, err);
+        const int c = decode<G>(I, mode, myW, 0, 0, act, area, NG, g, wk, err,
+                                act ? start + static_cast<long long>(l) * n : nullptr);
         if (act) {
-            const int *fin = area + pw * NG;
-            for (int i = g.lane; i < n; i += G) start[static_cast<long long>(l) * n + i] = fin[i * NG] - I.dur[i];
             if (g.lane == 0) {
                 cmax_out[l] = c;
                 work_out[l] = wk;
