@@ -130,6 +130,14 @@ void default_shape(const std::vector<LaunchItem> &items, int *G, int *warps) {
     *warps = std::max(1, std::min(16, w));
 }
 
+// Potential moves one stripe examines: the largest (N-3)*delta of the batch,
+// rounded up to a warp, at most kDefaultMoveCap.
+int launch_move_cap(const std::vector<LaunchItem> &items) {
+    int m = 32;
+    for (const LaunchItem &it : items) m = std::max(m, it.h.n > 3 ? (it.h.n - 3) * it.delta : 0);
+    return std::min(rcpsp::kDefaultMoveCap, (m + 31) & ~31);
+}
+
 size_t smem_bytes(const std::vector<LaunchItem> &items, int ngroups, int move_cap) {
     int words = 0;
     for (const LaunchItem &it : items) {
@@ -358,7 +366,7 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
     default_shape(sorted, &dG, &dW);
     if (!G) G = dG;
     if (!warps) warps = std::max(dW, (G + 31) / 32);
-    const int move_cap = rcpsp::kDefaultMoveCap;
+    const int move_cap = launch_move_cap(sorted);
     const size_t smem_limit = c->prop.sharedMemPerBlockOptin > 1024 ? c->prop.sharedMemPerBlockOptin - 1024 : 0;
     size_t smem = smem_bytes(sorted, warps * (32 / G), move_cap);
     while (smem > smem_limit && p->warps_per_cta == 0 && warps > 1) {
@@ -490,7 +498,7 @@ int rcpsp_tabu_search_noalloc(rcpsp_ctx *c, const int32_t *ids, int32_t count, c
     default_shape(c->noalloc_plan, &dG, &dW);
     if (!G) G = dG;
     if (!warps) warps = std::max(dW, (G + 31) / 32);
-    const int move_cap = rcpsp::kDefaultMoveCap;
+    const int move_cap = launch_move_cap(c->noalloc_plan);
     const size_t smem_limit = c->prop.sharedMemPerBlockOptin > 1024 ? c->prop.sharedMemPerBlockOptin - 1024 : 0;
     size_t smem = smem_bytes(c->noalloc_plan, warps * (32 / G), move_cap);
     while (smem > smem_limit && p->warps_per_cta == 0 && warps > 1) {

@@ -27,6 +27,7 @@
 // The kernel never spins: the work queue is a single atomicAdd.  Internal
 // inconsistencies set an error word that the host reads as a status.
 #include <cuda_runtime.h>
+#include <limits.h>
 #include <stdint.h>
 
 #include "kernels.h"
@@ -173,32 +174,49 @@ __device__ int decode_time(const SInst &I, const int *W, int u, int v, bool acti
         for (int w = 0; w < WPS; ++w) rq[w] = I.reqw[i * WPS + w];
         // Alg. 5: the first window [s, s+d), s >= es, whose steps all fit.
         // A round tests R window offsets k..k+R-1 (offset k + lane + G*j in
-        // lane `lane`); a step that does not fit moves s past it; steps at or
-        // after F always fit.
+        // lane `lane`); a step that does not fit moves s past the highest
+        // such offset; steps at or after F always fit.
         int s = es, k = 0;
         bool done = !active || d == 0;
         while (__any_sync(kFull, !done)) {
             if (!done && s + k >= F) done = true;
-            bool fit[U];
+            const int tlim = done ? INT_MIN : ::min(F, s + d);   // test t < tlim only
+            const int t0 = s + k + g.lane;
+            const uint32_t *a0 = prof + t0 * NG;
+            int hb = -1;                                          // highest failing offset
+            if (G >= 16) {
+                unsigned bad = 0;
 #pragma unroll
-            for (int j = 0; j < U; ++j) {
-                const int o = k + g.lane + G * j;
-                const int t = s + o;
-                fit[j] = true;
-                if (!done && o < d && t < F && t < ub) {
+                for (int j = 0; j < U; ++j) {
+                    bool fit = true;
+                    if (t0 + G * j < tlim) {
 #pragma unroll
-                    for (int w = 0; w < WPS; ++w) {
-                        const uint32_t x = prof[(w * ubs + t) * NG];
-                        fit[j] = fit[j] && (((x | hi) - rq[w]) & hi) == hi;
+                        for (int w = 0; w < WPS; ++w) {
+                            const uint32_t x = a0[(w * ubs + G * j) * NG];
+                            fit = fit && (((x | hi) - rq[w]) & hi) == hi;
+                        }
+                    }
+                    bad |= g.bits(__ballot_sync(kFull, !fit)) << (G * j);
+                }
+                hb = bad ? 31 - __clz(bad) : -1;
+            } else {
+#pragma unroll
+                for (int j = 0; j < U; ++j) {
+                    if (t0 + G * j < tlim) {
+                        bool fit = true;
+#pragma unroll
+                        for (int w = 0; w < WPS; ++w) {
+                            const uint32_t x = a0[(w * ubs + G * j) * NG];
+                            fit = fit && (((x | hi) - rq[w]) & hi) == hi;
+                        }
+                        if (!fit) hb = g.lane + G * j;
                     }
                 }
+                hb = g.max(hb);
             }
-            unsigned bad = 0;
-#pragma unroll
-            for (int j = 0; j < U; ++j) bad |= g.bits(__ballot_sync(kFull, !fit[j])) << (G * j);
             if (!done) {
-                if (bad) {
-                    s += k + (31 - __clz(bad)) + 1;
+                if (hb >= 0) {
+                    s += k + hb + 1;
                     k = 0;
                 } else {
                     k += R;
@@ -209,22 +227,20 @@ __device__ int decode_time(const SInst &I, const int *W, int u, int v, bool acti
         const int f = s + d;
         if (active) {
             // Alg. 6: take r_{i,k} units over [s, s+d) (fields never borrow);
-            // untouched steps in [F, s+d) first get R_k.
+            // untouched steps in [F, s) get R_k, those in [F, s+d) R_k - r.
             if (d > 0) {
+                const int fe = ::min(f, ub);
+                if (f > ub) err |= kErrHorizon;
 #pragma unroll 2
-                for (int t = ::min(s, F) + g.lane; t < f; t += G) {
-                    if (t >= ub) {
-                        err |= kErrHorizon;
-                        break;
-                    }
+                for (int t = ::min(s, F) + g.lane; t < fe; t += G) {
+                    uint32_t *x = prof + t * NG;
 #pragma unroll
                     for (int w = 0; w < WPS; ++w) {
-                        uint32_t *x = prof + (w * ubs + t) * NG;
-                        if (t < s) *x = capw[w];                       // gap between old frontier and s
-                        else *x = (t >= F ? capw[w] : *x) - rq[w];
+                        uint32_t *xw = x + w * ubs * NG;
+                        *xw = (t >= F ? capw[w] : *xw) - (t >= s ? rq[w] : 0u);
                     }
                 }
-                F = ::max(F, f);
+                F = ::max(F, fe);
             }
             push_finish<G>(I, i, f, esa, NG, g);
             if (S_out && g.lane == 0) S_out[i] = s;
