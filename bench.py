@@ -222,6 +222,10 @@ def run_ours(args):
               mode=R.EVAL_AUTO, group_size=args.group_size, warps_per_cta=args.warps)
     ids = solver.load(insts)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)   # 256 MiB > L2
+    tuned = None
+    if not args.group_size and not args.warps:
+        tuned = solver.autotune(ids, iterations=kw["iterations"], delta=kw["delta"], tabu_len=kw["tabu_len"],
+                                mode=R.EVAL_AUTO, trial_iterations=args.tune_iterations, stream=st)
 
     def barrier():
         torch.cuda.synchronize()
@@ -355,7 +359,10 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": sum(step_ms) / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": workload_config({"parallelism": f"replicas{world}" if world > 1 else "single GPU",
-                                   "schedules_per_step": ev_step, "wall_s_timed": t_wall}),
+                                   "schedules_per_step": ev_step, "wall_s_timed": t_wall,
+                                   "launch_shape": {"group_size": (tuned or (args.group_size, args.warps))[0],
+                                                    "warps_per_cta": (tuned or (args.group_size, args.warps))[1],
+                                                    "chosen_by": "rcpsp_autotune" if tuned else "command line"}}),
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": (h1 - h0) // e2e_steps,
                 "d2h_bytes_per_step": (d1 - d0) // e2e_steps},
         "gpu_launches": args.steps,
@@ -382,6 +389,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--group-size", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)
+    ap.add_argument("--tune-iterations", type=int, default=48)
     ap.add_argument("--plain-sample", type=int, default=48)
     ap.add_argument("--latency-reps", type=int, default=100)
     ap.add_argument("--cpu-sample", type=int, default=160)

@@ -163,6 +163,20 @@ int rcpsp_tabu_search(rcpsp_ctx *ctx, const int32_t *ids, int32_t count,
 int rcpsp_tabu_search_noalloc(rcpsp_ctx *ctx, const int32_t *ids, int32_t count,
                               const rcpsp_params *params, void *cuda_stream);
 
+/* Chooses the launch shape -- lanes per neighbour decode (group_size) and
+ * warps per CTA -- for searches like `params` over these instances by
+ * timing short trial searches (trial_iterations each, on `cuda_stream`) of
+ * every shape that fits, and keeps the fastest (neighbours decoded per
+ * second) in the context under the workload's signature (largest N, horizon,
+ * words per step, swap distance, evaluator mix, batch size).  Later searches
+ * with group_size = warps_per_cta = 0 and the same signature use it.  The
+ * trials overwrite the instances' results.  Synchronous.  The shape is the
+ * GPU's own split of the neighbourhood (Sec. 6 parallelises it over the
+ * threads of a block); the paper fixes it by hand (Sec. 7). */
+int rcpsp_autotune(rcpsp_ctx *ctx, const int32_t *ids, int32_t count, const rcpsp_params *params,
+                   int32_t trial_iterations, void *cuda_stream, int32_t *best_group_size,
+                   int32_t *best_warps);
+
 /* Waits for the last search of the context and copies results to host
  * buffers: order = best list W* and start = its start times S (both [sum of N
  * over the ids], concatenated in id order), makespan = C*_max [count].  Any

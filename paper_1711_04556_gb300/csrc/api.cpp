@@ -68,6 +68,8 @@ struct rcpsp_ctx {
     cudaStream_t g_stream = nullptr;
     long long h2d = 0, d2h = 0;   // bytes copied by the context
     std::vector<LaunchItem> noalloc_plan;   // host copy of the last no-allocation plan
+    // measured launch shapes: workload signature -> (G, warps)
+    std::vector<std::pair<std::string, std::pair<int, int>>> tuned;
 };
 
 namespace {
@@ -147,6 +149,34 @@ size_t smem_bytes(const std::vector<LaunchItem> &items, int ngroups, int move_ca
         words = std::max(words, S.total);
     }
     return static_cast<size_t>(words) * 4;
+}
+
+// Workload signature of a launch plan for the shape table: largest N, time
+// horizon in 64-step buckets, words per step, swap distance, evaluator mix,
+// and the batch size in powers of two.
+std::string shape_key(const std::vector<LaunchItem> &items) {
+    int n = 0, ub = 0, wps = 0, dl = 0, cnt = static_cast<int>(items.size()), lg = 0;
+    bool tm = false, cap = false;
+    for (const LaunchItem &it : items) {
+        n = std::max(n, it.h.n);
+        ub = std::max(ub, it.h.ub);
+        wps = std::max(wps, it.h.wps);
+        dl = std::max(dl, it.delta);
+        (it.mode == RCPSP_EVAL_CAPACITY ? cap : tm) = true;
+    }
+    while ((1 << lg) < cnt) ++lg;
+    return "n" + std::to_string(n) + "_ub" + std::to_string((ub + 63) / 64) + "_w" + std::to_string(wps) + "_d" +
+           std::to_string(dl) + (tm ? "_T" : "") + (cap ? "_C" : "") + "_b" + std::to_string(lg);
+}
+
+bool tuned_shape(const rcpsp_ctx *c, const std::string &key, int *G, int *warps) {
+    for (const auto &e : c->tuned)
+        if (e.first == key) {
+            *G = e.second.first;
+            *warps = e.second.second;
+            return true;
+        }
+    return false;
 }
 
 }  // namespace
@@ -364,6 +394,7 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
     int G = gs, warps = p->warps_per_cta;
     int dG, dW;
     default_shape(sorted, &dG, &dW);
+    if (!gs && !warps) tuned_shape(c, shape_key(sorted), &dG, &dW);
     if (!G) G = dG;
     if (!warps) warps = std::max(dW, (G + 31) / 32);
     const int move_cap = launch_move_cap(sorted);
@@ -496,6 +527,7 @@ int rcpsp_tabu_search_noalloc(rcpsp_ctx *c, const int32_t *ids, int32_t count, c
     int G = gs, warps = p->warps_per_cta;
     int dG, dW;
     default_shape(c->noalloc_plan, &dG, &dW);
+    if (!gs && !warps) tuned_shape(c, shape_key(c->noalloc_plan), &dG, &dW);
     if (!G) G = dG;
     if (!warps) warps = std::max(dW, (G + 31) / 32);
     const int move_cap = launch_move_cap(c->noalloc_plan);
@@ -528,6 +560,91 @@ int rcpsp_tabu_search_noalloc(rcpsp_ctx *c, const int32_t *ids, int32_t count, c
     e = cudaEventRecord(c->done, st);
     if (e != cudaSuccess) return cuda_err(c, e, "event record");
     c->pending = true;
+    return RCPSP_OK;
+}
+
+int rcpsp_autotune(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcpsp_params *p, int32_t trial_iterations,
+                   void *stream, int32_t *best_group_size, int32_t *best_warps) {
+    if (!c) return RCPSP_E_INVALID_ARG;
+    if (!p || count <= 0 || !ids || trial_iterations < 1) return set_err(c, RCPSP_E_INVALID_ARG, "bad arguments");
+    cudaSetDevice(c->device);
+    int rc = wait_done(c);
+    if (rc != RCPSP_OK) return rc;
+    // the signature of the real search (its parameters, not the trial's)
+    std::vector<LaunchItem> items(count);
+    for (int k = 0; k < count; ++k) {
+        const int id = ids[k];
+        if (id < 0 || id >= static_cast<int>(c->insts.size()) || !c->insts[id].alive)
+            return set_err(c, RCPSP_E_NOT_FOUND, "unknown instance id");
+        const Inst &in = c->insts[id];
+        LaunchItem &it = items[k];
+        std::memset(&it, 0, sizeof(it));
+        it.h = in.h;
+        it.mode = p->eval_mode == RCPSP_EVAL_AUTO ? in.h.sel_mode : p->eval_mode;
+        int dd, tl;
+        rcpsp::default_search_params(in.h.n, &dd, &tl);
+        it.delta = p->max_swap_dist ? p->max_swap_dist : dd;
+        it.tabu_len = p->tabu_len ? p->tabu_len : tl;
+    }
+    const std::string key = shape_key(items);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return set_err(c, RCPSP_E_CUDA, "event create");
+    rcpsp_params q = *p;
+    q.iterations = std::min(p->iterations, trial_iterations);
+    q.record_trace = 0;
+    q.use_graph = 0;
+    std::vector<rcpsp_stats> stats(count);
+    double best_rate = -1.0;
+    int bG = 0, bW = 0;
+    const int gsz[] = {1, 2, 4, 8, 16, 32};
+    const int wcnt[] = {1, 2, 3, 4, 6, 8, 12, 16};
+    for (int G : gsz)
+        for (int W : wcnt) {
+            const int ng = W * (32 / G);
+            if (ng < 8 || ng > 256) continue;
+            q.group_size = G;
+            q.warps_per_cta = W;
+            cudaEventRecord(e0, st);
+            int r = rcpsp_tabu_search(c, ids, count, &q, stream);
+            if (r == RCPSP_E_TOO_LARGE) continue;             // shape does not fit
+            if (r != RCPSP_OK) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return r;
+            }
+            cudaEventRecord(e1, st);
+            r = rcpsp_get_schedules(c, ids, count, nullptr, nullptr, nullptr, stats.data());
+            if (r != RCPSP_OK) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return r;
+            }
+            float ms = 0.f;
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&ms, e0, e1);
+            long long ev = 0;
+            for (const rcpsp_stats &x : stats) ev += x.evaluated;
+            const double rate = ms > 0 ? static_cast<double>(ev > 0 ? ev : 1) / ms : 0.0;
+            if (rate > best_rate) {
+                best_rate = rate;
+                bG = G;
+                bW = W;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!bG) return set_err(c, RCPSP_E_TOO_LARGE, "no launch shape fits");
+    bool found = false;
+    for (auto &e : c->tuned)
+        if (e.first == key) {
+            e.second = {bG, bW};
+            found = true;
+        }
+    if (!found) c->tuned.push_back({key, {bG, bW}});
+    if (best_group_size) *best_group_size = bG;
+    if (best_warps) *best_warps = bW;
     return RCPSP_OK;
 }
 

@@ -20,7 +20,7 @@ EVAL_AUTO, EVAL_TIME, EVAL_CAPACITY = 0, 1, 2
 ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "CYCLE", -3: "DUMMY", -4: "DEMAND_EXCEEDS_CAP",
           -5: "TOO_LARGE", -6: "CUDA", -7: "TIMEOUT", -8: "NOT_FOUND", -9: "DEVICE"}
 EXPORTS = ("rcpsp_create", "rcpsp_destroy", "rcpsp_load_instances", "rcpsp_free_instances",
-           "rcpsp_tabu_search", "rcpsp_tabu_search_noalloc", "rcpsp_get_schedules", "rcpsp_get_trace", "rcpsp_evaluate_lists",
+           "rcpsp_tabu_search", "rcpsp_tabu_search_noalloc", "rcpsp_autotune", "rcpsp_get_schedules", "rcpsp_get_trace", "rcpsp_evaluate_lists",
            "rcpsp_prepare_instance", "rcpsp_transfer_bytes", "rcpsp_last_error")
 
 
@@ -77,6 +77,8 @@ def library(path: Optional[str] = None):
         "rcpsp_free_instances": (C.c_int, [C.c_void_p, P(C.c_int32), C.c_int32]),
         "rcpsp_tabu_search": (C.c_int, [C.c_void_p, P(C.c_int32), C.c_int32, P(Params), C.c_void_p]),
         "rcpsp_tabu_search_noalloc": (C.c_int, [C.c_void_p, P(C.c_int32), C.c_int32, P(Params), C.c_void_p]),
+        "rcpsp_autotune": (C.c_int, [C.c_void_p, P(C.c_int32), C.c_int32, P(Params), C.c_int32, C.c_void_p,
+                                     P(C.c_int32), P(C.c_int32)]),
         "rcpsp_get_schedules": (C.c_int, [C.c_void_p, P(C.c_int32), C.c_int32, P(C.c_int32), P(C.c_int32),
                                           P(C.c_int32), P(Stats)]),
         "rcpsp_get_trace": (C.c_int, [C.c_void_p, C.c_int32, P(C.c_int32), C.c_int32, P(C.c_int32)]),
@@ -219,6 +221,17 @@ class Solver:
         p = Params(iterations, delta, tabu_len, mode, int(stop_at_cp), group_size, warps_per_cta, 0, 0)
         handle = getattr(stream, "cuda_stream", stream) or None
         self._check(self.lib.rcpsp_tabu_search_noalloc(self.ctx, _ptr(ids), len(ids), C.byref(p), handle))
+
+    def autotune(self, ids, iterations: int = 100, delta: int = 0, tabu_len: int = 0, mode: int = EVAL_AUTO,
+                 stop_at_cp: bool = True, trial_iterations: int = 48, stream=None):
+        """rcpsp_autotune: times trial searches of every launch shape; returns (group_size, warps)."""
+        ids = _i32(ids)
+        p = Params(iterations, delta, tabu_len, mode, int(stop_at_cp), 0, 0, 0, 0)
+        g, w = C.c_int32(0), C.c_int32(0)
+        handle = getattr(stream, "cuda_stream", stream) or None
+        self._check(self.lib.rcpsp_autotune(self.ctx, _ptr(ids), len(ids), C.byref(p), trial_iterations, handle,
+                                            C.byref(g), C.byref(w)))
+        return g.value, w.value
 
     def results(self, ids) -> List[dict]:
         ids = _i32(ids)

@@ -127,6 +127,19 @@ def test_mixed_sample_auto(solver, oracle):
     solver.free(ids)
 
 
+def test_autotuned_shape_keeps_results(solver, oracle):
+    insts = I.config_batch("j30_batch", 64, first=300)
+    ids = solver.load(insts)
+    g, w = solver.autotune(ids, iterations=80, delta=20, tabu_len=60, trial_iterations=8)
+    assert g in (1, 2, 4, 8, 16, 32) and 1 <= w <= 16
+    solver.search(ids, iterations=80, delta=20, tabu_len=60)            # shape 0/0: the tuned one
+    got = solver.results(ids)
+    ref = oracle.tabu_search_batch(insts, [(80, 20, 60, 0, 1)] * len(insts), NPROC)
+    for a, b in zip(got, ref):
+        compare_search(oracle, a, b)
+    solver.free(ids)
+
+
 # -------------------------------------------------------------- edge cases
 def test_edge_cases(solver, oracle):
     base = medium_instances(1, first=1000)[0]
