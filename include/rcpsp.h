@@ -137,8 +137,11 @@ int rcpsp_free_instances(rcpsp_ctx *ctx, const int32_t *ids, int32_t count);
 /* Runs one tabu search per listed instance (Sec. 6: neighbourhood of swap
  * moves with Eqs. 5-6 filtering, serial-SGS decoding with the chosen
  * evaluator, best admissible move under the simple tabu list (Algs. 2-3)
- * and the aspiration rule).  All searches share one persistent launch on
- * `cuda_stream` (a cudaStream_t; NULL = legacy default stream); the call is
+ * and the aspiration rule).  The searches are grouped by footprint class
+ * (per-group scratch up to 2K, up to 8K, above 8K words); each class is one
+ * persistent launch with its own shape, the first on `cuda_stream` (a
+ * cudaStream_t; NULL = legacy default stream), the others on streams of the
+ * context forked from it and joined back into it.  The call is
  * asynchronous.  Results stay on the device until rcpsp_get_schedules. */
 int rcpsp_tabu_search(rcpsp_ctx *ctx, const int32_t *ids, int32_t count,
                       const rcpsp_params *params, void *cuda_stream);
@@ -168,8 +171,11 @@ int rcpsp_tabu_search_noalloc(rcpsp_ctx *ctx, const int32_t *ids, int32_t count,
  * timing short trial searches (trial_iterations each, on `cuda_stream`) of
  * every shape that fits, and keeps the fastest (neighbours decoded per
  * second) in the context under the workload's signature (largest N, horizon,
- * words per step, swap distance, evaluator mix, batch size).  Later searches
- * with group_size = warps_per_cta = 0 and the same signature use it.  The
+ * words per step, swap distance, evaluator mix, batch size).  Instances are
+ * tuned per footprint class (per-group scratch up to 2K, up to 8K, above
+ * 8K words), the unit a search launches apart; the returned shape is the
+ * one of the largest class.  Later searches with group_size =
+ * warps_per_cta = 0 and the same signature use it.  The
  * trials overwrite the instances' results.  Synchronous.  The shape is the
  * GPU's own split of the neighbourhood (Sec. 6 parallelises it over the
  * threads of a block); the paper fixes it by hand (Sec. 7). */

@@ -64,10 +64,14 @@ struct rcpsp_ctx {
     // graph replay: the cached graph corresponds to the items now on the device
     cudaGraphExec_t gexec = nullptr;
     std::vector<LaunchItem> g_items;
-    int g_shape[5] = {0, 0, 0, 0, 0};
     cudaStream_t g_stream = nullptr;
     long long h2d = 0, d2h = 0;   // bytes copied by the context
     std::vector<LaunchItem> noalloc_plan;   // host copy of the last no-allocation plan
+    // footprint classes beyond the first run on their own streams, forked
+    // from and joined back to the caller's stream
+    cudaStream_t aux[2] = {nullptr, nullptr};
+    cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
+    std::vector<int> g_launch_sig;
     // measured launch shapes: workload signature -> (G, warps)
     std::vector<std::pair<std::string, std::pair<int, int>>> tuned;
 };
@@ -151,6 +155,22 @@ size_t smem_bytes(const std::vector<LaunchItem> &items, int ngroups, int move_ca
     return static_cast<size_t>(words) * 4;
 }
 
+// Footprint class of a search: per-group scratch words (profile or capacity
+// state plus N earliest starts) up to 2K, up to 8K, or more.  Each class of
+// a call gets its own launch shape, so that small instances are not run at
+// the group count the largest instance allows.
+constexpr int kClasses = 3;
+
+int footprint_class(const LaunchItem &it) {
+    const int gw = rcpsp::profile_words(it.mode, it.h.wps, it.h.ub, it.h.sum_cap) + it.h.n;
+    return gw <= 2048 ? 0 : (gw <= 8192 ? 1 : 2);
+}
+
+struct ClassLaunch {
+    int offset = 0, count = 0, G = 0, threads = 0, blocks = 0, move_cap = 0;
+    size_t smem = 0;
+};
+
 // Workload signature of a launch plan for the shape table: largest N, time
 // horizon in 64-step buckets, words per step, swap distance, evaluator mix,
 // and the batch size in powers of two.
@@ -197,6 +217,11 @@ int rcpsp_create(rcpsp_ctx **ctx, int device, const rcpsp_allocator *alloc) {
     cudaError_t e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaGetDeviceProperties(&c->prop, device);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming);
+    for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
+        e = cudaStreamCreateWithFlags(&c->aux[q], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join[q], cudaEventDisableTiming);
+    }
     if (e != cudaSuccess) {
         delete c;
         return RCPSP_E_CUDA;
@@ -223,6 +248,11 @@ int rcpsp_destroy(rcpsp_ctx *c) {
     dev_free(c, c->queue_dev, 16, nullptr);
     if (c->items_host) cudaFreeHost(c->items_host);
     cudaEventDestroy(c->done);
+    cudaEventDestroy(c->fork);
+    for (int q = 0; q < 2; ++q) {
+        if (c->aux[q]) cudaStreamDestroy(c->aux[q]);
+        if (c->join[q]) cudaEventDestroy(c->join[q]);
+    }
     delete c;
     return RCPSP_OK;
 }
@@ -384,42 +414,58 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
         }
         cost[k] = rcpsp::estimate_cost(in.h, it.mode, it.iterations, it.delta);
     }
-    // longest first (LPT) on the work queue
-    std::vector<int> order(count);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-    std::vector<LaunchItem> sorted(count);
-    for (int k = 0; k < count; ++k) sorted[k] = items[order[k]];
-    // launch shape
-    int G = gs, warps = p->warps_per_cta;
-    int dG, dW;
-    default_shape(sorted, &dG, &dW);
-    if (!gs && !warps) tuned_shape(c, shape_key(sorted), &dG, &dW);
-    if (!G) G = dG;
-    if (!warps) warps = std::max(dW, (G + 31) / 32);
-    const int move_cap = launch_move_cap(sorted);
+    // footprint classes, each ordered longest first (LPT) on its own queue
+    std::vector<LaunchItem> sorted;
+    sorted.reserve(count);
+    std::vector<ClassLaunch> launches;
     const size_t smem_limit = c->prop.sharedMemPerBlockOptin > 1024 ? c->prop.sharedMemPerBlockOptin - 1024 : 0;
-    size_t smem = smem_bytes(sorted, warps * (32 / G), move_cap);
-    while (smem > smem_limit && p->warps_per_cta == 0 && warps > 1) {
-        --warps;
-        smem = smem_bytes(sorted, warps * (32 / G), move_cap);
+    for (int q = 0; q < kClasses; ++q) {
+        std::vector<int> idx;
+        for (int k = 0; k < count; ++k)
+            if (footprint_class(items[k]) == q) idx.push_back(k);
+        if (idx.empty()) continue;
+        std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+        std::vector<LaunchItem> part;
+        for (int k : idx) part.push_back(items[k]);
+        ClassLaunch L;
+        L.offset = static_cast<int>(sorted.size());
+        L.count = static_cast<int>(part.size());
+        sorted.insert(sorted.end(), part.begin(), part.end());
+        int G = gs, warps = p->warps_per_cta;
+        int dG, dW;
+        default_shape(part, &dG, &dW);
+        if (!gs && !warps) tuned_shape(c, shape_key(part), &dG, &dW);
+        if (!G) G = dG;
+        if (!warps) warps = std::max(dW, (G + 31) / 32);
+        L.move_cap = launch_move_cap(part);
+        size_t smem = smem_bytes(part, warps * (32 / G), L.move_cap);
+        while (smem > smem_limit && p->warps_per_cta == 0 && warps > 1) {
+            --warps;
+            smem = smem_bytes(part, warps * (32 / G), L.move_cap);
+        }
+        if (smem > smem_limit)
+            return set_err(c, RCPSP_E_TOO_LARGE, "instance state does not fit in shared memory at this launch shape");
+        L.G = G;
+        L.threads = warps * 32;
+        L.smem = smem;
+        // the limit belongs to the kernel of this G, shared by every class that uses it
+        cudaError_t e = rcpsp::prepare_search(G, smem_limit);
+        if (e != cudaSuccess) return cuda_err(c, e, "kernel attributes");
+        int per_sm = 0;
+        e = rcpsp::search_occupancy(G, L.threads, smem, &per_sm);
+        if (e != cudaSuccess) return cuda_err(c, e, "occupancy");
+        if (per_sm < 1) return set_err(c, RCPSP_E_TOO_LARGE, "launch shape does not fit on an SM");
+        L.blocks = std::max(1, std::min(L.count, per_sm * c->prop.multiProcessorCount));
+        launches.push_back(L);
     }
-    if (smem > smem_limit)
-        return set_err(c, RCPSP_E_TOO_LARGE, "instance state does not fit in shared memory at this launch shape");
-    const int threads = warps * 32;
-    cudaError_t e = rcpsp::prepare_search(G, smem);
-    if (e != cudaSuccess) return cuda_err(c, e, "kernel attributes");
-    int per_sm = 0;
-    e = rcpsp::search_occupancy(G, threads, smem, &per_sm);
-    if (e != cudaSuccess) return cuda_err(c, e, "occupancy");
-    if (per_sm < 1) return set_err(c, RCPSP_E_TOO_LARGE, "launch shape does not fit on an SM");
-    const int blocks = std::max(1, std::min(count, per_sm * c->prop.multiProcessorCount));
+    std::vector<int> sig;
+    for (const ClassLaunch &L : launches)
+        sig.insert(sig.end(), {L.offset, L.count, L.G, L.threads, L.blocks, L.move_cap, static_cast<int>(L.smem)});
     // device copy of the plan
+    cudaError_t e = cudaSuccess;
     const size_t ibytes = sizeof(LaunchItem) * count;
-    const int shape[5] = {G, threads, static_cast<int>(smem), blocks, move_cap};
     const bool same_plan = c->gexec && c->g_stream == st && c->g_items.size() == sorted.size() &&
-                           std::memcmp(c->g_items.data(), sorted.data(), ibytes) == 0 &&
-                           std::memcmp(c->g_shape, shape, sizeof(shape)) == 0;
+                           std::memcmp(c->g_items.data(), sorted.data(), ibytes) == 0 && c->g_launch_sig == sig;
     if (!(p->use_graph && same_plan)) {
         if (c->items_cap < ibytes) {
             cudaStreamSynchronize(st);
@@ -444,14 +490,36 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
             c->g_items.clear();
         }
     }
+    // queue reset, then one persistent launch per class; classes after the
+    // first run on forked streams and join back before the done event
+    auto launch_all = [&](cudaStream_t s0) -> cudaError_t {
+        cudaError_t r = cudaMemsetAsync(c->queue_dev, 0, sizeof(int) * kClasses, s0);
+        if (r != cudaSuccess) return r;
+        if (launches.size() > 1 && (r = cudaEventRecord(c->fork, s0)) != cudaSuccess) return r;
+        for (size_t q = 0; q < launches.size(); ++q) {
+            const ClassLaunch &L = launches[q];
+            cudaStream_t sq = q == 0 ? s0 : c->aux[q - 1];
+            if (q > 0 && (r = cudaStreamWaitEvent(sq, c->fork, 0)) != cudaSuccess) return r;
+            r = rcpsp::launch_search(L.G, c->items_dev + L.offset, L.count, c->queue_dev + q, L.move_cap, L.blocks,
+                                     L.threads, L.smem, sq);
+            if (r != cudaSuccess) return r;
+            if (q > 0 && (r = cudaEventRecord(c->join[q - 1], sq)) != cudaSuccess) return r;
+        }
+        for (size_t q = 1; q < launches.size(); ++q)
+            if ((r = cudaStreamWaitEvent(s0, c->join[q - 1], 0)) != cudaSuccess) return r;
+        return cudaSuccess;
+    };
     if (p->use_graph) {
         if (!c->gexec) {
             cudaGraph_t graph = nullptr;
             e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
             if (e != cudaSuccess) return cuda_err(c, e, "begin capture");
-            cudaMemsetAsync(c->queue_dev, 0, sizeof(int), st);
-            rcpsp::launch_search(G, c->items_dev, count, c->queue_dev, move_cap, blocks, threads, smem, st);
+            const cudaError_t le = launch_all(st);
             e = cudaStreamEndCapture(st, &graph);
+            if (le != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                return cuda_err(c, le, "captured launch");
+            }
             if (e != cudaSuccess) return cuda_err(c, e, "end capture");
             e = cudaGraphInstantiate(&c->gexec, graph, 0);
             cudaGraphDestroy(graph);
@@ -460,15 +528,13 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
                 return cuda_err(c, e, "graph instantiate");
             }
             c->g_items = sorted;
-            std::memcpy(c->g_shape, shape, sizeof(shape));
+            c->g_launch_sig = sig;
             c->g_stream = st;
         }
         e = cudaGraphLaunch(c->gexec, st);
         if (e != cudaSuccess) return cuda_err(c, e, "graph launch");
     } else {
-        e = cudaMemsetAsync(c->queue_dev, 0, sizeof(int), st);
-        if (e == cudaSuccess)
-            e = rcpsp::launch_search(G, c->items_dev, count, c->queue_dev, move_cap, blocks, threads, smem, st);
+        e = launch_all(st);
         if (e != cudaSuccess) return cuda_err(c, e, "search launch");
     }
     e = cudaEventRecord(c->done, st);
@@ -586,7 +652,6 @@ int rcpsp_autotune(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcpsp_
         it.delta = p->max_swap_dist ? p->max_swap_dist : dd;
         it.tabu_len = p->tabu_len ? p->tabu_len : tl;
     }
-    const std::string key = shape_key(items);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
@@ -595,56 +660,77 @@ int rcpsp_autotune(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcpsp_
     q.iterations = std::min(p->iterations, trial_iterations);
     q.record_trace = 0;
     q.use_graph = 0;
-    std::vector<rcpsp_stats> stats(count);
-    double best_rate = -1.0;
-    int bG = 0, bW = 0;
-    const int gsz[] = {1, 2, 4, 8, 16, 32};
-    const int wcnt[] = {1, 2, 3, 4, 6, 8, 12, 16};
-    for (int G : gsz)
-        for (int W : wcnt) {
-            const int ng = W * (32 / G);
-            if (ng < 8 || ng > 256) continue;
-            q.group_size = G;
-            q.warps_per_cta = W;
-            cudaEventRecord(e0, st);
-            int r = rcpsp_tabu_search(c, ids, count, &q, stream);
-            if (r == RCPSP_E_TOO_LARGE) continue;             // shape does not fit
-            if (r != RCPSP_OK) {
-                cudaEventDestroy(e0);
-                cudaEventDestroy(e1);
-                return r;
+    int ret_G = 0, ret_W = 0, ret_count = -1;
+    // each footprint class is tuned on its own (searches launch them apart)
+    for (int cls = 0; cls < kClasses; ++cls) {
+        std::vector<int32_t> cids;
+        std::vector<LaunchItem> part;
+        for (int k = 0; k < count; ++k)
+            if (footprint_class(items[k]) == cls) {
+                cids.push_back(ids[k]);
+                part.push_back(items[k]);
             }
-            cudaEventRecord(e1, st);
-            r = rcpsp_get_schedules(c, ids, count, nullptr, nullptr, nullptr, stats.data());
-            if (r != RCPSP_OK) {
-                cudaEventDestroy(e0);
-                cudaEventDestroy(e1);
-                return r;
+        if (cids.empty()) continue;
+        const int cn = static_cast<int>(cids.size());
+        const std::string key = shape_key(part);
+        std::vector<rcpsp_stats> stats(cn);
+        double best_rate = -1.0;
+        int bG = 0, bW = 0;
+        const int gsz[] = {1, 2, 4, 8, 16, 32};
+        const int wcnt[] = {1, 2, 3, 4, 6, 8, 12, 16};
+        for (int G : gsz)
+            for (int W : wcnt) {
+                const int ng = W * (32 / G);
+                const int min_groups = cls == 0 ? 8 : (cls == 1 ? 2 : 1);   // large states fit few groups
+                if (ng < min_groups || ng > 256) continue;
+                q.group_size = G;
+                q.warps_per_cta = W;
+                cudaEventRecord(e0, st);
+                int r = rcpsp_tabu_search(c, cids.data(), cn, &q, stream);
+                if (r == RCPSP_E_TOO_LARGE) continue;             // shape does not fit
+                if (r == RCPSP_OK) {
+                    cudaEventRecord(e1, st);
+                    r = rcpsp_get_schedules(c, cids.data(), cn, nullptr, nullptr, nullptr, stats.data());
+                }
+                if (r != RCPSP_OK) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return r;
+                }
+                float ms = 0.f;
+                cudaEventSynchronize(e1);
+                cudaEventElapsedTime(&ms, e0, e1);
+                long long ev = 0;
+                for (const rcpsp_stats &x : stats) ev += x.evaluated;
+                const double rate = ms > 0 ? static_cast<double>(ev > 0 ? ev : 1) / ms : 0.0;
+                if (rate > best_rate) {
+                    best_rate = rate;
+                    bG = G;
+                    bW = W;
+                }
             }
-            float ms = 0.f;
-            cudaEventSynchronize(e1);
-            cudaEventElapsedTime(&ms, e0, e1);
-            long long ev = 0;
-            for (const rcpsp_stats &x : stats) ev += x.evaluated;
-            const double rate = ms > 0 ? static_cast<double>(ev > 0 ? ev : 1) / ms : 0.0;
-            if (rate > best_rate) {
-                best_rate = rate;
-                bG = G;
-                bW = W;
-            }
+        if (!bG) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return set_err(c, RCPSP_E_TOO_LARGE, "no launch shape fits");
         }
+        bool found = false;
+        for (auto &e : c->tuned)
+            if (e.first == key) {
+                e.second = {bG, bW};
+                found = true;
+            }
+        if (!found) c->tuned.push_back({key, {bG, bW}});
+        if (cn > ret_count) {
+            ret_count = cn;
+            ret_G = bG;
+            ret_W = bW;
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (!bG) return set_err(c, RCPSP_E_TOO_LARGE, "no launch shape fits");
-    bool found = false;
-    for (auto &e : c->tuned)
-        if (e.first == key) {
-            e.second = {bG, bW};
-            found = true;
-        }
-    if (!found) c->tuned.push_back({key, {bG, bW}});
-    if (best_group_size) *best_group_size = bG;
-    if (best_warps) *best_warps = bW;
+    if (best_group_size) *best_group_size = ret_G;
+    if (best_warps) *best_warps = ret_W;
     return RCPSP_OK;
 }
 
