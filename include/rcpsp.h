@@ -222,6 +222,60 @@ int rcpsp_prepare_instance(const rcpsp_instance *inst, int32_t *critical_path, i
  * created (instance records, launch plans, results, traces); host. */
 int rcpsp_transfer_bytes(const rcpsp_ctx *ctx, int64_t *h2d, int64_t *d2h);
 
+/* ------------------------------------------------------------------------
+ * Continuous-batching solve server.  Requests are admitted while others run,
+ * as launch slots and device memory free up, and their searches overlap on
+ * the GPU.  A search's result does not depend on what else is in flight.
+ * ---------------------------------------------------------------------- */
+typedef struct rcpsp_server rcpsp_server;
+
+typedef struct {
+    int32_t slots;              /* batches in flight (one stream each), 1..16; 0 = 4 */
+    int32_t max_batch;          /* requests per batch; 0 = 256                      */
+    int64_t memory_budget;      /* device bytes of admitted requests; 0 = 1 GiB.
+                                   A request larger than the budget is admitted
+                                   alone when nothing else is in flight          */
+    int32_t poll_us;            /* idle wait of the worker loop; 0 = 100 us        */
+} rcpsp_server_config;
+
+typedef struct {
+    int64_t tag;                /* the caller's tag of the request                 */
+    int32_t n;                  /* N of the instance                               */
+    int32_t status;             /* 0 or a negative RCPSP_E_* code                  */
+    int32_t best_cmax, iterations, eval_mode, critical_path;
+    int64_t evaluated, work;    /* as in rcpsp_stats                               */
+    int64_t t_submit_ns, t_launch_ns, t_done_ns;   /* host steady clock           */
+    const int32_t *order;       /* [n] best list W*; owned by the server until the
+                                   next rcpsp_server_poll                          */
+    const int32_t *start;       /* [n] its start times S                           */
+} rcpsp_completion;
+
+typedef struct {
+    int64_t submitted, rejected, admitted, completed, batches;
+    int64_t inflight_requests, pending, inflight_bytes, max_inflight_bytes;
+    int64_t evaluated;          /* neighbours decoded by completed requests        */
+} rcpsp_server_stats;
+
+/* Starts a server on `device` (cfg may be NULL for the defaults).  It owns
+ * `slots` library contexts whose device memory comes from stream-ordered
+ * allocations on their own streams, and one worker thread. */
+int rcpsp_server_create(rcpsp_server **srv, int device, const rcpsp_server_config *cfg);
+/* Stops the worker after the batches in flight and frees everything. */
+int rcpsp_server_destroy(rcpsp_server *srv);
+/* Validates one instance (as rcpsp_load_instances does; the same error
+ * codes), copies it and queues it with its search parameters (record_trace
+ * and use_graph must be 0).  Requests with identical parameters share
+ * batches, in arrival order.  Returns at once. */
+int rcpsp_server_submit(rcpsp_server *srv, const rcpsp_instance *inst, const rcpsp_params *params,
+                        int64_t tag);
+/* Moves up to `capacity` finished requests into `out` (host), waiting up to
+ * wait_ms for the first one; *count gets how many.  The arrays they point to
+ * stay valid until the next call. */
+int rcpsp_server_poll(rcpsp_server *srv, rcpsp_completion *out, int32_t capacity, int32_t *count,
+                      int32_t wait_ms);
+/* Counters of the server (host). */
+int rcpsp_server_get_stats(rcpsp_server *srv, rcpsp_server_stats *stats);
+
 /* Text of the last error of the context (never NULL). */
 const char *rcpsp_last_error(const rcpsp_ctx *ctx);
 

@@ -201,6 +201,23 @@ bool tuned_shape(const rcpsp_ctx *c, const std::string &key, int *G, int *warps)
 
 }  // namespace
 
+namespace rcpsp {
+
+// 1 when the context's last search has finished (or none is pending), 0 while
+// it runs, a negative RCPSP_E_* code when the device reported an error.
+int ctx_search_done(rcpsp_ctx *c) {
+    if (!c->pending) return 1;
+    const cudaError_t e = cudaEventQuery(c->done);
+    if (e == cudaSuccess) {
+        c->pending = false;
+        return 1;
+    }
+    if (e == cudaErrorNotReady) return 0;
+    return cuda_err(c, e, "search");
+}
+
+}  // namespace rcpsp
+
 extern "C" {
 
 int rcpsp_create(rcpsp_ctx **ctx, int device, const rcpsp_allocator *alloc) {

@@ -21,7 +21,8 @@ ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "CYCLE", -3: "DUMMY", -4: "DEMAND_EXCE
           -5: "TOO_LARGE", -6: "CUDA", -7: "TIMEOUT", -8: "NOT_FOUND", -9: "DEVICE"}
 EXPORTS = ("rcpsp_create", "rcpsp_destroy", "rcpsp_load_instances", "rcpsp_free_instances",
            "rcpsp_tabu_search", "rcpsp_tabu_search_noalloc", "rcpsp_autotune", "rcpsp_get_schedules", "rcpsp_get_trace", "rcpsp_evaluate_lists",
-           "rcpsp_prepare_instance", "rcpsp_transfer_bytes", "rcpsp_last_error")
+           "rcpsp_prepare_instance", "rcpsp_transfer_bytes", "rcpsp_server_create", "rcpsp_server_destroy",
+           "rcpsp_server_submit", "rcpsp_server_poll", "rcpsp_server_get_stats", "rcpsp_last_error")
 
 
 class RcpspError(RuntimeError):
@@ -47,6 +48,25 @@ class Stats(C.Structure):
     _fields_ = [("evaluated", C.c_int64), ("work", C.c_int64), ("iterations", C.c_int32),
                 ("eval_mode", C.c_int32), ("critical_path", C.c_int32), ("status", C.c_int32),
                 ("t_start_ns", C.c_int64), ("t_end_ns", C.c_int64)]
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("slots", C.c_int32), ("max_batch", C.c_int32), ("memory_budget", C.c_int64),
+                ("poll_us", C.c_int32)]
+
+
+class Completion(C.Structure):
+    _fields_ = [("tag", C.c_int64), ("n", C.c_int32), ("status", C.c_int32), ("best_cmax", C.c_int32),
+                ("iterations", C.c_int32), ("eval_mode", C.c_int32), ("critical_path", C.c_int32),
+                ("evaluated", C.c_int64), ("work", C.c_int64), ("t_submit_ns", C.c_int64),
+                ("t_launch_ns", C.c_int64), ("t_done_ns", C.c_int64), ("order", C.POINTER(C.c_int32)),
+                ("start", C.POINTER(C.c_int32))]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [(k, C.c_int64) for k in ("submitted", "rejected", "admitted", "completed", "batches",
+                                         "inflight_requests", "pending", "inflight_bytes",
+                                         "max_inflight_bytes", "evaluated")]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -87,6 +107,11 @@ def library(path: Optional[str] = None):
         "rcpsp_prepare_instance": (C.c_int, [P(Instance), P(C.c_int32), P(C.c_int32), P(C.c_int32),
                                              P(C.c_int32), C.c_char_p, C.c_int32]),
         "rcpsp_transfer_bytes": (C.c_int, [C.c_void_p, P(C.c_int64), P(C.c_int64)]),
+        "rcpsp_server_create": (C.c_int, [P(C.c_void_p), C.c_int, P(ServerConfig)]),
+        "rcpsp_server_destroy": (C.c_int, [C.c_void_p]),
+        "rcpsp_server_submit": (C.c_int, [C.c_void_p, P(Instance), P(Params), C.c_int64]),
+        "rcpsp_server_poll": (C.c_int, [C.c_void_p, P(Completion), C.c_int32, P(C.c_int32), C.c_int32]),
+        "rcpsp_server_get_stats": (C.c_int, [C.c_void_p, P(ServerStats)]),
         "rcpsp_last_error": (C.c_char_p, [C.c_void_p]),
     }
     for name, (res, args) in sig.items():
@@ -275,3 +300,64 @@ class Solver:
         self._check(self.lib.rcpsp_evaluate_lists(self.ctx, int(id_), _ptr(lists), cnt, mode, _ptr(start),
                                                   _ptr(cmax), _ptr(work, C.c_int64), handle))
         return cmax, start.reshape(cnt, n), work
+
+
+class Server:
+    """Continuous-batching solve server (rcpsp_server_* in include/rcpsp.h)."""
+
+    def __init__(self, device: int = 0, slots: int = 4, max_batch: int = 256, memory_budget: int = 1 << 30,
+                 poll_us: int = 100, lib_path: Optional[str] = None):
+        self.lib = library(lib_path)
+        self.srv = C.c_void_p()
+        cfg = ServerConfig(slots, max_batch, memory_budget, poll_us)
+        rc = self.lib.rcpsp_server_create(C.byref(self.srv), device, C.byref(cfg))
+        if rc != 0:
+            raise RcpspError(rc, "server create")
+        self._buf = (Completion * 4096)()
+
+    def submit(self, inst, tag: int, iterations: int = 1000, delta: int = 0, tabu_len: int = 0,
+               mode: int = EVAL_AUTO, stop_at_cp: bool = True, level_key=None) -> None:
+        m = _Marshalled(inst, level_key)
+        p = Params(iterations, delta, tabu_len, mode, int(stop_at_cp), 0, 0, 0, 0)
+        rc = self.lib.rcpsp_server_submit(self.srv, C.byref(m.s), C.byref(p), int(tag))
+        if rc != 0:
+            raise RcpspError(rc, "submit")
+
+    def poll(self, wait_ms: int = 0, capacity: int = 4096) -> List[dict]:
+        cnt = C.c_int32(0)
+        rc = self.lib.rcpsp_server_poll(self.srv, self._buf, min(capacity, 4096), C.byref(cnt), wait_ms)
+        if rc != 0:
+            raise RcpspError(rc, "poll")
+        out = []
+        for k in range(cnt.value):
+            c = self._buf[k]
+            n = c.n
+            W = np.ctypeslib.as_array(c.order, (n,)).copy() if c.order else np.zeros(0, np.int32)
+            S = np.ctypeslib.as_array(c.start, (n,)).copy() if c.start else np.zeros(0, np.int32)
+            out.append(dict(tag=c.tag, status=c.status, best_cmax=c.best_cmax, iterations=c.iterations,
+                            mode=c.eval_mode, cp=c.critical_path, evaluated=c.evaluated, work=c.work,
+                            best_W=W, best_S=S, t_submit_ns=c.t_submit_ns, t_launch_ns=c.t_launch_ns,
+                            t_done_ns=c.t_done_ns))
+        return out
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        self.lib.rcpsp_server_get_stats(self.srv, C.byref(st))
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if self.srv:
+            self.lib.rcpsp_server_destroy(self.srv)
+            self.srv = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
