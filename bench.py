@@ -195,6 +195,45 @@ def run_reference(args):
     return 0
 
 
+def serving_run(R, I, device, family, rate, seconds, iterations, pool_size=512, seed=5, drain_s=30.0):
+    """Poisson arrivals at `rate` req/s for `seconds` into the continuous-batching server.
+
+    Requests cycle through a pool of distinct instances of `family`; each is
+    one search of `iterations` iterations.  Latency = host time from submit
+    to the completion record.  Requests still in flight `drain_s` after the
+    last arrival are counted as not completed.
+    """
+    pool = I.config_batch(family, pool_size)
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, int(rate * seconds * 1.5) + 16)
+    arrivals = np.cumsum(gaps)
+    arrivals = arrivals[arrivals < seconds]
+    done = []
+    with R.Server(device, slots=4, max_batch=256, memory_budget=2 << 30) as srv:
+        t0 = time.perf_counter()
+        k = 0
+        while True:
+            now = time.perf_counter() - t0
+            while k < len(arrivals) and arrivals[k] <= now:
+                srv.submit(pool[k % pool_size], tag=k, iterations=iterations)
+                k += 1
+            done += srv.poll(wait_ms=0)
+            if k == len(arrivals) and (len(done) == k or now > seconds + drain_s):
+                break
+            nxt = arrivals[k] - now if k < len(arrivals) else 0.002
+            time.sleep(min(max(nxt, 0.0), 0.002))
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+    lat = [(c["t_done_ns"] - c["t_submit_ns"]) / 1e6 for c in done if c["status"] == 0]
+    ev = sum(c["evaluated"] for c in done)
+    p50, p99 = percentiles(lat) if lat else (None, None)
+    return {"workload": f"{family} requests, {iterations} iterations each, Poisson {rate:g} req/s for {seconds:g} s",
+            "offered_req_s": len(arrivals) / seconds, "completed": len(lat), "submitted": int(len(arrivals)),
+            "completed_req_s": len(lat) / wall, "schedules_per_s": ev / wall, "wall_s": wall,
+            "latency_ms": {"p50": p50, "p99": p99}, "batches": st["batches"],
+            "max_inflight_bytes": st["max_inflight_bytes"]}
+
+
 def percentiles(xs):
     xs = np.asarray(xs, dtype=np.float64)
     return float(np.percentile(xs, 50)), float(np.percentile(xs, 99))
@@ -334,6 +373,9 @@ def run_ours(args):
         p50, p99 = percentiles(lat)
         b50, b99 = percentiles(done_ms)
         s50, s99 = percentiles(service_ms)
+        if args.serving_seconds > 0:
+            extra["serving"] = serving_run(R, I, local, WORKLOAD["family"], args.serving_rate, args.serving_seconds,
+                                           WORKLOAD["iterations"])
         extra["latency_ms"] = {
             "single_instance_e2e": {"p50": p50, "p99": p99, "reps": args.latency_reps,
                                     "what": "1 instance, 100 iterations, load+search+results through the C API"},
@@ -390,6 +432,8 @@ def main():
     ap.add_argument("--group-size", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--tune-iterations", type=int, default=48)
+    ap.add_argument("--serving-seconds", type=float, default=5.0)
+    ap.add_argument("--serving-rate", type=float, default=2000.0)
     ap.add_argument("--plain-sample", type=int, default=48)
     ap.add_argument("--latency-reps", type=int, default=100)
     ap.add_argument("--cpu-sample", type=int, default=160)
