@@ -172,55 +172,68 @@ __device__ int decode_time(const SInst &I, const int *W, int u, int v, bool acti
         uint32_t rq[WPS];
 #pragma unroll
         for (int w = 0; w < WPS; ++w) rq[w] = I.reqw[i * WPS + w];
-        // Alg. 5: the first window [s, s+d), s >= es, whose steps all fit.
-        // A round tests R window offsets k..k+R-1 (offset k + lane + G*j in
-        // lane `lane`); a step that does not fit moves s past the highest
-        // such offset; steps at or after F always fit.
+        // Alg. 5: the first window [s, s+d), s >= es, whose steps all fit,
+        // read off bit masks.  [s, s+k) is known to fit; a round tests the R
+        // steps s+k .. s+k+R-1 (step s+k+lane+G*j in lane `lane`; steps at or
+        // after F always fit) and either finds the first run of d fitting
+        // steps, or keeps the trailing run of fitting steps as the new
+        // verified prefix -- the same window as Alg. 5's loadTime count.
         int s = es, k = 0;
         bool done = !active || d == 0;
         while (__any_sync(kFull, !done)) {
             if (!done && s + k >= F) done = true;
-            const int tlim = done ? INT_MIN : ::min(F, s + d);   // test t < tlim only
+            const int tlim = done ? INT_MIN : F;
             const int t0 = s + k + g.lane;
             const uint32_t *a0 = prof + t0 * NG;
-            int hb = -1;                                          // highest failing offset
-            if (G >= 16) {
-                unsigned bad = 0;
+            bool fit[U];
 #pragma unroll
-                for (int j = 0; j < U; ++j) {
-                    bool fit = true;
-                    if (t0 + G * j < tlim) {
+            for (int j = 0; j < U; ++j) {
+                fit[j] = true;
+                if (t0 + G * j < tlim) {
 #pragma unroll
-                        for (int w = 0; w < WPS; ++w) {
-                            const uint32_t x = a0[(w * ubs + G * j) * NG];
-                            fit = fit && (((x | hi) - rq[w]) & hi) == hi;
-                        }
-                    }
-                    bad |= g.bits(__ballot_sync(kFull, !fit)) << (G * j);
-                }
-                hb = bad ? 31 - __clz(bad) : -1;
-            } else {
-#pragma unroll
-                for (int j = 0; j < U; ++j) {
-                    if (t0 + G * j < tlim) {
-                        bool fit = true;
-#pragma unroll
-                        for (int w = 0; w < WPS; ++w) {
-                            const uint32_t x = a0[(w * ubs + G * j) * NG];
-                            fit = fit && (((x | hi) - rq[w]) & hi) == hi;
-                        }
-                        if (!fit) hb = g.lane + G * j;
+                    for (int w = 0; w < WPS; ++w) {
+                        const uint32_t x = a0[(w * ubs + G * j) * NG];
+                        fit[j] = fit[j] && (((x | hi) - rq[w]) & hi) == hi;
                     }
                 }
-                hb = g.max(hb);
+            }
+            unsigned x = 0;                                       // bit o: step s+k+o fits
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                if (G == 1) x |= static_cast<unsigned>(fit[j]) << j;
+                else x |= g.bits(__ballot_sync(kFull, fit[j])) << (G * j);
             }
             if (!done) {
-                if (hb >= 0) {
-                    s += k + hb + 1;
-                    k = 0;
+                const unsigned full = R == 32 ? 0xffffffffu : ((1u << R) - 1u);
+                const int need = d - k;                           // >= 1
+                const unsigned lowneed = need >= 32 ? 0xffffffffu : ((1u << need) - 1u);
+                if (need <= R && (x & lowneed) == lowneed) {
+                    done = true;                                  // [s, s+d) fits
+                } else if (x == full) {
+                    k += R;                                       // all fit, the window needs more
                 } else {
-                    k += R;
-                    if (k >= d) done = true;
+                    const int b = __ffs(~x) - 1;                  // first failing step of the round
+                    const int avail = R - b - 1;                  // steps after it in the round
+                    const unsigned xs = b + 1 >= 32 ? 0u : (x >> (b + 1));
+                    int w = -1;
+                    if (d <= avail) {
+                        unsigned y = xs;                          // y bit w: steps w..w+d-1 fit
+                        int len = 1;
+                        while (2 * len <= d) {
+                            y &= y >> len;
+                            len *= 2;
+                        }
+                        if (len < d) y &= y >> (d - len);
+                        if (y) w = __ffs(y) - 1;
+                    }
+                    if (w >= 0) {
+                        s += k + b + 1 + w;
+                        done = true;
+                    } else {
+                        const int h = 31 - __clz(~x & full);      // last failing step of the round
+                        s += k + h + 1;
+                        k = R - h - 1;
+                    }
                 }
             }
         }
