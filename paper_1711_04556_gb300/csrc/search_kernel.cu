@@ -298,18 +298,34 @@ __device__ int decode_capacity(const SInst &I, const int *W, int u, int v, bool 
                 // Alg. 4 as a per-index closed form of its result:
                 //   j <  r : c'[j] = max(c[j], s+d)
                 //   j >= r : c'[j] = c[j-r] <= s ? c[j] : max(c[j], min(c[j-r], s+d))
-                // Chunks go from the top so that c[j-r] is still old when read.
+                // c_k is non-increasing, so with a = #{j : c[j] > s} nothing at
+                // j >= r + a changes (there c[j-r] <= s).  a is found chunk by
+                // chunk; the update then runs from the top chunk down so that
+                // c[j-r] is still old when it is read.
                 const int R = I.cap[k];
                 int *ck = cst + I.cbase[k] * NG;
-                for (int J = ((R - 1) / G) * G; J >= 0; J -= G) {
+                int a = 0;
+                bool more = upd;
+                for (int J = 0; __any_sync(kFull, more); J += G) {
+                    const int j = J + g.lane;
+                    const bool above = more && j < R && ck[j * NG] > s;
+                    const unsigned m = g.bits(__ballot_sync(kFull, above));
+                    if (more) {
+                        a += __popc(m);
+                        more = m == (G == 32 ? 0xffffffffu : ((1u << G) - 1u)) && J + G < R;
+                    }
+                }
+                const int top = ::min(R, r + a);            // indices that can change: [0, top)
+                const int topmax = __reduce_max_sync(kFull, upd ? top : 0);
+                for (int J = ((topmax - 1) / G) * G; J >= 0; J -= G) {
                     const int j = J + g.lane;
                     int old = 0, prev = 0;
-                    if (upd && j < R) {
+                    if (upd && j < top) {
                         old = ck[j * NG];
                         if (j >= r) prev = ck[(j - r) * NG];
                     }
                     __syncwarp();
-                    if (upd && j < R) {
+                    if (upd && j < top) {
                         const int nv = j < r ? ::max(old, s + d)
                                              : (prev <= s ? old : ::max(old, ::min(prev, s + d)));
                         if (nv != old) {

@@ -54,13 +54,23 @@ def test_table1_decode(solver, oracle):
     solver.free(ids)
 
 
-@pytest.mark.parametrize("family", ["medium", "j30", "j120", "mixed"])
+def wide_instances(count, first=0):
+    """Demands up to 200, so capacities exceed 127 (16-bit profile fields); M in
+    {1, 2, 3, 5, 8} gives 1, 2 and 4 profile words per time step."""
+    ms = (1, 2, 3, 5, 8)
+    return [I.generate(s, 12 + s % 25, ms[s % 5], 150 + 30 * (s % 3), 20 + 40 * (s % 3),
+                       dmax=4 + s % 7, rmax=200, relabel=bool(s % 2), stream=31)
+            for s in range(first, first + count)]
+
+
+@pytest.mark.parametrize("family", ["medium", "j30", "j120", "mixed", "wide"])
 def test_decoders_on_random_lists(solver, oracle, family):
     rng = np.random.default_rng(17)
     insts = {"medium": medium_instances(24, first=900),
              "j30": I.config_batch("j30_batch", 12),
              "j120": I.config_batch("j120_batch", 4),
-             "mixed": I.config_batch("mixed_batch", 12)}[family]
+             "mixed": I.config_batch("mixed_batch", 12),
+             "wide": wide_instances(15)}[family]
     ids = solver.load(insts)
     for inst, i in zip(insts, ids):
         lists = np.stack([random_feasible_list(inst, rng) for _ in range(5)])
@@ -108,6 +118,19 @@ def test_j120_sample(solver, oracle, mode):
     ref = oracle.tabu_search_batch(insts, [(60, 60, 800, mode, 1)] * len(insts), NPROC, trace=True)
     for k, (g, r) in enumerate(zip(got, ref)):
         compare_search(oracle, g, r, solver.trace(ids[k], 60))
+    solver.free(ids)
+
+
+@pytest.mark.parametrize("mode", [R.EVAL_TIME, R.EVAL_CAPACITY])
+def test_wide_fields_search(solver, oracle, mode):
+    insts = wide_instances(10, first=40)
+    assert max(int(x.cap.max()) for x in insts) > 127
+    ids = solver.load(insts)
+    solver.search(ids, iterations=40, delta=8, tabu_len=15, mode=mode, trace=True)
+    got = solver.results(ids)
+    ref = oracle.tabu_search_batch(insts, [(40, 8, 15, mode, 1)] * len(insts), NPROC, trace=True)
+    for k, (g, r) in enumerate(zip(got, ref)):
+        compare_search(oracle, g, r, solver.trace(ids[k], 40))
     solver.free(ids)
 
 
