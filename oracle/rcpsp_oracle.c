@@ -32,11 +32,12 @@
  *   R7  Duplicate tabu-list entries follow Alg. 3 literally: evicting the
  *       older copy clears the cache entry.
  *   R8  The learned selection rules of Sec. 5.4 are not printed (Fig. 5 is
- *       lost).  The rule used: capacity-indexed iff the average capacity
- *       times SEL_K is below the average duration, SEL_K = SEL_KNUM/SEL_KDEN,
- *       compared exactly in integers (attributes of Table 3; direction from
- *       Sec. 7.2: capacity-indexed wins on long activities and small
- *       capacities).
+ *       lost).  The rule used keeps two attributes of Table 3, the critical
+ *       path length and the average capacity, and the direction of Sec. 7.2
+ *       (capacity-indexed for long schedules with low capacities):
+ *       capacity-indexed iff CP > SEL_K * avgCap, compared exactly as
+ *       CP * M > SEL_K * sum R_k.  SEL_K = 24 was fitted, as Sec. 5.4 does,
+ *       by timing both evaluators on a grid of instances on the target GPU.
  *   R9  "Evaluated schedules" counts neighbour decodes only (every feasible
  *       move, tabu or not); the initial and final decodes are not counted.
  */
@@ -48,8 +49,7 @@
 #include <string.h>
 
 /* Selection constant of reading R8. */
-#define SEL_KNUM 1
-#define SEL_KDEN 1
+#define SEL_K 24
 
 static int imax(int a, int b) { return a > b ? a : b; }
 
@@ -322,11 +322,11 @@ int orc_decode_capacity(const orc_instance *in, const int *W, int *S, long long 
 
 /* ---------------------- Sec. 5.4 selection (R8) ------------------------- */
 int orc_select_mode(const orc_instance *in) {
-    long long sumR = 0, sumD = 0;
+    long long sumR = 0;
     for (int k = 0; k < in->m; ++k) sumR += in->cap[k];
-    for (int i = 0; i < in->n; ++i) sumD += in->dur[i];
-    /* avgCap * K < avgDur  <=>  sumR * N * KNUM < sumD * M * KDEN */
-    return sumR * in->n * SEL_KNUM < sumD * in->m * SEL_KDEN ? ORC_CAPACITY : ORC_TIME;
+    const long long cp = orc_critical_path(in);
+    /* CP > K * avgCap  <=>  CP * M > K * sumR */
+    return cp * in->m > (long long)SEL_K * sumR ? ORC_CAPACITY : ORC_TIME;
 }
 
 /* --------------------------- Sec. 6 search ------------------------------ */

@@ -16,12 +16,14 @@ namespace rcpsp {
 namespace {
 
 // Selection rule (Sec. 5.4).  The learned JRip rules are not printed in the
-// paper (Fig. 5 is lost); the rule keeps their attributes (Table 3) and the
-// stated tendency (Sec. 7.2: capacity-indexed wins for long activities and
-// small capacities): capacity-indexed iff avgCap * K < avgDur, K = 1/1,
-// compared exactly as sumR * N * KNUM < sumD * M * KDEN.
-constexpr long long kSelKNum = 1;
-constexpr long long kSelKDen = 1;
+// paper (Fig. 5 is lost).  The rule keeps two attributes of Table 3 -- the
+// critical path length and the average capacity -- and the direction of
+// Sec. 7.2 (capacity-indexed for long schedules with low capacities):
+// capacity-indexed iff CP > K * avgCap, compared exactly as CP * M > K * sumR.
+// K = 24 was fitted by timing both evaluators on a grid of instances on
+// GB300 (selection_study.py), as Sec. 5.4 derives its classes from
+// measured run times.
+constexpr long long kSelK = 24;
 
 int fail(std::string &err, int code, const std::string &msg) {
     err = msg;
@@ -30,11 +32,10 @@ int fail(std::string &err, int code, const std::string &msg) {
 
 }  // namespace
 
-int select_evaluator(int n, int m, const int32_t *dur, const int32_t *cap) {
-    long long sum_r = 0, sum_d = 0;
+int select_evaluator(int m, const int32_t *cap, int critical_path) {
+    long long sum_r = 0;
     for (int k = 0; k < m; ++k) sum_r += cap[k];
-    for (int i = 0; i < n; ++i) sum_d += dur[i];
-    return sum_r * n * kSelKNum < sum_d * m * kSelKDen ? RCPSP_EVAL_CAPACITY : RCPSP_EVAL_TIME;
+    return static_cast<long long>(critical_path) * m > kSelK * sum_r ? RCPSP_EVAL_CAPACITY : RCPSP_EVAL_TIME;
 }
 
 int prepare_instance(const rcpsp_instance &in, PackedInstance &out, std::string &err) {
@@ -140,7 +141,7 @@ int prepare_instance(const rcpsp_instance &in, PackedInstance &out, std::string 
     h.m = m;
     h.ub = static_cast<int>(horizon);
     h.cp = es[n - 1];
-    h.sel_mode = select_evaluator(n, m, in.dur, in.cap);
+    h.sel_mode = select_evaluator(m, in.cap, es[n - 1]);
     h.wps = wps;
     h.lane_bits = lane_bits;
     h.sum_cap = 0;

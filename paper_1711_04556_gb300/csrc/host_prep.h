@@ -19,8 +19,9 @@ struct PackedInstance {
 // with a message in `err`.
 int prepare_instance(const rcpsp_instance &in, PackedInstance &out, std::string &err);
 
-// Evaluator chosen by the selection rule (Sec. 5.4).
-int select_evaluator(int n, int m, const int32_t *dur, const int32_t *cap);
+// Evaluator chosen by the selection rule (Sec. 5.4) from the capacities and
+// the critical-path length.
+int select_evaluator(int m, const int32_t *cap, int critical_path);
 
 // (delta, |tabuList|) by instance size (Table 2).
 void default_search_params(int n, int *delta, int *tabu_len);
