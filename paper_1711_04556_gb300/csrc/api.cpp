@@ -412,7 +412,8 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
         it.mode = p->eval_mode == RCPSP_EVAL_AUTO ? in.h.sel_mode : p->eval_mode;
         int dd, tl;
         rcpsp::default_search_params(in.h.n, &dd, &tl);
-        it.delta = p->max_swap_dist ? p->max_swap_dist : dd;
+        // v - u never exceeds N - 3, so a larger delta names the same moves
+        it.delta = std::max(1, std::min(p->max_swap_dist ? p->max_swap_dist : dd, in.h.n - 3));
         it.tabu_len = p->tabu_len ? p->tabu_len : tl;
         it.iterations = p->iterations;
         it.stop_at_cp = p->stop_at_cp ? 1 : 0;
@@ -595,7 +596,8 @@ int rcpsp_tabu_search_noalloc(rcpsp_ctx *c, const int32_t *ids, int32_t count, c
         it.mode = p->eval_mode == RCPSP_EVAL_AUTO ? in.h.sel_mode : p->eval_mode;
         int dd, tl;
         rcpsp::default_search_params(in.h.n, &dd, &tl);
-        it.delta = p->max_swap_dist ? p->max_swap_dist : dd;
+        // v - u never exceeds N - 3, so a larger delta names the same moves
+        it.delta = std::max(1, std::min(p->max_swap_dist ? p->max_swap_dist : dd, in.h.n - 3));
         it.tabu_len = p->tabu_len ? p->tabu_len : tl;
         it.iterations = p->iterations;
         it.stop_at_cp = p->stop_at_cp ? 1 : 0;
@@ -666,7 +668,8 @@ int rcpsp_autotune(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcpsp_
         it.mode = p->eval_mode == RCPSP_EVAL_AUTO ? in.h.sel_mode : p->eval_mode;
         int dd, tl;
         rcpsp::default_search_params(in.h.n, &dd, &tl);
-        it.delta = p->max_swap_dist ? p->max_swap_dist : dd;
+        // v - u never exceeds N - 3, so a larger delta names the same moves
+        it.delta = std::max(1, std::min(p->max_swap_dist ? p->max_swap_dist : dd, in.h.n - 3));
         it.tabu_len = p->tabu_len ? p->tabu_len : tl;
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);

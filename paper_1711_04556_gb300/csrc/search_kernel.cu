@@ -127,10 +127,11 @@ __device__ __forceinline__ int activity_at(const int *W, int p, int u, int v) {
     return p == u ? W[v] : (p == v ? W[u] : W[p]);
 }
 
-// es of every successor of i := max(es, f)
+// es of every successor of i := max(es, f); inactive groups write nothing.
 template <int G>
-__device__ __forceinline__ void push_finish(const SInst &I, int i, int f, int *es, int NG, const Group<G> &g) {
-    const int e0 = I.soff[i], ns = I.soff[i + 1] - e0;
+__device__ __forceinline__ void push_finish(const SInst &I, int i, int f, int *es, int NG, const Group<G> &g,
+                                            bool active) {
+    const int e0 = I.soff[i], ns = active ? I.soff[i + 1] - e0 : 0;
     for (int b = g.lane; b < ns; b += G) {
         int *x = es + I.slist[e0 + b] * NG;
         *x = ::max(*x, f);
@@ -255,11 +256,11 @@ __device__ int decode_time(const SInst &I, const int *W, int u, int v, bool acti
                 }
                 F = ::max(F, fe);
             }
-            push_finish<G>(I, i, f, esa, NG, g);
             if (S_out && g.lane == 0) S_out[i] = s;
             work += f - es;
             cmax = ::max(cmax, f);
         }
+        push_finish<G>(I, i, f, esa, NG, g, active);
         __syncwarp();
         i = inext;
     }
@@ -340,10 +341,10 @@ __device__ int decode_capacity(const SInst &I, const int *W, int u, int v, bool 
             if (upd) work += last + 1;                 // Alg. 4 stops after its last change
         }
         if (active) {
-            push_finish<G>(I, i, s + d, esa, NG, g);
             if (S_out && g.lane == 0) S_out[i] = s;
             cmax = ::max(cmax, s + d);
         }
+        push_finish<G>(I, i, s + d, esa, NG, g, active);
         __syncwarp();
         i = inext;
     }
@@ -464,6 +465,9 @@ __global__ void __launch_bounds__(512, 2) search_kernel(const LaunchItem *__rest
         }
         __syncthreads();
         const int nslots = n > 3 ? (n - 3) * delta : 0;
+        // slot / delta by a multiply-high: exact while slot * delta < 2^32,
+        // which holds because the host clamps delta to N - 3 (same moves)
+        const unsigned dmagic = delta > 1 ? 0xffffffffu / static_cast<unsigned>(delta) + 1u : 0u;
         long long my_work = 0;
         for (;;) {
             if (s_it >= it.iterations || (it.stop_at_cp && s_Cbest == h.cp)) break;
@@ -491,8 +495,9 @@ __global__ void __launch_bounds__(512, 2) search_kernel(const LaunchItem *__rest
                     int code = 0;
                     if (k < stripe) {
                         const int slot = base + k;
-                        const int u = 1 + slot / delta;
-                        const int v = u + 1 + slot % delta;
+                        const int q = delta > 1 ? static_cast<int>(__umulhi(static_cast<unsigned>(slot), dmagic)) : slot;
+                        const int u = 1 + q;
+                        const int v = u + 1 + (slot - q * delta);
                         if (v <= n - 2 && fsp[u] > v && lpp[v] < u) {
                             ok = true;
                             code = u | (v << 16);
