@@ -254,7 +254,8 @@ def run_ours(args):
     from paper_1711_04556_gb300 import instances as I
     from paper_1711_04556_gb300 import rcpsp as R
     B.build()
-    insts = I.config_batch(WORKLOAD["family"], WORKLOAD["count"], first=rank * WORKLOAD["count"])
+    from paper_1711_04556_gb300 import replicas
+    insts = replicas.shard(WORKLOAD["family"], WORKLOAD["count"], rank)
     solver = R.Solver(local)
     st = torch.cuda.Stream(device=dev)
     kw = dict(iterations=WORKLOAD["iterations"], delta=WORKLOAD["delta"], tabu_len=WORKLOAD["tabu_len"],
@@ -301,16 +302,7 @@ def run_ours(args):
     res = solver.results(ids)
     for a, b in zip(res, ref_res):   # every step reproduces the same searches
         assert a["best_cmax"] == b["best_cmax"] and a["evaluated"] == b["evaluated"]
-    dev_s = sum(step_ms) / 1000.0
-    if world > 1:
-        t = torch.tensor([dev_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_s = float(t.item())
-        e = torch.tensor([ev_step], dtype=torch.float64, device=dev)
-        dist.all_reduce(e, op=dist.ReduceOp.SUM)
-        ev_all = float(e.item())
-    else:
-        ev_all = float(ev_step)
+    dev_s, ev_all = replicas.reduce_timing(dist, dev, sum(step_ms) / 1000.0, float(ev_step), world)
     value = ev_all * args.steps / dev_s
 
     # in-batch solve latency from the device timestamps of the last step
@@ -333,13 +325,8 @@ def run_ours(args):
     barrier()
     t_e2e = time.perf_counter() - t_e2e
     h1, d1 = solver.transfer_bytes()
-    e2e_val = ev_e2e / t_e2e
-    if world > 1:
-        t = torch.tensor([t_e2e, ev_e2e], dtype=torch.float64, device=dev)
-        tm = t.clone()
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        e2e_val = float(t[1].item()) / float(tm[0].item())
+    t_e2e_max, ev_e2e_all = replicas.reduce_timing(dist, dev, t_e2e, float(ev_e2e), world)
+    e2e_val = ev_e2e_all / t_e2e_max
 
     extra = {}
     if rank == 0:
