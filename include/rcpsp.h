@@ -88,6 +88,10 @@ typedef struct {
     int32_t record_trace;       /* 1: keep (u, v, C) of every iteration          */
     int32_t use_graph;          /* 1: capture the launch in a CUDA graph and
                                    replay it on later identical calls            */
+    int32_t cluster_size;       /* CTAs that share one search (1, 2, 4, 8): they
+                                   split its neighbourhood and exchange the best
+                                   move through distributed shared memory;
+                                   0 = choose automatically                      */
 } rcpsp_params;
 
 /* Result statistics of one instance. */
@@ -137,12 +141,14 @@ int rcpsp_free_instances(rcpsp_ctx *ctx, const int32_t *ids, int32_t count);
 /* Runs one tabu search per listed instance (Sec. 6: neighbourhood of swap
  * moves with Eqs. 5-6 filtering, serial-SGS decoding with the chosen
  * evaluator, best admissible move under the simple tabu list (Algs. 2-3)
- * and the aspiration rule).  The searches are grouped by footprint class
- * (per-group scratch up to 2K, up to 8K, above 8K words); each class is one
- * persistent launch with its own shape, the first on `cuda_stream` (a
- * cudaStream_t; NULL = legacy default stream), the others on streams of the
- * context forked from it and joined back into it.  The call is
- * asynchronous.  Results stay on the device until rcpsp_get_schedules. */
+ * and the aspiration rule).  The searches are grouped into launch classes
+ * by footprint (per-group scratch up to 2K, up to 8K, above 8K words) and
+ * size (N up to 64, up to 160, larger); each class is one persistent launch
+ * with its own shape -- lanes per decode, warps per CTA, CTAs per search --
+ * the first on `cuda_stream` (a cudaStream_t; NULL = legacy default stream),
+ * the others on streams of the context forked from it and joined back into
+ * it.  The call is asynchronous.  Results stay on the device until
+ * rcpsp_get_schedules. */
 int rcpsp_tabu_search(rcpsp_ctx *ctx, const int32_t *ids, int32_t count,
                       const rcpsp_params *params, void *cuda_stream);
 
@@ -172,10 +178,11 @@ int rcpsp_tabu_search_noalloc(rcpsp_ctx *ctx, const int32_t *ids, int32_t count,
  * every shape that fits, and keeps the fastest (neighbours decoded per
  * second) in the context under the workload's signature (largest N, horizon,
  * words per step, swap distance, evaluator mix, batch size).  Instances are
- * tuned per footprint class (per-group scratch up to 2K, up to 8K, above
- * 8K words), the unit a search launches apart; the returned shape is the
+ * tuned per launch class (see rcpsp_tabu_search), the unit a search launches
+ * apart; classes with at most half as many searches as the GPU has SMs also
+ * try clusters of 2, 4 and 8 CTAs per search.  The returned shape is the
  * one of the largest class.  Later searches with group_size =
- * warps_per_cta = 0 and the same signature use it.  The
+ * warps_per_cta = cluster_size = 0 and the same signature use it.  The
  * trials overwrite the instances' results.  Synchronous.  The shape is the
  * GPU's own split of the neighbourhood (Sec. 6 parallelises it over the
  * threads of a block); the paper fixes it by hand (Sec. 7). */

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cstdlib>
 #include <cstring>
@@ -45,6 +46,9 @@ struct Inst {
 
 int out_words(int n) { return rcpsp::align4(2 * n + rcpsp::kOutStats); }
 
+constexpr int kClasses = 9;                  // launch classes of one call (see footprint_class)
+constexpr int kAuxStreams = kClasses - 1;
+
 }  // namespace
 
 struct rcpsp_ctx {
@@ -69,11 +73,11 @@ struct rcpsp_ctx {
     std::vector<LaunchItem> noalloc_plan;   // host copy of the last no-allocation plan
     // footprint classes beyond the first run on their own streams, forked
     // from and joined back to the caller's stream
-    cudaStream_t aux[2] = {nullptr, nullptr};
-    cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
+    cudaStream_t aux[kAuxStreams] = {};
+    cudaEvent_t fork = nullptr, join[kAuxStreams] = {};
     std::vector<int> g_launch_sig;
-    // measured launch shapes: workload signature -> (G, warps)
-    std::vector<std::pair<std::string, std::pair<int, int>>> tuned;
+    // measured launch shapes: workload signature -> (G, warps, CTAs per search)
+    std::vector<std::pair<std::string, std::array<int, 3>>> tuned;
 };
 
 namespace {
@@ -155,21 +159,37 @@ size_t smem_bytes(const std::vector<LaunchItem> &items, int ngroups, int move_ca
     return static_cast<size_t>(words) * 4;
 }
 
-// Footprint class of a search: per-group scratch words (profile or capacity
-// state plus N earliest starts) up to 2K, up to 8K, or more.  Each class of
-// a call gets its own launch shape, so that small instances are not run at
-// the group count the largest instance allows.
-constexpr int kClasses = 3;
+// Launch class of a search: its footprint -- per-group scratch words (profile
+// or capacity state plus N earliest starts) up to 2K, up to 8K, or more --
+// times its size (N up to 64, up to 160, larger).  Each class of a call gets
+// its own launch shape, so that small instances are not run at the group
+// count the largest one allows, and a few large searches can share clusters
+// of CTAs while many small ones take one CTA each.
 
 int footprint_class(const LaunchItem &it) {
     const int gw = rcpsp::profile_words(it.mode, it.h.wps, it.h.ub, it.h.sum_cap) + it.h.n;
-    return gw <= 2048 ? 0 : (gw <= 8192 ? 1 : 2);
+    const int fp = gw <= 2048 ? 0 : (gw <= 8192 ? 1 : 2);
+    const int sz = it.h.n <= 64 ? 0 : (it.h.n <= 160 ? 1 : 2);
+    return fp * 3 + sz;
 }
 
 struct ClassLaunch {
-    int offset = 0, count = 0, G = 0, threads = 0, blocks = 0, move_cap = 0;
+    int offset = 0, count = 0, G = 0, threads = 0, blocks = 0, move_cap = 0, csize = 1;
     size_t smem = 0;
 };
+
+// CTAs that share one search: 1 unless the class has few searches for the
+// GPU and each has a large neighbourhood.
+int default_cluster(const std::vector<LaunchItem> &items, int sms) {
+    const int cnt = static_cast<int>(items.size());
+    double feas = 0;
+    for (const LaunchItem &it : items) feas += it.h.n > 3 ? 0.12 * (it.h.n - 3) * it.delta : 0.0;
+    feas /= std::max(1, cnt);
+    if (cnt * 4 > sms || feas < 128) return 1;
+    int c = 1;
+    while (c < 8 && cnt * c * 2 <= sms) c *= 2;
+    return c;
+}
 
 // Workload signature of a launch plan for the shape table: largest N, time
 // horizon in 64-step buckets, words per step, swap distance, evaluator mix,
@@ -189,11 +209,12 @@ std::string shape_key(const std::vector<LaunchItem> &items) {
            std::to_string(dl) + (tm ? "_T" : "") + (cap ? "_C" : "") + "_b" + std::to_string(lg);
 }
 
-bool tuned_shape(const rcpsp_ctx *c, const std::string &key, int *G, int *warps) {
+bool tuned_shape(const rcpsp_ctx *c, const std::string &key, int *G, int *warps, int *csize = nullptr) {
     for (const auto &e : c->tuned)
         if (e.first == key) {
-            *G = e.second.first;
-            *warps = e.second.second;
+            *G = e.second[0];
+            *warps = e.second[1];
+            if (csize) *csize = e.second[2];
             return true;
         }
     return false;
@@ -235,7 +256,7 @@ int rcpsp_create(rcpsp_ctx **ctx, int device, const rcpsp_allocator *alloc) {
     if (e == cudaSuccess) e = cudaGetDeviceProperties(&c->prop, device);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming);
-    for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
+    for (int q = 0; q < kAuxStreams && e == cudaSuccess; ++q) {
         e = cudaStreamCreateWithFlags(&c->aux[q], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join[q], cudaEventDisableTiming);
     }
@@ -243,7 +264,7 @@ int rcpsp_create(rcpsp_ctx **ctx, int device, const rcpsp_allocator *alloc) {
         delete c;
         return RCPSP_E_CUDA;
     }
-    c->queue_dev = static_cast<int *>(dev_alloc(c, 16, nullptr));
+    c->queue_dev = static_cast<int *>(dev_alloc(c, 64, nullptr));          // one counter per class
     if (!c->queue_dev) {
         cudaEventDestroy(c->done);
         delete c;
@@ -262,11 +283,11 @@ int rcpsp_destroy(rcpsp_ctx *c) {
     for (Inst &in : c->insts) dev_free(c, in.trace, in.trace_bytes, nullptr);
     for (Block &b : c->blocks) dev_free(c, b.ptr, b.bytes, nullptr);
     dev_free(c, c->items_dev, c->items_cap, nullptr);
-    dev_free(c, c->queue_dev, 16, nullptr);
+    dev_free(c, c->queue_dev, 64, nullptr);
     if (c->items_host) cudaFreeHost(c->items_host);
     cudaEventDestroy(c->done);
     cudaEventDestroy(c->fork);
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < kAuxStreams; ++q) {
         if (c->aux[q]) cudaStreamDestroy(c->aux[q]);
         if (c->join[q]) cudaEventDestroy(c->join[q]);
     }
@@ -390,6 +411,9 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
     const int gs = p->group_size;
     if (gs != 0 && gs != 1 && gs != 2 && gs != 4 && gs != 8 && gs != 16 && gs != 32)
         return set_err(c, RCPSP_E_INVALID_ARG, "group_size must be 0, 1, 2, 4, 8, 16 or 32");
+    const int cs = p->cluster_size;
+    if (cs != 0 && cs != 1 && cs != 2 && cs != 4 && cs != 8)
+        return set_err(c, RCPSP_E_INVALID_ARG, "cluster_size must be 0, 1, 2, 4 or 8");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (p->use_graph && st == nullptr)
         return set_err(c, RCPSP_E_INVALID_ARG, "graph capture needs a non-default stream");
@@ -450,11 +474,12 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
         L.count = static_cast<int>(part.size());
         sorted.insert(sorted.end(), part.begin(), part.end());
         int G = gs, warps = p->warps_per_cta;
-        int dG, dW;
+        int dG, dW, dC = default_cluster(part, c->prop.multiProcessorCount);
         default_shape(part, &dG, &dW);
-        if (!gs && !warps) tuned_shape(c, shape_key(part), &dG, &dW);
+        if (!gs && !warps) tuned_shape(c, shape_key(part), &dG, &dW, &dC);
         if (!G) G = dG;
         if (!warps) warps = std::max(dW, (G + 31) / 32);
+        L.csize = cs ? cs : dC;
         L.move_cap = launch_move_cap(part);
         size_t smem = smem_bytes(part, warps * (32 / G), L.move_cap);
         while (smem > smem_limit && p->warps_per_cta == 0 && warps > 1) {
@@ -469,16 +494,17 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
         // the limit belongs to the kernel of this G, shared by every class that uses it
         cudaError_t e = rcpsp::prepare_search(G, smem_limit);
         if (e != cudaSuccess) return cuda_err(c, e, "kernel attributes");
-        int per_sm = 0;
-        e = rcpsp::search_occupancy(G, L.threads, smem, &per_sm);
+        int units = 0;
+        e = rcpsp::search_occupancy(G, L.threads, smem, L.csize, &units);
         if (e != cudaSuccess) return cuda_err(c, e, "occupancy");
-        if (per_sm < 1) return set_err(c, RCPSP_E_TOO_LARGE, "launch shape does not fit on an SM");
-        L.blocks = std::max(1, std::min(L.count, per_sm * c->prop.multiProcessorCount));
+        if (units < 1) return set_err(c, RCPSP_E_TOO_LARGE, "launch shape does not fit on the GPU");
+        L.blocks = L.csize == 1 ? std::max(1, std::min(L.count, units * c->prop.multiProcessorCount))
+                                : L.csize * std::max(1, std::min(L.count, units));
         launches.push_back(L);
     }
     std::vector<int> sig;
     for (const ClassLaunch &L : launches)
-        sig.insert(sig.end(), {L.offset, L.count, L.G, L.threads, L.blocks, L.move_cap, static_cast<int>(L.smem)});
+        sig.insert(sig.end(), {L.offset, L.count, L.G, L.threads, L.blocks, L.move_cap, static_cast<int>(L.smem), L.csize});
     // device copy of the plan
     cudaError_t e = cudaSuccess;
     const size_t ibytes = sizeof(LaunchItem) * count;
@@ -519,7 +545,7 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
             cudaStream_t sq = q == 0 ? s0 : c->aux[q - 1];
             if (q > 0 && (r = cudaStreamWaitEvent(sq, c->fork, 0)) != cudaSuccess) return r;
             r = rcpsp::launch_search(L.G, c->items_dev + L.offset, L.count, c->queue_dev + q, L.move_cap, L.blocks,
-                                     L.threads, L.smem, sq);
+                                     L.threads, L.smem, sq, L.csize);
             if (r != cudaSuccess) return r;
             if (q > 0 && (r = cudaEventRecord(c->join[q - 1], sq)) != cudaSuccess) return r;
         }
@@ -632,14 +658,14 @@ int rcpsp_tabu_search_noalloc(rcpsp_ctx *c, const int32_t *ids, int32_t count, c
     e = rcpsp::prepare_search(G, smem);
     if (e != cudaSuccess) return cuda_err(c, e, "kernel attributes");
     int per_sm = 0;
-    e = rcpsp::search_occupancy(G, threads, smem, &per_sm);
+    e = rcpsp::search_occupancy(G, threads, smem, 1, &per_sm);
     if (e != cudaSuccess) return cuda_err(c, e, "occupancy");
     if (per_sm < 1) return set_err(c, RCPSP_E_TOO_LARGE, "launch shape does not fit on an SM");
     const int blocks = std::max(1, std::min(count, per_sm * c->prop.multiProcessorCount));
     const size_t ibytes = sizeof(LaunchItem) * count;
     e = cudaMemcpyAsync(plan, c->noalloc_plan.data(), ibytes, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(queue, 0, sizeof(int), st);      // the counter starts at 0
-    if (e == cudaSuccess) e = rcpsp::launch_search(G, plan, count, queue, move_cap, blocks, threads, smem, st);
+    if (e == cudaSuccess) e = rcpsp::launch_search(G, plan, count, queue, move_cap, blocks, threads, smem, st, 1);
     if (e != cudaSuccess) return cuda_err(c, e, "no-allocation search launch");
     c->h2d += static_cast<long long>(ibytes);
     e = cudaEventRecord(c->done, st);
@@ -695,16 +721,21 @@ int rcpsp_autotune(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcpsp_
         const std::string key = shape_key(part);
         std::vector<rcpsp_stats> stats(cn);
         double best_rate = -1.0;
-        int bG = 0, bW = 0;
+        int bG = 0, bW = 0, bC = 1;
         const int gsz[] = {1, 2, 4, 8, 16, 32};
         const int wcnt[] = {1, 2, 3, 4, 6, 8, 12, 16};
+        // clusters only pay when the class has fewer searches than the GPU has SMs
+        const int cmax = 2 * cn <= c->prop.multiProcessorCount ? 8 : 1;
+        for (int C = 1; C <= cmax; C *= 2)
         for (int G : gsz)
             for (int W : wcnt) {
                 const int ng = W * (32 / G);
                 const int min_groups = cls == 0 ? 8 : (cls == 1 ? 2 : 1);   // large states fit few groups
                 if (ng < min_groups || ng > 256) continue;
+                if (C > 1 && (G < 4 || W < 4)) continue;                     // fewer trials for clusters
                 q.group_size = G;
                 q.warps_per_cta = W;
+                q.cluster_size = C;
                 cudaEventRecord(e0, st);
                 int r = rcpsp_tabu_search(c, cids.data(), cn, &q, stream);
                 if (r == RCPSP_E_TOO_LARGE) continue;             // shape does not fit
@@ -727,6 +758,7 @@ int rcpsp_autotune(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcpsp_
                     best_rate = rate;
                     bG = G;
                     bW = W;
+                    bC = C;
                 }
             }
         if (!bG) {
@@ -737,10 +769,10 @@ int rcpsp_autotune(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcpsp_
         bool found = false;
         for (auto &e : c->tuned)
             if (e.first == key) {
-                e.second = {bG, bW};
+                e.second = {bG, bW, bC};
                 found = true;
             }
-        if (!found) c->tuned.push_back({key, {bG, bW}});
+        if (!found) c->tuned.push_back({key, {bG, bW, bC}});
         if (cn > ret_count) {
             ret_count = cn;
             ret_G = bG;

@@ -26,6 +26,7 @@
 //
 // The kernel never spins: the work queue is a single atomicAdd.  Internal
 // inconsistencies set an error word that the host reads as a status.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <limits.h>
 #include <stdint.h>
@@ -35,6 +36,8 @@
 
 namespace rcpsp {
 namespace {
+
+namespace cg = cooperative_groups;
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kErrHorizon = 1;     // a profile window ran past UB
@@ -398,15 +401,22 @@ __device__ __forceinline__ void tc_put(unsigned *tc, int u, int v, int delta, bo
 }
 
 // ---------------------------------------------------------------------------
-// Persistent search kernel.
+// Persistent search kernel.  With csize > 1 it runs as clusters of csize
+// CTAs, one search per cluster: every CTA holds the same search state,
+// examines its share of the potential moves (chunks of 32 slots, round
+// robin over the cluster ranks), finds its best admissible key, and after a
+// cluster barrier reads the other CTAs' keys through distributed shared
+// memory; all CTAs then apply the same move.  Rank 0 pops the work queue,
+// sums the counters and writes the results.
 // ---------------------------------------------------------------------------
 template <int G>
 __global__ void __launch_bounds__(512, 2) search_kernel(const LaunchItem *__restrict__ items, int count,
-                                                      int *__restrict__ queue, int move_cap) {
+                                                      int *__restrict__ queue, int move_cap, int csize) {
     extern __shared__ __align__(16) int sm[];
     __shared__ int s_item, s_nmoves, s_C, s_Cbest, s_widx, s_it, s_improved, s_err;
-    __shared__ unsigned long long s_best, s_t0;
+    __shared__ unsigned long long s_bestp[2], s_t0;      // best key of the iteration, by parity
     __shared__ long long s_eval, s_work;
+    const unsigned crank = csize > 1 ? cg::this_cluster().block_rank() : 0u;
 
     constexpr int NG = 32 / G;
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -416,9 +426,16 @@ __global__ void __launch_bounds__(512, 2) search_kernel(const LaunchItem *__rest
     const Group<G> g;
 
     for (;;) {
-        if (tid == 0) s_item = atomicAdd(queue, 1);
-        __syncthreads();
-        const int item = s_item;
+        if (tid == 0 && crank == 0) s_item = atomicAdd(queue, 1);
+        int item;
+        if (csize > 1) {
+            cg::this_cluster().sync();
+            item = *cg::this_cluster().map_shared_rank(&s_item, 0);
+            cg::this_cluster().sync();                      // read before rank 0 pops again
+        } else {
+            __syncthreads();
+            item = s_item;
+        }
         if (item >= count) break;
         const LaunchItem it = items[item];
         const InstHeader &h = it.h;
@@ -480,7 +497,8 @@ __global__ void __launch_bounds__(512, 2) search_kernel(const LaunchItem *__rest
                 fsp[p] = f;
                 lpp[p] = l;
             }
-            if (tid == 0) s_best = ~0ull;
+            const int par = s_it & 1;
+            if (tid == 0) s_bestp[par] = ~0ull;
             __syncthreads();
             const int cbest = s_Cbest;
             unsigned long long my_key = ~0ull;
@@ -498,7 +516,8 @@ __global__ void __launch_bounds__(512, 2) search_kernel(const LaunchItem *__rest
                         const int q = delta > 1 ? static_cast<int>(__umulhi(static_cast<unsigned>(slot), dmagic)) : slot;
                         const int u = 1 + q;
                         const int v = u + 1 + (slot - q * delta);
-                        if (v <= n - 2 && fsp[u] > v && lpp[v] < u) {
+                        const bool mine = csize == 1 || static_cast<unsigned>((slot >> 5) % csize) == crank;
+                        if (mine && v <= n - 2 && fsp[u] > v && lpp[v] < u) {
                             ok = true;
                             code = u | (v << 16);
                         }
@@ -529,13 +548,19 @@ __global__ void __launch_bounds__(512, 2) search_kernel(const LaunchItem *__rest
                 if (tid == 0) s_eval += nm;
                 __syncthreads();
             }
-            // 4. best admissible move of the block
+            // 4. best admissible move of the block, then of the cluster
             const unsigned long long wk = warp_min_u64(my_key);
-            if (wl == 0 && wk != ~0ull) atomicMin(&s_best, wk);
-            __syncthreads();
-            // 5. apply, Alg. 3
+            if (wl == 0 && wk != ~0ull) atomicMin(&s_bestp[par], wk);
+            if (csize > 1) cg::this_cluster().sync();
+            else __syncthreads();
+            // 5. apply, Alg. 3 (every CTA of a cluster applies the same move)
             if (tid == 0) {
-                const unsigned long long kb = s_best;
+                unsigned long long kb = s_bestp[par];
+                for (int r = 1; r < csize; ++r) {
+                    const unsigned long long o = *cg::this_cluster().map_shared_rank(&s_bestp[par],
+                                                                                  (crank + r) % csize);
+                    kb = o < kb ? o : kb;
+                }
                 int bu = 0, bv = 0;
                 s_improved = 0;
                 if (kb != ~0ull) {
@@ -558,7 +583,7 @@ __global__ void __launch_bounds__(512, 2) search_kernel(const LaunchItem *__rest
                 stl[s_widx] = bu | (bv << 16);
                 if (bu | bv) tc_put(tc, bu, bv, delta, true);
                 s_widx = s_widx + 1 == tl ? 0 : s_widx + 1;
-                if (it.trace) {
+                if (it.trace && crank == 0) {
                     it.trace[3 * s_it + 0] = bu;
                     it.trace[3 * s_it + 1] = bv;
                     it.trace[3 * s_it + 2] = s_C;
@@ -574,8 +599,21 @@ __global__ void __launch_bounds__(512, 2) search_kernel(const LaunchItem *__rest
         if (wl == 0) atomicAdd(reinterpret_cast<unsigned long long *>(&s_work), static_cast<unsigned long long>(ws));
         if (err) atomicOr(&s_err, err);
         __syncthreads();
-        // outputs: W*, its schedule S*, statistics
+        if (csize > 1) {
+            // rank 0 adds up the cluster's counters; the other CTAs go on to
+            // the next queue pop, which waits for rank 0
+            cg::this_cluster().sync();
+            if (crank == 0 && tid == 0)
+                for (int r = 1; r < csize; ++r) {
+                    s_eval += *cg::this_cluster().map_shared_rank(&s_eval, r);
+                    s_work += *cg::this_cluster().map_shared_rank(&s_work, r);
+                    s_err |= *cg::this_cluster().map_shared_rank(&s_err, r);
+                }
+            __syncthreads();
+        }
+        // outputs: W*, its schedule S*, statistics (rank 0)
         int32_t *out = it.out;
+        if (crank == 0) {
         if (warp == 0) {
             long long w1 = 0;
             int e1 = 0;
@@ -603,6 +641,7 @@ __global__ void __launch_bounds__(512, 2) search_kernel(const LaunchItem *__rest
             st[kOutT0Hi] = static_cast<int32_t>(s_t0 >> 32);
             st[kOutT1Lo] = static_cast<int32_t>(t1 & 0xffffffffull);
             st[kOutT1Hi] = static_cast<int32_t>(t1 >> 32);
+        }
         }
         __syncthreads();
     }
@@ -662,15 +701,42 @@ cudaError_t prepare_search_g(size_t smem) {
 }
 
 template <int G>
-cudaError_t occupancy_g(int threads, size_t smem, int *ctas) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, search_kernel<G>, threads, smem);
+cudaError_t occupancy_g(int threads, size_t smem, int csize, int *units) {
+    if (csize <= 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(units, search_kernel<G>, threads, smem);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(csize);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = csize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaOccupancyMaxActiveClusters(units, search_kernel<G>, &cfg);
 }
 
 template <int G>
 cudaError_t launch_search_g(const LaunchItem *items, int count, int *queue, int move_cap, int blocks,
-                            int threads, size_t smem, cudaStream_t st) {
-    search_kernel<G><<<blocks, threads, smem, st>>>(items, count, queue, move_cap);
-    return cudaGetLastError();
+                            int threads, size_t smem, cudaStream_t st, int csize) {
+    if (csize <= 1) {
+        search_kernel<G><<<blocks, threads, smem, st>>>(items, count, queue, move_cap, 1);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = csize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, search_kernel<G>, items, count, queue, move_cap, csize);
 }
 
 template <int G>
@@ -701,21 +767,14 @@ cudaError_t prepare_search(int group_size, size_t smem) {
     RCPSP_DISPATCH_G(group_size, return prepare_search_g<GG>(smem))
 }
 
-cudaError_t search_occupancy(int group_size, int threads, size_t smem, int *ctas) {
-    RCPSP_DISPATCH_G(group_size, return occupancy_g<GG>(threads, smem, ctas))
+cudaError_t search_occupancy(int group_size, int threads, size_t smem, int csize, int *units) {
+    RCPSP_DISPATCH_G(group_size, return occupancy_g<GG>(threads, smem, csize, units))
 }
 
 cudaError_t launch_search(int group_size, const LaunchItem *items, int count, int *queue, int move_cap,
-                          int blocks, int threads, size_t smem, cudaStream_t st) {
-    switch (group_size) {
-        case 1: return launch_search_g<1>(items, count, queue, move_cap, blocks, threads, smem, st);
-        case 2: return launch_search_g<2>(items, count, queue, move_cap, blocks, threads, smem, st);
-        case 4: return launch_search_g<4>(items, count, queue, move_cap, blocks, threads, smem, st);
-        case 8: return launch_search_g<8>(items, count, queue, move_cap, blocks, threads, smem, st);
-        case 16: return launch_search_g<16>(items, count, queue, move_cap, blocks, threads, smem, st);
-        case 32: return launch_search_g<32>(items, count, queue, move_cap, blocks, threads, smem, st);
-        default: return cudaErrorInvalidValue;
-    }
+                          int blocks, int threads, size_t smem, cudaStream_t st, int csize) {
+    RCPSP_DISPATCH_G(group_size,
+                     return launch_search_g<GG>(items, count, queue, move_cap, blocks, threads, smem, st, csize))
 }
 
 cudaError_t launch_evaluate(int group_size, const LaunchItem &item, const int32_t *lists, int count,

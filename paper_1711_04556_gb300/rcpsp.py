@@ -41,7 +41,8 @@ class Instance(C.Structure):
 class Params(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("max_swap_dist", C.c_int32), ("tabu_len", C.c_int32),
                 ("eval_mode", C.c_int32), ("stop_at_cp", C.c_int32), ("group_size", C.c_int32),
-                ("warps_per_cta", C.c_int32), ("record_trace", C.c_int32), ("use_graph", C.c_int32)]
+                ("warps_per_cta", C.c_int32), ("record_trace", C.c_int32), ("use_graph", C.c_int32),
+                ("cluster_size", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -230,11 +231,11 @@ class Solver:
 
     def search(self, ids, iterations: int = 100, delta: int = 0, tabu_len: int = 0, mode: int = EVAL_AUTO,
                stop_at_cp: bool = True, group_size: int = 0, warps_per_cta: int = 0, trace: bool = False,
-               use_graph: bool = False, stream=None):
+               use_graph: bool = False, stream=None, cluster_size: int = 0):
         """Asynchronous search on ``stream`` (a torch.cuda.Stream, a raw handle or None)."""
         ids = _i32(ids)
         p = Params(iterations, delta, tabu_len, mode, int(stop_at_cp), group_size, warps_per_cta,
-                   int(trace), int(use_graph))
+                   int(trace), int(use_graph), cluster_size)
         handle = getattr(stream, "cuda_stream", stream) or None
         self._check(self.lib.rcpsp_tabu_search(self.ctx, _ptr(ids), len(ids), C.byref(p), handle))
 
@@ -243,7 +244,7 @@ class Solver:
                        warps_per_cta: int = 0, stream=None):
         """rcpsp_tabu_search_noalloc: the search without any device allocation."""
         ids = _i32(ids)
-        p = Params(iterations, delta, tabu_len, mode, int(stop_at_cp), group_size, warps_per_cta, 0, 0)
+        p = Params(iterations, delta, tabu_len, mode, int(stop_at_cp), group_size, warps_per_cta, 0, 0, 1)
         handle = getattr(stream, "cuda_stream", stream) or None
         self._check(self.lib.rcpsp_tabu_search_noalloc(self.ctx, _ptr(ids), len(ids), C.byref(p), handle))
 
@@ -251,7 +252,7 @@ class Solver:
                  stop_at_cp: bool = True, trial_iterations: int = 48, stream=None):
         """rcpsp_autotune: times trial searches of every launch shape; returns (group_size, warps)."""
         ids = _i32(ids)
-        p = Params(iterations, delta, tabu_len, mode, int(stop_at_cp), 0, 0, 0, 0)
+        p = Params(iterations, delta, tabu_len, mode, int(stop_at_cp), 0, 0, 0, 0, 0)
         g, w = C.c_int32(0), C.c_int32(0)
         handle = getattr(stream, "cuda_stream", stream) or None
         self._check(self.lib.rcpsp_autotune(self.ctx, _ptr(ids), len(ids), C.byref(p), trial_iterations, handle,
@@ -318,7 +319,7 @@ class Server:
     def submit(self, inst, tag: int, iterations: int = 1000, delta: int = 0, tabu_len: int = 0,
                mode: int = EVAL_AUTO, stop_at_cp: bool = True, level_key=None) -> None:
         m = _Marshalled(inst, level_key)
-        p = Params(iterations, delta, tabu_len, mode, int(stop_at_cp), 0, 0, 0, 0)
+        p = Params(iterations, delta, tabu_len, mode, int(stop_at_cp), 0, 0, 0, 0, 0)
         rc = self.lib.rcpsp_server_submit(self.srv, C.byref(m.s), C.byref(p), int(tag))
         if rc != 0:
             raise RcpspError(rc, "submit")

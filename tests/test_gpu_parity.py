@@ -163,6 +163,30 @@ def test_autotuned_shape_keeps_results(solver, oracle):
     solver.free(ids)
 
 
+@pytest.mark.parametrize("csize", [2, 4, 8])
+def test_cluster_split_search(solver, oracle, csize):
+    """One search per cluster of CTAs: neighbourhood split, keys exchanged
+    through distributed shared memory; results unchanged."""
+    single = I.config_batch("j30_single")
+    j120 = I.config_batch("j120_batch", 6, first=30)
+    mixed = [x for x in I.config_batch("mixed_batch", 24) if x.n <= 122][:6]
+    for insts, it, dl, tl, mode in ((single, 100, 20, 60, R.EVAL_TIME), (j120, 30, 60, 800, R.EVAL_AUTO),
+                                    (j120, 30, 60, 800, R.EVAL_CAPACITY), (mixed, 10, 0, 0, R.EVAL_AUTO)):
+        ids = solver.load(insts)
+        solver.search(ids, iterations=it, delta=dl, tabu_len=tl, mode=mode, cluster_size=csize, trace=True)
+        got = solver.results(ids)
+        params = []
+        for x in insts:
+            a = x.n - 2
+            d_, t_ = (dl, tl) if dl else ((20, 60) if a <= 45 else (60, 250) if a <= 75 else (60, 600) if a <= 105
+                                          else (60, 800))
+            params.append((it, d_, t_, mode, 1))
+        ref = oracle.tabu_search_batch(insts, params, NPROC, trace=True)
+        for k, (g, r) in enumerate(zip(got, ref)):
+            compare_search(oracle, g, r, solver.trace(ids[k], it))
+        solver.free(ids)
+
+
 # -------------------------------------------------------------- edge cases
 def test_edge_cases(solver, oracle):
     base = medium_instances(1, first=1000)[0]
