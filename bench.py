@@ -361,8 +361,8 @@ def run_ours(args):
         b50, b99 = percentiles(done_ms)
         s50, s99 = percentiles(service_ms)
         if args.serving_seconds > 0:
-            extra["serving"] = serving_run(R, I, local, WORKLOAD["family"], args.serving_rate, args.serving_seconds,
-                                           WORKLOAD["iterations"])
+            extra["serving"] = serving_run(R, I, local, args.serving_family, args.serving_rate, args.serving_seconds,
+                                           args.serving_iterations, drain_s=args.serving_drain)
         extra["latency_ms"] = {
             "single_instance_e2e": {"p50": p50, "p99": p99, "reps": args.latency_reps,
                                     "what": "1 instance, 100 iterations, load+search+results through the C API"},
@@ -421,6 +421,11 @@ def main():
     ap.add_argument("--tune-iterations", type=int, default=48)
     ap.add_argument("--serving-seconds", type=float, default=5.0)
     ap.add_argument("--serving-rate", type=float, default=2000.0)
+    ap.add_argument("--serving-family", default=WORKLOAD["family"])
+    ap.add_argument("--serving-iterations", type=int, default=WORKLOAD["iterations"])
+    ap.add_argument("--serving-drain", type=float, default=30.0)
+    ap.add_argument("--serving-only", action="store_true",
+                    help="run only the serving measurement and print its JSON object")
     ap.add_argument("--plain-sample", type=int, default=48)
     ap.add_argument("--latency-reps", type=int, default=100)
     ap.add_argument("--cpu-sample", type=int, default=160)
@@ -429,6 +434,17 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.serving_only:
+        import torch
+        from paper_1711_04556_gb300 import build as B
+        from paper_1711_04556_gb300 import instances as I
+        from paper_1711_04556_gb300 import rcpsp as R
+        B.build()
+        torch.cuda.init()
+        print(json.dumps({"serving": serving_run(R, I, 0, args.serving_family, args.serving_rate,
+                                                 args.serving_seconds, args.serving_iterations,
+                                                 drain_s=args.serving_drain)}), flush=True)
+        return 0
     return run_reference(args) if args.impl == "reference" else run_ours(args)
 
 
