@@ -209,7 +209,7 @@ def serving_run(R, I, device, family, rate, seconds, iterations, pool_size=512, 
     arrivals = np.cumsum(gaps)
     arrivals = arrivals[arrivals < seconds]
     done = []
-    with R.Server(device, slots=4, max_batch=256, memory_budget=2 << 30) as srv:
+    with R.Server(device, slots=8, max_batch=256, memory_budget=2 << 30) as srv:
         t0 = time.perf_counter()
         k = 0
         while True:

@@ -237,8 +237,11 @@ int rcpsp_transfer_bytes(const rcpsp_ctx *ctx, int64_t *h2d, int64_t *d2h);
 typedef struct rcpsp_server rcpsp_server;
 
 typedef struct {
-    int32_t slots;              /* batches in flight (one stream each), 1..16; 0 = 4 */
-    int32_t max_batch;          /* requests per batch; 0 = 256                      */
+    int32_t slots;              /* batches in flight (one stream each), 1..16; 0 = 8 */
+    int32_t max_batch;          /* most requests per batch; 0 = 256.  A batch holds
+                                   one launch class (footprint x size, see
+                                   rcpsp_tabu_search) and at most 256 / 64 / 16
+                                   requests of N up to 64 / 160 / more           */
     int64_t memory_budget;      /* device bytes of admitted requests; 0 = 1 GiB.
                                    A request larger than the budget is admitted
                                    alone when nothing else is in flight          */
@@ -271,8 +274,9 @@ int rcpsp_server_create(rcpsp_server **srv, int device, const rcpsp_server_confi
 int rcpsp_server_destroy(rcpsp_server *srv);
 /* Validates one instance (as rcpsp_load_instances does; the same error
  * codes), copies it and queues it with its search parameters (record_trace
- * and use_graph must be 0).  Requests with identical parameters share
- * batches, in arrival order.  Returns at once. */
+ * and use_graph must be 0).  Requests of one launch class with identical
+ * parameters share batches, in arrival order; the class whose oldest
+ * request is oldest is served first.  Returns at once. */
 int rcpsp_server_submit(rcpsp_server *srv, const rcpsp_instance *inst, const rcpsp_params *params,
                         int64_t tag);
 /* Moves up to `capacity` finished requests into `out` (host), waiting up to

@@ -10,9 +10,11 @@
 //   1. harvests every context whose batch finished: copies the results,
 //      frees the batch's device memory, returns its footprint to the budget
 //      and publishes one completion per request;
-//   2. fills every free context with a batch: queued requests in arrival
-//      order with identical search parameters, while the footprint fits the
-//      budget (a lone request is admitted even if larger), up to max_batch;
+//   2. fills every free context with a batch: the launch class whose oldest
+//      request is oldest, then its requests in arrival order with identical
+//      search parameters, while the footprint fits the budget (a lone request
+//      is admitted even if larger), up to a batch size that shrinks with the
+//      instance size (256 / 64 / 16) and max_batch;
 //   3. sleeps on a condition variable until a submission or the next poll
 //      tick (no GPU spin: completion is an event query).
 // Searches are deterministic and independent per instance, so a request's
@@ -47,6 +49,7 @@ int64_t now_ns() {
 
 struct Request {
     int64_t tag = 0;
+    int cls = 0;                 // launch class (footprint x size), as the search groups them
     rcpsp_params params{};
     int32_t n = 0, m = 0;
     std::vector<int32_t> dur, cap, req, succ_off, succ, key;
@@ -80,6 +83,7 @@ struct Slot {
     std::vector<int32_t> ids;
     int64_t bytes = 0;
     int64_t t_launch = 0;
+    int cls = -1;                // launch class of the batch in flight
 };
 
 bool same_params(const rcpsp_params &a, const rcpsp_params &b) { return std::memcmp(&a, &b, sizeof(a)) == 0; }
@@ -105,7 +109,7 @@ struct rcpsp_server {
     std::vector<rcpsp_allocator> allocs;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
-    std::deque<Request> pending;
+    std::deque<Request> pending[9];      // one FIFO per launch class
     std::deque<Completion> done;
     std::vector<Completion> handed;      // returned by the last poll, owned until the next one
     std::thread worker;
@@ -170,23 +174,56 @@ void harvest(rcpsp_server *s, Slot &sl) {
     sl.bytes = 0;
 }
 
-// Takes a batch for a free slot; false when nothing can be admitted now.
+// Launch class of a request: footprint (per-group scratch words up to 2K,
+// 8K, more) times size (N up to 64, 160, more), as rcpsp_tabu_search splits
+// a call.  Batches take one class, so small requests do not wait for the
+// completion of large ones, and large requests come in small batches that
+// can share clusters of CTAs.
+int request_class(const rcpsp::PackedInstance &pk, const rcpsp_params &p) {
+    const int mode = p.eval_mode == RCPSP_EVAL_AUTO ? pk.h.sel_mode : p.eval_mode;
+    const int gw = rcpsp::profile_words(mode, pk.h.wps, pk.h.ub, pk.h.sum_cap) + pk.h.n;
+    const int fp = gw <= 2048 ? 0 : (gw <= 8192 ? 1 : 2);
+    const int sz = pk.h.n <= 64 ? 0 : (pk.h.n <= 160 ? 1 : 2);
+    return fp * 3 + sz;
+}
+
+int batch_limit(const rcpsp_server *s, int cls) {
+    const int sz = cls % 3;
+    return std::max(1, std::min(s->cfg.max_batch, sz == 0 ? 256 : (sz == 1 ? 64 : 16)));
+}
+
+// Takes a batch for a free slot: the class whose oldest request is oldest,
+// then that class's requests in arrival order with the same parameters.
+// Batches of the largest size class hold at most half of the slots, so that
+// long searches cannot keep short ones waiting.  False when nothing can be
+// admitted now.
 bool admit(rcpsp_server *s, Slot &sl) {
     {
         std::lock_guard<std::mutex> lk(s->mu);
-        if (s->pending.empty()) return false;
-        const rcpsp_params p0 = s->pending.front().params;
-        while (!s->pending.empty() && static_cast<int>(sl.reqs.size()) < s->cfg.max_batch) {
-            Request &r = s->pending.front();
+        int large_busy = 0;
+        for (const Slot &o : s->slots) large_busy += o.busy && o.cls % 3 == 2;
+        const bool large_ok = 2 * (large_busy + 1) <= static_cast<int>(s->slots.size()) || large_busy == 0;
+        int cls = -1;
+        for (int q = 0; q < 9; ++q)
+            if (!s->pending[q].empty() && (large_ok || q % 3 != 2) &&
+                (cls < 0 || s->pending[q].front().t_submit < s->pending[cls].front().t_submit))
+                cls = q;
+        if (cls < 0) return false;
+        std::deque<Request> &pq = s->pending[cls];
+        const rcpsp_params p0 = pq.front().params;
+        const int lim = batch_limit(s, cls);
+        while (!pq.empty() && static_cast<int>(sl.reqs.size()) < lim) {
+            Request &r = pq.front();
             if (!same_params(r.params, p0)) break;
             const bool lone = s->inflight_bytes == 0 && sl.reqs.empty();
             if (!lone && s->inflight_bytes + r.bytes > s->cfg.memory_budget) break;
             s->inflight_bytes += r.bytes;
             sl.bytes += r.bytes;
             sl.reqs.push_back(std::move(r));
-            s->pending.pop_front();
+            pq.pop_front();
         }
         if (sl.reqs.empty()) return false;
+        sl.cls = cls;
         s->st.admitted += static_cast<int64_t>(sl.reqs.size());
         s->st.inflight_requests += static_cast<int64_t>(sl.reqs.size());
         s->st.batches++;
@@ -243,8 +280,12 @@ void run(rcpsp_server *s) {
             if (!sl.busy && admit(s, sl)) progress = true;
         if (!progress) {
             std::unique_lock<std::mutex> lk(s->mu);
-            s->cv_work.wait_for(lk, std::chrono::microseconds(s->cfg.poll_us),
-                                [&] { return s->stop.load() || !s->pending.empty(); });
+            s->cv_work.wait_for(lk, std::chrono::microseconds(s->cfg.poll_us), [&] {
+                if (s->stop.load()) return true;
+                for (const auto &q : s->pending)
+                    if (!q.empty()) return true;
+                return false;
+            });
         }
     }
 }
@@ -258,7 +299,7 @@ int rcpsp_server_create(rcpsp_server **out, int device, const rcpsp_server_confi
     *out = nullptr;
     rcpsp_server *s = new rcpsp_server();
     s->device = device;
-    s->cfg.slots = 4;
+    s->cfg.slots = 8;
     s->cfg.max_batch = 256;
     s->cfg.memory_budget = int64_t(1) << 30;
     s->cfg.poll_us = 100;
@@ -332,11 +373,12 @@ int rcpsp_server_submit(rcpsp_server *s, const rcpsp_instance *inst, const rcpsp
         r.has_key = true;
     }
     r.bytes = footprint(pk);
+    r.cls = request_class(pk, *params);
     r.t_submit = now_ns();
     {
         std::lock_guard<std::mutex> lk(s->mu);
         s->st.submitted++;
-        s->pending.push_back(std::move(r));
+        s->pending[r.cls].push_back(std::move(r));
     }
     s->cv_work.notify_one();
     return RCPSP_OK;
@@ -368,7 +410,8 @@ int rcpsp_server_get_stats(rcpsp_server *s, rcpsp_server_stats *out) {
     if (!s || !out) return RCPSP_E_INVALID_ARG;
     std::lock_guard<std::mutex> lk(s->mu);
     *out = s->st;
-    out->pending = static_cast<int64_t>(s->pending.size());
+    out->pending = 0;
+    for (const auto &q : s->pending) out->pending += static_cast<int64_t>(q.size());
     out->inflight_bytes = s->inflight_bytes;
     return RCPSP_OK;
 }

@@ -306,7 +306,7 @@ class Solver:
 class Server:
     """Continuous-batching solve server (rcpsp_server_* in include/rcpsp.h)."""
 
-    def __init__(self, device: int = 0, slots: int = 4, max_batch: int = 256, memory_budget: int = 1 << 30,
+    def __init__(self, device: int = 0, slots: int = 8, max_batch: int = 256, memory_budget: int = 1 << 30,
                  poll_us: int = 100, lib_path: Optional[str] = None):
         self.lib = library(lib_path)
         self.srv = C.c_void_p()
