@@ -187,6 +187,33 @@ def test_cluster_split_search(solver, oracle, csize):
         solver.free(ids)
 
 
+def test_multistart_keeps_the_best_start(solver, oracle):
+    from paper_1711_04556_gb300.multistart import multistart
+    inst = I.config_batch("j30_batch", 1, first=123)[0]
+    out = multistart(solver, inst, starts=8, seed=5, iterations=60, delta=20, tabu_len=60)
+    refs = [oracle.tabu_search(inst, 60, 20, 60, 0, 1, level_key=k) for k in out["keys"]]
+    assert out["makespans"] == [r["best_cmax"] for r in refs]
+    best = min(range(8), key=lambda k: (refs[k]["best_cmax"], k))
+    assert out["start"] == best and out["best_W"].tolist() == refs[best]["best_W"].tolist()
+
+
+def test_bounded_wait_reports_timeout(solver, monkeypatch):
+    """A host wait with a tiny limit returns RCPSP_E_TIMEOUT instead of
+    blocking; the context stays usable and a later wait succeeds."""
+    import time
+    insts = I.config_batch("j30_batch", 240, first=600)
+    ids = solver.load(insts)
+    monkeypatch.setenv("RCPSP_WAIT_SECONDS", "0")
+    solver.search(ids, iterations=1000, delta=20, tabu_len=60)
+    with pytest.raises(R.RcpspError) as e:
+        solver.results(ids)
+    assert e.value.code == -7
+    monkeypatch.setenv("RCPSP_WAIT_SECONDS", "300")
+    time.sleep(0.2)
+    assert all(r["status"] == 0 for r in solver.results(ids))
+    solver.free(ids)
+
+
 # -------------------------------------------------------------- edge cases
 def test_edge_cases(solver, oracle):
     base = medium_instances(1, first=1000)[0]
