@@ -182,7 +182,9 @@ int rcpsp_tabu_search_noalloc(rcpsp_ctx *ctx, const int32_t *ids, int32_t count,
  * apart; classes with at most half as many searches as the GPU has SMs also
  * try clusters of 2, 4 and 8 CTAs per search.  The returned shape is the
  * one of the largest class.  Later searches with group_size =
- * warps_per_cta = cluster_size = 0 and the same signature use it.  The
+ * warps_per_cta = cluster_size = 0 and the same signature use it.  When the
+ * environment variable RCPSP_TUNE_CACHE names a file, the table is written
+ * there per device name and read back by contexts created later.  The
  * trials overwrite the instances' results.  Synchronous.  The shape is the
  * GPU's own split of the neighbourhood (Sec. 6 parallelises it over the
  * threads of a block); the paper fixes it by hand (Sec. 7). */

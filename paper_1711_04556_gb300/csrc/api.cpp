@@ -8,7 +8,9 @@
 #include <chrono>
 #include <cstdlib>
 #include <cstring>
+#include <fstream>
 #include <new>
+#include <sstream>
 #include <numeric>
 #include <string>
 #include <thread>
@@ -209,6 +211,49 @@ std::string shape_key(const std::vector<LaunchItem> &items) {
            std::to_string(dl) + (tm ? "_T" : "") + (cap ? "_C" : "") + "_b" + std::to_string(lg);
 }
 
+// Shape table on disk: the file named by RCPSP_TUNE_CACHE holds lines
+// "<device name>\t<signature>\t<G> <warps> <CTAs per search>"; a context
+// loads the lines of its own device and rcpsp_autotune writes them back.
+std::string device_tag(const rcpsp_ctx *c) {
+    std::string t = c->prop.name;
+    for (char &ch : t)
+        if (ch == '\t' || ch == '\n') ch = ' ';
+    return t;
+}
+
+void load_tune_cache(rcpsp_ctx *c) {
+    const char *path = std::getenv("RCPSP_TUNE_CACHE");
+    if (!path || !*path) return;
+    std::ifstream f(path);
+    std::string line;
+    const std::string dev = device_tag(c);
+    while (std::getline(f, line)) {
+        std::istringstream ls(line);
+        std::string d, key;
+        if (!std::getline(ls, d, '\t') || !std::getline(ls, key, '\t') || d != dev) continue;
+        std::array<int, 3> v{};
+        if (ls >> v[0] >> v[1] >> v[2]) c->tuned.push_back({key, v});
+    }
+}
+
+void save_tune_cache(const rcpsp_ctx *c) {
+    const char *path = std::getenv("RCPSP_TUNE_CACHE");
+    if (!path || !*path) return;
+    const std::string dev = device_tag(c);
+    std::vector<std::string> keep;
+    {
+        std::ifstream f(path);
+        std::string line;
+        while (std::getline(f, line))
+            if (line.compare(0, dev.size() + 1, dev + "\t") != 0) keep.push_back(line);   // other devices
+    }
+    std::ofstream o(std::string(path) + ".tmp");
+    for (const std::string &l : keep) o << l << "\n";
+    for (const auto &e : c->tuned) o << dev << "\t" << e.first << "\t" << e.second[0] << " " << e.second[1] << " " << e.second[2] << "\n";
+    o.close();
+    std::rename((std::string(path) + ".tmp").c_str(), path);
+}
+
 bool tuned_shape(const rcpsp_ctx *c, const std::string &key, int *G, int *warps, int *csize = nullptr) {
     for (const auto &e : c->tuned)
         if (e.first == key) {
@@ -264,6 +309,7 @@ int rcpsp_create(rcpsp_ctx **ctx, int device, const rcpsp_allocator *alloc) {
         delete c;
         return RCPSP_E_CUDA;
     }
+    load_tune_cache(c);
     c->queue_dev = static_cast<int *>(dev_alloc(c, 64, nullptr));          // one counter per class
     if (!c->queue_dev) {
         cudaEventDestroy(c->done);
@@ -781,6 +827,7 @@ int rcpsp_autotune(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcpsp_
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    save_tune_cache(c);
     if (best_group_size) *best_group_size = ret_G;
     if (best_warps) *best_warps = ret_W;
     return RCPSP_OK;

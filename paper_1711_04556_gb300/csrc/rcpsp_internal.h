@@ -18,7 +18,6 @@
 
 namespace rcpsp {
 
-constexpr int kMaxGroupsPerCta = 1024;
 constexpr int kDefaultMoveCap = 2048;   // potential moves examined per stripe
 
 // Per-instance header (64 bytes).
@@ -35,7 +34,7 @@ struct InstHeader {
 };
 static_assert(sizeof(InstHeader) == 64, "InstHeader is 64 bytes");
 
-// One entry of a launch (96 bytes), ordered by estimated cost on the host.
+// One entry of a launch (112 bytes), ordered by estimated cost on the host.
 struct LaunchItem {
     InstHeader h;
     const int32_t *record;      // packed record in device memory
