@@ -373,12 +373,24 @@ int rcpsp_load_instances(rcpsp_ctx *c, const rcpsp_instance *inst, int32_t count
     if (count < 0 || (count > 0 && (!inst || !out_ids))) return set_err(c, RCPSP_E_INVALID_ARG, "bad arguments");
     if (count == 0) return RCPSP_OK;
     cudaSetDevice(c->device);
+    // host preparation of every instance, spread over host threads
     std::vector<rcpsp::PackedInstance> packed(count);
+    std::vector<int> codes(count, RCPSP_OK);
+    std::vector<std::string> msgs(count);
+    {
+        const int hw = static_cast<int>(std::max(1u, std::thread::hardware_concurrency()));
+        const int nt = std::max(1, std::min({hw, 16, count / 32}));
+        auto work = [&](int t) {
+            for (int k = t; k < count; k += nt) codes[k] = rcpsp::prepare_instance(inst[k], packed[k], msgs[k]);
+        };
+        std::vector<std::thread> pool;
+        for (int t = 1; t < nt; ++t) pool.emplace_back(work, t);
+        work(0);
+        for (std::thread &th : pool) th.join();
+    }
     size_t rec_words = 0, o_words = 0;
     for (int k = 0; k < count; ++k) {
-        std::string msg;
-        int rc = rcpsp::prepare_instance(inst[k], packed[k], msg);
-        if (rc != RCPSP_OK) return set_err(c, rc, "instance " + std::to_string(k) + ": " + msg);
+        if (codes[k] != RCPSP_OK) return set_err(c, codes[k], "instance " + std::to_string(k) + ": " + msgs[k]);
         rec_words += packed[k].h.record_words;
         o_words += out_words(packed[k].h.n);
     }

@@ -139,6 +139,38 @@ class _Marshalled:
                           _ptr(self.key) if self.key is not None else None)
 
 
+# numpy image of rcpsp_instance: two int32 then six pointers
+_INSTANCE_DTYPE = np.dtype([("n", "<i4"), ("m", "<i4"), ("dur", "<u8"), ("cap", "<u8"), ("req", "<u8"),
+                            ("succ_off", "<u8"), ("succ", "<u8"), ("level_key", "<u8")])
+assert _INSTANCE_DTYPE.itemsize == C.sizeof(Instance)
+
+
+class _BatchMarshalled:
+    """rcpsp_instance array for many instances: each field is concatenated
+    once and the structs are filled with vectorized pointer arithmetic."""
+
+    def __init__(self, instances, level_keys=None):
+        cnt = len(instances)
+        self.keep = []
+        self.rec = np.zeros(cnt, _INSTANCE_DTYPE)
+        self.rec["n"] = [x.n for x in instances]
+        self.rec["m"] = [x.m for x in instances]
+        for field in ("dur", "cap", "req", "succ_off", "succ"):
+            parts = [getattr(x, field) for x in instances]
+            flat = np.ascontiguousarray(np.concatenate(parts), dtype=np.int32)
+            lens = np.fromiter((len(a) for a in parts), np.int64, cnt)
+            offs = np.concatenate(([0], np.cumsum(lens)[:-1])) if cnt else np.zeros(0, np.int64)
+            self.rec[field] = flat.ctypes.data + 4 * offs
+            self.keep.append(flat)
+        if level_keys is not None:
+            for k, key in enumerate(level_keys):
+                if key is not None:
+                    a = _i32(key)
+                    self.keep.append(a)
+                    self.rec["level_key"][k] = a.ctypes.data
+        self.ptr = self.rec.ctypes.data_as(C.POINTER(Instance))
+
+
 def _torch_allocator():
     """Device memory from PyTorch's caching allocator."""
     import torch
@@ -215,10 +247,9 @@ class Solver:
 
     # ------------------------------------------------------------------ calls
     def load(self, instances: Sequence, level_keys: Optional[Sequence] = None) -> np.ndarray:
-        ms = [_Marshalled(x, None if level_keys is None else level_keys[k]) for k, x in enumerate(instances)]
-        arr = (Instance * len(ms))(*[m.s for m in ms])
-        ids = np.zeros(len(ms), np.int32)
-        self._check(self.lib.rcpsp_load_instances(self.ctx, arr, len(ms), _ptr(ids)))
+        bm = _BatchMarshalled(instances, level_keys)
+        ids = np.zeros(len(instances), np.int32)
+        self._check(self.lib.rcpsp_load_instances(self.ctx, bm.ptr, len(instances), _ptr(ids)))
         for i, x in zip(ids, instances):
             self.n_of[int(i)] = x.n
         return ids
