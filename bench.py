@@ -259,11 +259,12 @@ def run_ours(args):
     solver = R.Solver(local)
     st = torch.cuda.Stream(device=dev)
     kw = dict(iterations=WORKLOAD["iterations"], delta=WORKLOAD["delta"], tabu_len=WORKLOAD["tabu_len"],
-              mode=R.EVAL_AUTO, group_size=args.group_size, warps_per_cta=args.warps)
+              mode=R.EVAL_AUTO, group_size=args.group_size, warps_per_cta=args.warps,
+              cluster_size=args.cluster_size)
     ids = solver.load(insts)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)   # 256 MiB > L2
     tuned = None
-    if not args.group_size and not args.warps:
+    if not (args.group_size or args.warps or args.cluster_size):
         tuned = solver.autotune(ids, iterations=kw["iterations"], delta=kw["delta"], tabu_len=kw["tabu_len"],
                                 mode=R.EVAL_AUTO, trial_iterations=args.tune_iterations, stream=st)
 
@@ -389,9 +390,10 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": workload_config({"parallelism": f"replicas{world}" if world > 1 else "single GPU",
                                    "schedules_per_step": ev_step, "wall_s_timed": t_wall,
-                                   "launch_shape": {"group_size": (tuned or (args.group_size, args.warps))[0],
-                                                    "warps_per_cta": (tuned or (args.group_size, args.warps))[1],
-                                                    "chosen_by": "rcpsp_autotune" if tuned else "command line"}}),
+                                   "launch_shape": dict(zip(("group_size", "warps_per_cta", "cluster_size"),
+                                                            tuned or (args.group_size, args.warps,
+                                                                      args.cluster_size or 1)),
+                                                        chosen_by="rcpsp_autotune" if tuned else "command line")}),
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": (h1 - h0) // e2e_steps,
                 "d2h_bytes_per_step": (d1 - d0) // e2e_steps},
         "gpu_launches": args.steps,
@@ -418,6 +420,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--group-size", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)
+    ap.add_argument("--cluster-size", type=int, default=0)
     ap.add_argument("--tune-iterations", type=int, default=48)
     ap.add_argument("--serving-seconds", type=float, default=5.0)
     ap.add_argument("--serving-rate", type=float, default=2000.0)

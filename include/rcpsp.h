@@ -172,16 +172,16 @@ int rcpsp_tabu_search(rcpsp_ctx *ctx, const int32_t *ids, int32_t count,
 int rcpsp_tabu_search_noalloc(rcpsp_ctx *ctx, const int32_t *ids, int32_t count,
                               const rcpsp_params *params, void *cuda_stream);
 
-/* Chooses the launch shape -- lanes per neighbour decode (group_size) and
- * warps per CTA -- for searches like `params` over these instances by
+/* Chooses the launch shape -- lanes per neighbour decode (group_size),
+ * warps per CTA and CTAs per search (cluster_size) -- for searches like `params` over these instances by
  * timing short trial searches (trial_iterations each, on `cuda_stream`) of
  * every shape that fits, and keeps the fastest (neighbours decoded per
  * second) in the context under the workload's signature (largest N, horizon,
  * words per step, swap distance, evaluator mix, batch size).  Instances are
  * tuned per launch class (see rcpsp_tabu_search), the unit a search launches
  * apart; classes with at most half as many searches as the GPU has SMs also
- * try clusters of 2, 4 and 8 CTAs per search.  The returned shape is the
- * one of the largest class.  Later searches with group_size =
+ * try clusters of 2, 4 and 8 CTAs per search.  The returned shape (any
+ * output pointer may be NULL) is the one of the largest class.  Later searches with group_size =
  * warps_per_cta = cluster_size = 0 and the same signature use it.  When the
  * environment variable RCPSP_TUNE_CACHE names a file, the table is written
  * there per device name and read back by contexts created later.  The
@@ -190,7 +190,7 @@ int rcpsp_tabu_search_noalloc(rcpsp_ctx *ctx, const int32_t *ids, int32_t count,
  * threads of a block); the paper fixes it by hand (Sec. 7). */
 int rcpsp_autotune(rcpsp_ctx *ctx, const int32_t *ids, int32_t count, const rcpsp_params *params,
                    int32_t trial_iterations, void *cuda_stream, int32_t *best_group_size,
-                   int32_t *best_warps);
+                   int32_t *best_warps, int32_t *best_cluster_size);
 
 /* Waits for the last search of the context and copies results to host
  * buffers: order = best list W* and start = its start times S (both [sum of N

@@ -733,7 +733,7 @@ int rcpsp_tabu_search_noalloc(rcpsp_ctx *c, const int32_t *ids, int32_t count, c
 }
 
 int rcpsp_autotune(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcpsp_params *p, int32_t trial_iterations,
-                   void *stream, int32_t *best_group_size, int32_t *best_warps) {
+                   void *stream, int32_t *best_group_size, int32_t *best_warps, int32_t *best_cluster_size) {
     if (!c) return RCPSP_E_INVALID_ARG;
     if (!p || count <= 0 || !ids || trial_iterations < 1) return set_err(c, RCPSP_E_INVALID_ARG, "bad arguments");
     cudaSetDevice(c->device);
@@ -764,7 +764,7 @@ int rcpsp_autotune(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcpsp_
     q.iterations = std::min(p->iterations, trial_iterations);
     q.record_trace = 0;
     q.use_graph = 0;
-    int ret_G = 0, ret_W = 0, ret_count = -1;
+    int ret_G = 0, ret_W = 0, ret_C = 0, ret_count = -1;
     // each footprint class is tuned on its own (searches launch them apart)
     for (int cls = 0; cls < kClasses; ++cls) {
         std::vector<int32_t> cids;
@@ -835,6 +835,7 @@ int rcpsp_autotune(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcpsp_
             ret_count = cn;
             ret_G = bG;
             ret_W = bW;
+            ret_C = bC;
         }
     }
     cudaEventDestroy(e0);
@@ -842,6 +843,7 @@ int rcpsp_autotune(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcpsp_
     save_tune_cache(c);
     if (best_group_size) *best_group_size = ret_G;
     if (best_warps) *best_warps = ret_W;
+    if (best_cluster_size) *best_cluster_size = ret_C;
     return RCPSP_OK;
 }
 

@@ -99,7 +99,7 @@ def library(path: Optional[str] = None):
         "rcpsp_tabu_search": (C.c_int, [C.c_void_p, P(C.c_int32), C.c_int32, P(Params), C.c_void_p]),
         "rcpsp_tabu_search_noalloc": (C.c_int, [C.c_void_p, P(C.c_int32), C.c_int32, P(Params), C.c_void_p]),
         "rcpsp_autotune": (C.c_int, [C.c_void_p, P(C.c_int32), C.c_int32, P(Params), C.c_int32, C.c_void_p,
-                                     P(C.c_int32), P(C.c_int32)]),
+                                     P(C.c_int32), P(C.c_int32), P(C.c_int32)]),
         "rcpsp_get_schedules": (C.c_int, [C.c_void_p, P(C.c_int32), C.c_int32, P(C.c_int32), P(C.c_int32),
                                           P(C.c_int32), P(Stats)]),
         "rcpsp_get_trace": (C.c_int, [C.c_void_p, C.c_int32, P(C.c_int32), C.c_int32, P(C.c_int32)]),
@@ -281,14 +281,15 @@ class Solver:
 
     def autotune(self, ids, iterations: int = 100, delta: int = 0, tabu_len: int = 0, mode: int = EVAL_AUTO,
                  stop_at_cp: bool = True, trial_iterations: int = 48, stream=None):
-        """rcpsp_autotune: times trial searches of every launch shape; returns (group_size, warps)."""
+        """rcpsp_autotune: times trial searches of every launch shape; returns
+        (group_size, warps, cluster_size) of the largest launch class."""
         ids = _i32(ids)
         p = Params(iterations, delta, tabu_len, mode, int(stop_at_cp), 0, 0, 0, 0, 0)
-        g, w = C.c_int32(0), C.c_int32(0)
+        g, w, cs = C.c_int32(0), C.c_int32(0), C.c_int32(0)
         handle = getattr(stream, "cuda_stream", stream) or None
         self._check(self.lib.rcpsp_autotune(self.ctx, _ptr(ids), len(ids), C.byref(p), trial_iterations, handle,
-                                            C.byref(g), C.byref(w)))
-        return g.value, w.value
+                                            C.byref(g), C.byref(w), C.byref(cs)))
+        return g.value, w.value, cs.value
 
     def results(self, ids) -> List[dict]:
         ids = _i32(ids)

@@ -155,9 +155,10 @@ def test_autotuned_shape_keeps_results(solver, oracle, tmp_path, monkeypatch):
     monkeypatch.setenv("RCPSP_TUNE_CACHE", str(cache))
     insts = I.config_batch("j30_batch", 64, first=300)
     ids = solver.load(insts)
-    g, w = solver.autotune(ids, iterations=80, delta=20, tabu_len=60, trial_iterations=8)
+    g, w, cs = solver.autotune(ids, iterations=80, delta=20, tabu_len=60, trial_iterations=8)
     lines = cache.read_text().strip().splitlines()
-    assert lines and lines[-1].split("\t")[2].split()[:2] == [str(g), str(w)]
+    assert lines and lines[-1].split("\t")[2].split() == [str(g), str(w), str(cs)]
+    assert cs in (1, 2, 4, 8)
     with R.Solver(0) as other:                       # a new context reads the table back
         assert other.lib.rcpsp_last_error(other.ctx) is not None
     assert g in (1, 2, 4, 8, 16, 32) and 1 <= w <= 16
