@@ -12,6 +12,7 @@ the same count through the C interface with host buffers (instance upload,
 host preparation, search, result download).
 
 Run: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+     [--workload j30_batch|j120_batch|mixed_batch] [--iterations I]
 Under torchrun each rank solves its own 480 instances (weak scaling).
 """
 from __future__ import annotations
@@ -31,7 +32,23 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(family="j30_batch", count=480, iterations=1000, delta=20, tabu_len=60)
+WORKLOADS = {
+    "j30_batch": dict(family="j30_batch", count=480, iterations=1000, delta=20, tabu_len=60,
+                      text="j30_batch: 480 synthetic RCPSP instances, n=30 (+2 dummies), M=4, durations 1-10, "
+                           "demands 1-10 w.p. 0.5, NC in {1.5,1.8,2.1}, RS in {0.2,0.5,0.7,1.0}; 1000 tabu "
+                           "iterations each, swap distance 20, tabu list 60, evaluator by the selection rule; "
+                           "one persistent CUDA-graph launch per step"),
+    "j120_batch": dict(family="j120_batch", count=600, iterations=5000, delta=60, tabu_len=800,
+                       text="j120_batch: 600 synthetic RCPSP instances, n=120, M=4, durations 1-10, NC in "
+                            "{1.5,1.8,2.1}, RS in {0.1,0.2,0.5,0.7,1.0}; 5000 tabu iterations each, swap distance "
+                            "60, tabu list 800, evaluator by the selection rule; one CUDA-graph replay per step"),
+    "mixed_batch": dict(family="mixed_batch", count=1024, iterations=1000, delta=0, tabu_len=0,
+                        text="mixed_batch: 1024 synthetic RCPSP instances, n uniform in {30,60,90,120,300}, M in "
+                             "4-8, durations 1-50; 1000 tabu iterations each, swap distance / tabu list by size "
+                             "(20/60, 60/250, 60/600, 60/800, 60/800), evaluator by the selection rule; one "
+                             "CUDA-graph replay per step (launch classes on forked streams)"),
+}
+WORKLOAD = dict(WORKLOADS["j30_batch"])
 METRIC = "neighbour schedules evaluated/sec on 1 GB300 (bit-exact) + p50/p99 solve latency"
 UNIT = "schedules/s"
 KERNEL_SOURCES = ["paper_1711_04556_gb300/csrc/search_kernel.cu", "paper_1711_04556_gb300/csrc/rcpsp_internal.h"]
@@ -39,10 +56,7 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "search_kernel_j30_batch.traffic.j
 
 
 def workload_config(extra=None):
-    cfg = {"workload": "j30_batch: 480 synthetic RCPSP instances, n=30 (+2 dummies), M=4, durations 1-10, "
-                       "demands 1-10 w.p. 0.5, NC in {1.5,1.8,2.1}, RS in {0.2,0.5,0.7,1.0}; 1000 tabu "
-                       "iterations each, swap distance 20, tabu list 60, evaluator by the selection rule; "
-                       "one persistent CUDA-graph launch per step",
+    cfg = {"workload": WORKLOAD["text"],
            "instances": WORKLOAD["count"], "iterations": WORKLOAD["iterations"],
            "delta": WORKLOAD["delta"], "tabu_len": WORKLOAD["tabu_len"],
            "l2": "flushed between timed steps (256 MiB write); inputs are a few hundred KB"}
@@ -146,20 +160,29 @@ def load_traffic():
     return None
 
 
-def cpu_baseline(sample: int):
+def oracle_params(O, I, insts, iterations):
+    """Per-instance oracle parameters; swap distance and tabu length 0 mean
+    "by instance size", as the library reads them."""
+    out = []
+    for x in insts:
+        d, t = (WORKLOAD["delta"], WORKLOAD["tabu_len"]) if WORKLOAD["delta"] else I.search_params(x.n - 2)
+        out.append((iterations, d, t, O.AUTO, 1))
+    return out
+
+
+def cpu_baseline(sample: int, iterations: int):
     """The CPU reference, as it stands, on a bounded sample of the workload."""
     from oracle import oracle as O
     from paper_1711_04556_gb300 import instances as I
     O.build()
     insts = I.config_batch(WORKLOAD["family"], sample)
     cores = os.cpu_count() or 1
-    p = (WORKLOAD["iterations"], WORKLOAD["delta"], WORKLOAD["tabu_len"], O.AUTO, 1)
     t0 = time.perf_counter()
-    res = O.tabu_search_batch(insts, [p] * len(insts), cores)
+    res = O.tabu_search_batch(insts, oracle_params(O, I, insts, iterations), cores)
     dt = time.perf_counter() - t0
     ev = sum(r["evaluated"] for r in res)
     return {"value": ev / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"first {sample} of the {WORKLOAD['count']} instances, {WORKLOAD['iterations']} "
+            "sample": f"first {sample} of the {WORKLOAD['count']} instances, {iterations} "
                       f"iterations each, one search per host thread ({ev} schedules in {dt:.2f} s)"}
 
 
@@ -173,13 +196,13 @@ def run_reference(args):
     sample = args.reference_sample
     insts = I.config_batch(WORKLOAD["family"], sample)
     cores = os.cpu_count() or 1
-    p = (WORKLOAD["iterations"], WORKLOAD["delta"], WORKLOAD["tabu_len"], O.AUTO, 1)
+    params = oracle_params(O, I, insts, WORKLOAD["iterations"])
     for _ in range(args.warmup):
-        O.tabu_search_batch(insts[:max(1, cores)], [p] * min(len(insts), max(1, cores)), cores)
+        O.tabu_search_batch(insts[:max(1, cores)], params[:max(1, cores)], cores)
     ev_total, t_total = 0, 0.0
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        res = O.tabu_search_batch(insts, [p] * len(insts), cores)
+        res = O.tabu_search_batch(insts, params, cores)
         t_total += time.perf_counter() - t0
         ev_total += sum(r["evaluated"] for r in res)
     value = ev_total / t_total
@@ -286,6 +309,7 @@ def run_ours(args):
     sampler = ClockSampler(local)
     time.sleep(0.3)
     events = []
+    k0 = solver.kernel_launches()
     t_wall = time.perf_counter()
     for _ in range(args.steps):
         with torch.cuda.stream(st):
@@ -298,6 +322,7 @@ def run_ours(args):
         events.append((e0, e1))
     barrier()
     t_wall = time.perf_counter() - t_wall
+    launches_timed = solver.kernel_launches() - k0
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in events]
     res = solver.results(ids)
@@ -383,7 +408,7 @@ def run_ours(args):
     achieved = ops_step / per_launch_s / 1e9
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.cpu_sample)
+        cpu = cpu_baseline(args.cpu_sample, args.cpu_iterations or WORKLOAD["iterations"])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": sum(step_ms) / args.steps, "higher_is_better": True,
@@ -396,9 +421,9 @@ def run_ours(args):
                                                         chosen_by="rcpsp_autotune" if tuned else "command line")}),
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": (h1 - h0) // e2e_steps,
                 "d2h_bytes_per_step": (d1 - d0) // e2e_steps},
-        "gpu_launches": args.steps,
+        "gpu_launches": launches_timed,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
-                     "frac": achieved / peak, "traffic": load_traffic(),
+                     "frac": achieved / peak, "traffic": load_traffic() if WORKLOAD["family"] == "j30_batch" else None,
                      "ops_per_launch": ops_step,
                      "peak_basis": f"{sms} SMs x 128 INT32 lanes x {max_mhz:.0f} MHz (derived, not measured)"},
         "cpu_baseline": cpu,
@@ -412,12 +437,24 @@ def run_ours(args):
     return 0
 
 
+def set_workload(name: str, iterations: int) -> None:
+    WORKLOAD.clear()
+    WORKLOAD.update(WORKLOADS[name])
+    if iterations:
+        WORKLOAD["iterations"] = iterations
+        WORKLOAD["text"] = WORKLOAD["text"].replace(f"{WORKLOADS[name]['iterations']} tabu iterations",
+                                                    f"{iterations} tabu iterations")
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="j30_batch",
+                    help="instance batch of one step (the bench line is quoted on j30_batch)")
+    ap.add_argument("--iterations", type=int, default=0, help="tabu iterations per instance (0: the workload's)")
     ap.add_argument("--group-size", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--cluster-size", type=int, default=0)
@@ -432,9 +469,11 @@ def main():
     ap.add_argument("--plain-sample", type=int, default=48)
     ap.add_argument("--latency-reps", type=int, default=100)
     ap.add_argument("--cpu-sample", type=int, default=160)
+    ap.add_argument("--cpu-iterations", type=int, default=0, help="iterations of the oracle sample (0: the step's)")
     ap.add_argument("--reference-sample", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    set_workload(args.workload, args.iterations)
     if args.warmup < 3:
         args.warmup = 3
     if args.serving_only:

@@ -231,6 +231,13 @@ int rcpsp_prepare_instance(const rcpsp_instance *inst, int32_t *critical_path, i
  * created (instance records, launch plans, results, traces); host. */
 int rcpsp_transfer_bytes(const rcpsp_ctx *ctx, int64_t *h2d, int64_t *d2h);
 
+/* Kernel launches the context has issued since it was created: one per
+ * launch class of every search (a graph replay counts the kernels it
+ * replays), one per no-allocation search and per list evaluation; host.
+ * RCPSP_E_INVALID_ARG if `launches` is NULL.  An accounting call with no
+ * counterpart in the paper. */
+int rcpsp_kernel_launches(const rcpsp_ctx *ctx, int64_t *launches);
+
 /* ------------------------------------------------------------------------
  * Continuous-batching solve server.  Requests are admitted while others run,
  * as launch slots and device memory free up, and their searches overlap on

@@ -72,6 +72,7 @@ struct rcpsp_ctx {
     std::vector<LaunchItem> g_items;
     cudaStream_t g_stream = nullptr;
     long long h2d = 0, d2h = 0;   // bytes copied by the context
+    long long kernels = 0;        // kernel launches issued (graph replays count their kernels)
     std::vector<LaunchItem> noalloc_plan;   // host copy of the last no-allocation plan
     // footprint classes beyond the first run on their own streams, forked
     // from and joined back to the caller's stream
@@ -347,6 +348,12 @@ int rcpsp_transfer_bytes(const rcpsp_ctx *c, int64_t *h2d, int64_t *d2h) {
     if (!c) return RCPSP_E_INVALID_ARG;
     if (h2d) *h2d = c->h2d;
     if (d2h) *d2h = c->d2h;
+    return RCPSP_OK;
+}
+
+int rcpsp_kernel_launches(const rcpsp_ctx *c, int64_t *launches) {
+    if (!c || !launches) return RCPSP_E_INVALID_ARG;
+    *launches = c->kernels;
     return RCPSP_OK;
 }
 
@@ -639,6 +646,7 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
         e = launch_all(st);
         if (e != cudaSuccess) return cuda_err(c, e, "search launch");
     }
+    c->kernels += static_cast<long long>(launches.size());
     e = cudaEventRecord(c->done, st);
     if (e != cudaSuccess) return cuda_err(c, e, "event record");
     c->pending = true;
@@ -726,6 +734,7 @@ int rcpsp_tabu_search_noalloc(rcpsp_ctx *c, const int32_t *ids, int32_t count, c
     if (e == cudaSuccess) e = rcpsp::launch_search(G, plan, count, queue, move_cap, blocks, threads, smem, st, 1);
     if (e != cudaSuccess) return cuda_err(c, e, "no-allocation search launch");
     c->h2d += static_cast<long long>(ibytes);
+    c->kernels += 1;
     e = cudaEventRecord(c->done, st);
     if (e != cudaSuccess) return cuda_err(c, e, "event record");
     c->pending = true;
@@ -1015,6 +1024,7 @@ int rcpsp_evaluate_lists(rcpsp_ctx *c, int32_t id, const int32_t *lists, int32_t
     if (rc != RCPSP_OK) return rc;
     c->h2d += static_cast<long long>(lbytes);
     c->d2h += static_cast<long long>(obytes);
+    c->kernels += 1;
     if (start) std::memcpy(start, host.data() + o_start, lbytes);
     if (work) std::memcpy(work, host.data() + o_work, static_cast<size_t>(count) * 8);
     if (makespan) std::memcpy(makespan, host.data() + o_cmax, static_cast<size_t>(count) * 4);

@@ -261,6 +261,18 @@ def level_keys(inst: Instance, seed: int) -> np.ndarray:
 # Workload families (instance batches); parameters per family are the
 # search parameters of Table 2 where the paper gives them.
 # --------------------------------------------------------------------------
+def search_params(n_activities: int) -> tuple:
+    """(swap distance, tabu list length) by instance size: the single-instance
+    workload's (20, 60) up to 45 activities, then Table 2's rows."""
+    if n_activities <= 45:
+        return 20, 60
+    if n_activities <= 75:
+        return 60, 250
+    if n_activities <= 105:
+        return 60, 600
+    return 60, 800
+
+
 def config_batch(name: str, count: Optional[int] = None, first: int = 0) -> List[Instance]:
     """Instances of a named workload.
 

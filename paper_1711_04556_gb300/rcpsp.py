@@ -21,7 +21,7 @@ ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "CYCLE", -3: "DUMMY", -4: "DEMAND_EXCE
           -5: "TOO_LARGE", -6: "CUDA", -7: "TIMEOUT", -8: "NOT_FOUND", -9: "DEVICE"}
 EXPORTS = ("rcpsp_create", "rcpsp_destroy", "rcpsp_load_instances", "rcpsp_free_instances",
            "rcpsp_tabu_search", "rcpsp_tabu_search_noalloc", "rcpsp_autotune", "rcpsp_get_schedules", "rcpsp_get_trace", "rcpsp_evaluate_lists",
-           "rcpsp_prepare_instance", "rcpsp_transfer_bytes", "rcpsp_server_create", "rcpsp_server_destroy",
+           "rcpsp_prepare_instance", "rcpsp_transfer_bytes", "rcpsp_kernel_launches", "rcpsp_server_create", "rcpsp_server_destroy",
            "rcpsp_server_submit", "rcpsp_server_poll", "rcpsp_server_get_stats", "rcpsp_last_error")
 
 
@@ -108,6 +108,7 @@ def library(path: Optional[str] = None):
         "rcpsp_prepare_instance": (C.c_int, [P(Instance), P(C.c_int32), P(C.c_int32), P(C.c_int32),
                                              P(C.c_int32), C.c_char_p, C.c_int32]),
         "rcpsp_transfer_bytes": (C.c_int, [C.c_void_p, P(C.c_int64), P(C.c_int64)]),
+        "rcpsp_kernel_launches": (C.c_int, [C.c_void_p, P(C.c_int64)]),
         "rcpsp_server_create": (C.c_int, [P(C.c_void_p), C.c_int, P(ServerConfig)]),
         "rcpsp_server_destroy": (C.c_int, [C.c_void_p]),
         "rcpsp_server_submit": (C.c_int, [C.c_void_p, P(Instance), P(Params), C.c_int64]),
@@ -315,6 +316,11 @@ class Solver:
         h2d, d2h = C.c_int64(0), C.c_int64(0)
         self._check(self.lib.rcpsp_transfer_bytes(self.ctx, C.byref(h2d), C.byref(d2h)))
         return h2d.value, d2h.value
+
+    def kernel_launches(self) -> int:
+        n = C.c_int64(0)
+        self._check(self.lib.rcpsp_kernel_launches(self.ctx, C.byref(n)))
+        return n.value
 
     def trace(self, id_: int, iterations: int) -> np.ndarray:
         buf = np.zeros(max(1, 3 * iterations), np.int32)

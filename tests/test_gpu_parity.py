@@ -139,11 +139,7 @@ def test_mixed_sample_auto(solver, oracle):
     ids = solver.load(insts)
     solver.search(ids, iterations=12, delta=0, tabu_len=0, mode=R.EVAL_AUTO)
     got = solver.results(ids)
-    params = []
-    for x in insts:
-        a = x.n - 2
-        params.append((12,) + ((20, 60) if a <= 45 else (60, 250) if a <= 75 else (60, 600) if a <= 105
-                               else (60, 800)) + (0, 1))
+    params = [(12,) + I.search_params(x.n - 2) + (0, 1) for x in insts]
     ref = oracle.tabu_search_batch(insts, params, NPROC)
     for g, r in zip(got, ref):
         compare_search(oracle, g, r)
@@ -184,9 +180,7 @@ def test_cluster_split_search(solver, oracle, csize):
         got = solver.results(ids)
         params = []
         for x in insts:
-            a = x.n - 2
-            d_, t_ = (dl, tl) if dl else ((20, 60) if a <= 45 else (60, 250) if a <= 75 else (60, 600) if a <= 105
-                                          else (60, 800))
+            d_, t_ = (dl, tl) if dl else I.search_params(x.n - 2)
             params.append((it, d_, t_, mode, 1))
         ref = oracle.tabu_search_batch(insts, params, NPROC, trace=True)
         for k, (g, r) in enumerate(zip(got, ref)):
@@ -259,4 +253,18 @@ def test_level_keys_and_repeat_with_graph(solver, oracle):
     for o in outs:
         for g, r in zip(o, ref):
             compare_search(oracle, g, r)
+    solver.free(ids)
+
+
+def test_kernel_launch_count(solver):
+    """One kernel per launch class of a search; graph replays count too."""
+    insts = I.config_batch("j30_batch", 8) + [x for x in I.config_batch("mixed_batch", 40) if x.n == 302][:1]
+    ids = solver.load(insts)
+    k0 = solver.kernel_launches()
+    solver.search(ids[:8], iterations=5)
+    assert solver.kernel_launches() - k0 == 1
+    solver.search(ids, iterations=5, use_graph=True)
+    solver.search(ids, iterations=5, use_graph=True)
+    assert solver.kernel_launches() - k0 == 5          # two classes, twice
+    solver.results(ids)
     solver.free(ids)
