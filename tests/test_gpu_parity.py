@@ -263,8 +263,10 @@ def test_kernel_launch_count(solver):
     k0 = solver.kernel_launches()
     solver.search(ids[:8], iterations=5)
     assert solver.kernel_launches() - k0 == 1
-    solver.search(ids, iterations=5, use_graph=True)
-    solver.search(ids, iterations=5, use_graph=True)
+    import torch
+    st = torch.cuda.Stream()
+    solver.search(ids, iterations=5, use_graph=True, stream=st)
+    solver.search(ids, iterations=5, use_graph=True, stream=st)
     assert solver.kernel_launches() - k0 == 5          # two classes, twice
     solver.results(ids)
     solver.free(ids)
