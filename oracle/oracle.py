@@ -4,7 +4,8 @@ TEST INFRASTRUCTURE ONLY: imported by the tests, the smoke check and the
 benchmark's CPU-baseline leg.  The product path never imports this module.
 
 The C sources sit beside this file; ``build()`` compiles them with the host
-compiler (plain C, -O2, no target-specific flags) into
+compiler (plain C, -O2, no target-specific flags, no floating-point
+contraction) into
 ``librcpsp_oracle.so`` next to them.
 """
 from __future__ import annotations
@@ -34,7 +35,7 @@ def build(force: bool = False) -> str:
                  os.path.getmtime(LIB) < max(os.path.getmtime(SRC), os.path.getmtime(HDR)))
         if stale:
             tmp = LIB + f".tmp{os.getpid()}"
-            subprocess.run(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread",
+            subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-shared", "-fPIC", "-pthread",
                             "-Wall", "-Wextra", "-o", tmp, SRC], check=True)
             os.replace(tmp, LIB)
     return LIB
@@ -50,6 +51,17 @@ class _Inst(C.Structure):
 class _Params(C.Structure):
     _fields_ = [("iterations", C.c_int), ("max_swap_dist", C.c_int), ("tabu_len", C.c_int),
                 ("eval_mode", C.c_int), ("stop_at_cp", C.c_int)]
+
+
+class _CoopParams(C.Structure):
+    _fields_ = [("blocks", C.c_int), ("working_set", C.c_int), ("phi_max", C.c_int),
+                ("phi_steps", C.c_int), ("assign_fixed", C.c_int), ("words_per_block", C.c_int)]
+
+
+class _CoopEvent(C.Structure):
+    _fields_ = [("iteration", C.c_int), ("block", C.c_int), ("kind", C.c_int), ("slot", C.c_int),
+                ("cmax", C.c_int), ("assigned", C.c_int), ("diversified", C.c_int), ("phi", C.c_int),
+                ("ic", C.c_longlong)]
 
 
 class _Result(C.Structure):
@@ -75,6 +87,12 @@ def load(path: str):
         "orc_select_mode": (C.c_int, [P(_Inst)]),
         "orc_tabu_search": (C.c_int, [P(_Inst), P(_Params), P(_Result)]),
         "orc_tabu_search_batch": (C.c_int, [P(_Inst), C.c_int, P(_Params), P(_Result), C.c_int]),
+        "orc_exp_neg": (C.c_double, [C.c_double]),
+        "orc_assigned_iterations": (C.c_int, [C.c_int, C.c_int, C.c_longlong, C.c_int]),
+        "orc_diversify": (C.c_int, [P(_Inst), P(C.c_int), C.c_int, C.c_int, P(C.c_uint), C.c_int,
+                                    P(C.c_int)]),
+        "orc_coop_search": (C.c_int, [P(_Inst), P(_Params), P(_CoopParams), P(P(C.c_int)), P(C.c_uint),
+                                      P(_Result), P(_CoopEvent), C.c_int, P(C.c_int)]),
         "orc_brute_force_lists": (C.c_int, [P(_Inst), C.c_int, P(C.c_longlong)]),
         "orc_brute_force_starts": (C.c_int, [P(_Inst)]),
     }
@@ -214,3 +232,73 @@ def brute_force_lists(inst, mode=TIME) -> tuple:
 
 def brute_force_starts(inst) -> int:
     return _lib().orc_brute_force_starts(C.byref(_Marshalled(inst).s))
+
+
+# ---------------------------------------------------------------------------
+# Sec. 6.1: co-operating searches (readings C1-C8 in the C source)
+# ---------------------------------------------------------------------------
+COOP_EVENT_FIELDS = [f for f, _ in _CoopEvent._fields_]
+
+
+def exp_neg(x: float) -> float:
+    return _lib().orc_exp_neg(float(x))
+
+
+def assigned_iterations(c_k: int, c_star: int, ic_k: int, i_block: int) -> int:
+    return _lib().orc_assigned_iterations(int(c_k), int(c_star), int(ic_k), int(i_block))
+
+
+def diversify(inst, W, delta: int, steps: int, words, cursor: int = 0) -> tuple:
+    """Returns (new list, swaps applied, new cursor)."""
+    W = np.array(W, np.int32)
+    words = np.ascontiguousarray(words, np.uint32)
+    cur = C.c_int(cursor)
+    done = _lib().orc_diversify(C.byref(_Marshalled(inst).s), _ip(W), delta, steps,
+                                words.ctypes.data_as(C.POINTER(C.c_uint)), len(words), C.byref(cur))
+    return W, done, cur.value
+
+
+def coop_search(inst, iterations=100, delta=20, tabu_len=60, mode=AUTO, stop_at_cp=1, blocks=4,
+                working_set=16, phi_max=3, phi_steps=20, assign_fixed=0, slot_keys=None, words=None,
+                log_cap=0) -> dict:
+    """B co-operating searches of one instance through a working set of
+    `working_set` slots.  slot_keys: None or a list of |F| entries (None or
+    N keys).  words: uint32 [blocks, P] random words (None if phi_steps == 0).
+    With log_cap > 0 the result carries the exchange events under "log"."""
+    mi = _Marshalled(inst)
+    p = _Params(iterations, delta, tabu_len, mode, stop_at_cp)
+    keep = []
+    keys_arr = None
+    if slot_keys is not None:
+        keys_arr = (C.POINTER(C.c_int) * working_set)()
+        for k in range(working_set):
+            if slot_keys[k] is not None:
+                a = np.ascontiguousarray(slot_keys[k], np.int32)
+                keep.append(a)
+                keys_arr[k] = _ip(a)
+    P = 0
+    wptr = None
+    if words is not None:
+        w = np.ascontiguousarray(words, np.uint32).reshape(blocks, -1)
+        keep.append(w)
+        P = w.shape[1]
+        wptr = w.ctypes.data_as(C.POINTER(C.c_uint))
+    cp = _CoopParams(blocks, working_set, phi_max, phi_steps, assign_fixed, P)
+    r, W, S, _ = _result_buffers(inst.n, iterations, False)
+    ev = (_CoopEvent * max(1, log_cap))()
+    n_ev = C.c_int(0)
+    _lib().orc_coop_search(C.byref(mi.s), C.byref(p), C.byref(cp), keys_arr, wptr, C.byref(r),
+                           ev if log_cap > 0 else None, log_cap, C.byref(n_ev))
+    d = _to_dict(r, W, S, None)
+    if log_cap > 0:
+        d["log"] = [{f: getattr(ev[k], f) for f in COOP_EVENT_FIELDS} for k in range(min(n_ev.value, log_cap))]
+        d["log_events"] = n_ev.value
+    return d
+
+
+def coop_search_batch(insts: Sequence, kwargs: Sequence[dict], nthreads: int) -> List[dict]:
+    """coop_search over a pool of host threads (the C calls run without the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+    _lib()
+    with ThreadPoolExecutor(max_workers=max(1, nthreads)) as ex:
+        return list(ex.map(lambda a: coop_search(a[0], **a[1]), zip(insts, kwargs)))

@@ -14,6 +14,8 @@
  *   - capacity-indexed ... Alg. 7 with Eq. 7 and Alg. 4 (Sec. 5.1)
  *   - tabu list .......... Algs. 2-3 (Sec. 4.5)
  *   - search loop ........ Sec. 6 (one block's main loop, no working set)
+ *   - co-operation ....... Sec. 6.1, Eq. 8 (blocks exchanging through the
+ *                          working set F; readings C1-C8 beside the code)
  *
  * Readings where the paper is silent, garbled or ambiguous (each one is
  * also listed with the design notes of the repository):
@@ -444,6 +446,316 @@ int orc_tabu_search_batch(const orc_instance *in, int count, const orc_params *p
     int rc = 0;
     for (int k = 0; k < count; ++k) if (res[k].status != 0) rc = res[k].status;
     return rc;
+}
+
+/* -------------- Sec. 6.1: co-operation through a working set ------------ */
+/*
+ * The paper's blocks run asynchronously and lock the working set, so the
+ * order of their exchanges is not defined.  Readings:
+ *   C1  The B searches advance in lockstep, one iteration each; after every
+ *       iteration come the exchanges: first all writes, then all reads,
+ *       each in block order.
+ *   C2  C*_max (aspiration threshold, Eq. 8) is the best makespan known when
+ *       the iteration starts: the working set's best and every block's best
+ *       since its last read.
+ *   C3  A block exchanges when its best makespan since its last read is
+ *       below the makespan of the solution it read (an improvement), or
+ *       when more than I_assigned iterations have passed since that read.
+ *   C4  A write goes to the slot the block last read, and only if the
+ *       block's best list is better than what the slot holds now; it stores
+ *       that list and makespan, the block's tabu list (entries, write index,
+ *       cache), IC = the IC read plus the block's iterations since the read,
+ *       and clears the slot's read count Phi.  Without a write the slot's IC
+ *       grows by the block's iterations since the read.
+ *   C5  Reads take slots round robin (one pointer for all blocks, starting
+ *       at slot 0), add one to the slot's Phi and copy list, makespan and
+ *       tabu state.  If then Phi > Phi_max, Phi_steps random feasible swaps
+ *       follow: each takes the block's next random word w and applies the
+ *       floor(w * n_f / 2^32)-th of the n_f feasible swaps (u-major order,
+ *       v - u <= delta); the new makespan is decoded and not counted.
+ *   C6  Eq. 8's quantity factor, printed as (1/5) I_block / I_total, is read
+ *       as I_block / 5 ("at least five reads per block"):
+ *       I_assigned = floor(I_block/5 * (0.8 e^{-100 (C^k/C* - 1)} +
+ *       0.2 e^{-4 IC^k / I_block})).  e^{-x} is computed as
+ *       (sum_{i=0..24} (-x/1024)^i / i!)^(2^10), Horner form, IEEE double
+ *       without contraction, 0 for x > 700.  assign_fixed > 0 replaces it.
+ *   C7  Slot k starts from the level order with slot k's shuffle keys
+ *       (Sec. 4.1); the forward-backward improvement is not applied.
+ *   C8  The search ends when the blocks have run I_block iterations each or,
+ *       with stop_at_cp, when C* equals the critical path at the start of
+ *       an iteration.  The result is the best slot (lowest index), unless a
+ *       block's best since its last read is strictly better (lowest block).
+ *       Iterations, evaluated schedules and work add up over the blocks.
+ */
+
+double orc_exp_neg(double x) {
+    if (x > 700.0) return 0.0;
+    double y = x / 1024.0;
+    double t = 1.0;
+    for (int i = 24; i >= 1; --i) t = 1.0 - (y * t) / (double)i;
+    for (int k = 0; k < 10; ++k) t = t * t;
+    return t;
+}
+
+int orc_assigned_iterations(int c_k, int c_star, long long ic_k, int i_block) {
+    if (i_block <= 0) return 0;
+    double xq = c_star > 0 ? 100.0 * ((double)c_k / (double)c_star - 1.0) : 0.0;
+    double xi = 4.0 * ((double)ic_k / (double)i_block);
+    double quality = orc_exp_neg(xq);
+    double intact = orc_exp_neg(xi);
+    double a = 0.8 * quality;
+    double b = 0.2 * intact;
+    double v = ((double)i_block / 5.0) * (a + b);
+    return (int)v;                      /* v >= 0: truncation is the floor */
+}
+
+int orc_diversify(const orc_instance *in, int *W, int delta, int steps, const unsigned *words,
+                  int P, int *cursor) {
+    int N = in->n, done = 0;
+    for (int s = 0; s < steps; ++s) {
+        int nf = 0;
+        for (int u = 1; u <= N - 2; ++u)
+            for (int v = u + 1; v <= N - 2 && v - u <= delta; ++v)
+                nf += orc_move_feasible(in, W, u, v);
+        if (nf == 0) break;
+        unsigned w = words[*cursor % P];
+        *cursor += 1;
+        int pick = (int)(((unsigned long long)w * (unsigned long long)nf) >> 32);
+        int k = 0, applied = 0;
+        for (int u = 1; u <= N - 2 && !applied; ++u)
+            for (int v = u + 1; v <= N - 2 && v - u <= delta; ++v) {
+                if (!orc_move_feasible(in, W, u, v)) continue;
+                if (k++ == pick) {
+                    int x = W[u]; W[u] = W[v]; W[v] = x;
+                    applied = 1;
+                    break;
+                }
+            }
+        ++done;
+    }
+    return done;
+}
+
+typedef struct {          /* tabu state: Alg. 3's list and cache */
+    int *tlU, *tlV;
+    char *cache;          /* N x N */
+    int widx;
+} tabu_t;
+
+typedef struct {          /* one slot k of the working set F */
+    int *W;
+    tabu_t T;
+    int C, phi;
+    long long IC;
+} slot_t;
+
+typedef struct {          /* one co-operating search (a block) */
+    int *W, *Wbb;         /* current list, best list since the last read */
+    tabu_t T;
+    int C, Cbb;           /* current makespan, best since the last read */
+    int slot, Cread, since, assigned, cursor;
+    long long ICread;
+} cblock_t;
+
+static void tabu_copy(tabu_t *dst, const tabu_t *src, int N, int L) {
+    memcpy(dst->tlU, src->tlU, sizeof(int) * (size_t)L);
+    memcpy(dst->tlV, src->tlV, sizeof(int) * (size_t)L);
+    memcpy(dst->cache, src->cache, (size_t)N * (size_t)N);
+    dst->widx = src->widx;
+}
+
+static int tabu_alloc(tabu_t *t, int N, int L) {
+    t->tlU = (int *)calloc((size_t)L, sizeof(int));
+    t->tlV = (int *)calloc((size_t)L, sizeof(int));
+    t->cache = (char *)calloc((size_t)N * (size_t)N, 1);
+    t->widx = 0;
+    return t->tlU && t->tlV && t->cache ? 0 : -1;
+}
+
+static void tabu_free(tabu_t *t) { free(t->tlU); free(t->tlV); free(t->cache); }
+
+static void coop_log(orc_coop_event *log, int cap, int *len, int it, int b, int kind, int slot, int c,
+                     int assigned, int div, int phi, long long ic) {
+    if (!log || *len >= cap) { if (log) ++*len; return; }
+    orc_coop_event *e = &log[*len];
+    e->iteration = it; e->block = b; e->kind = kind; e->slot = slot; e->cmax = c;
+    e->assigned = assigned; e->diversified = div; e->phi = phi; e->ic = ic;
+    ++*len;
+}
+
+int orc_coop_search(const orc_instance *in, const orc_params *p, const orc_coop_params *cp,
+                    const int *const *slot_keys, const unsigned *words, orc_result *res,
+                    orc_coop_event *log, int log_cap, int *log_len) {
+    const int N = in->n, B = cp->blocks, F = cp->working_set, L = p->tabu_len;
+    const int Ib = p->iterations;
+    int log_n = 0;
+    res->status = 0;
+    if (N < 2 || L < 1 || p->max_swap_dist < 1 || Ib < 0 || B < 1 || F < 1 || cp->phi_steps < 0 ||
+        (cp->phi_steps > 0 && (!words || cp->words_per_block < 1))) {
+        res->status = -1;
+        return -1;
+    }
+    const int mode = p->eval_mode == ORC_AUTO ? orc_select_mode(in) : p->eval_mode;
+    preds_t P;
+    if (build_preds(in, &P) != 0) { res->status = -1; return -1; }
+    slot_t *slot = (slot_t *)calloc((size_t)F, sizeof(slot_t));
+    cblock_t *blk = (cblock_t *)calloc((size_t)B, sizeof(cblock_t));
+    int *Wc = (int *)malloc(sizeof(int) * (size_t)N);
+    int *S = (int *)malloc(sizeof(int) * (size_t)N);
+    char *exch = (char *)calloc((size_t)B, 1);
+    int ok = slot && blk && Wc && S && exch;
+    for (int k = 0; ok && k < F; ++k) {
+        slot[k].W = (int *)malloc(sizeof(int) * (size_t)N);
+        ok = slot[k].W && tabu_alloc(&slot[k].T, N, L) == 0;
+    }
+    for (int b = 0; ok && b < B; ++b) {
+        blk[b].W = (int *)malloc(sizeof(int) * (size_t)N);
+        blk[b].Wbb = (int *)malloc(sizeof(int) * (size_t)N);
+        ok = blk[b].W && blk[b].Wbb && tabu_alloc(&blk[b].T, N, L) == 0;
+    }
+    if (!ok) { res->status = -1; goto done; }
+    res->mode = mode;
+    res->cp = orc_critical_path(in);
+#define DECODE(Wl, work_ptr) (mode == ORC_TIME ? decode_time(in, &P, (Wl), S, (work_ptr)) \
+                                               : decode_capacity(in, &P, (Wl), S, (work_ptr)))
+    /* C7: the initial working set */
+    for (int k = 0; k < F; ++k) {
+        orc_instance ik = *in;
+        if (slot_keys) ik.level_key = slot_keys[k];
+        if (orc_initial_order(&ik, slot[k].W) != 0) { res->status = -1; goto done; }
+        slot[k].C = DECODE(slot[k].W, NULL);
+        slot[k].phi = 0;
+        slot[k].IC = 0;
+    }
+    int Cstar = slot[0].C;
+    for (int k = 1; k < F; ++k) if (slot[k].C < Cstar) Cstar = slot[k].C;
+    int rp = 0, its = 0;
+    long long evaluated = 0, work = 0;
+    /* C5: a read of block b */
+#define READ_SLOT(b_, itlog)                                                              \
+    do {                                                                                  \
+        cblock_t *x_ = &blk[(b_)];                                                        \
+        int k_ = rp;                                                                      \
+        rp = (rp + 1) % F;                                                                \
+        slot[k_].phi += 1;                                                                \
+        memcpy(x_->W, slot[k_].W, sizeof(int) * (size_t)N);                               \
+        tabu_copy(&x_->T, &slot[k_].T, N, L);                                             \
+        x_->slot = k_;                                                                    \
+        x_->Cread = slot[k_].C;                                                           \
+        x_->ICread = slot[k_].IC;                                                         \
+        x_->since = 0;                                                                    \
+        int div_ = 0;                                                                     \
+        if (slot[k_].phi > cp->phi_max && cp->phi_steps > 0) {                            \
+            div_ = orc_diversify(in, x_->W, p->max_swap_dist, cp->phi_steps,               \
+                                 words + (size_t)(b_) * (size_t)cp->words_per_block,      \
+                                 cp->words_per_block, &x_->cursor);                        \
+            x_->C = DECODE(x_->W, NULL);                                                  \
+        } else {                                                                          \
+            x_->C = slot[k_].C;                                                           \
+        }                                                                                 \
+        x_->Cbb = x_->C;                                                                  \
+        memcpy(x_->Wbb, x_->W, sizeof(int) * (size_t)N);                                  \
+        x_->assigned = cp->assign_fixed > 0 ? cp->assign_fixed                            \
+                                            : orc_assigned_iterations(slot[k_].C, Cstar,  \
+                                                                      slot[k_].IC, Ib);   \
+        coop_log(log, log_cap, &log_n, (itlog), (b_), 2, k_, x_->C, x_->assigned, div_,   \
+                 slot[k_].phi, slot[k_].IC);                                              \
+    } while (0)
+
+    for (int b = 0; b < B; ++b) READ_SLOT(b, -1);
+    for (int b = 0; b < B; ++b) if (blk[b].Cbb < Cstar) Cstar = blk[b].Cbb;   /* C2 */
+    while (its < Ib) {
+        if (p->stop_at_cp && Cstar == res->cp) break;                 /* C8 */
+        const int Casp = Cstar;
+        /* one Sec. 6 iteration of every block (as orc_tabu_search) */
+        for (int b = 0; b < B; ++b) {
+            cblock_t *x = &blk[b];
+            int found = 0, bu = 0, bv = 0, bc = INT_MAX;
+            for (int u = 1; u <= N - 2; ++u)
+                for (int v = u + 1; v <= N - 2 && v - u <= p->max_swap_dist; ++v) {
+                    if (!orc_move_feasible(in, x->W, u, v)) continue;
+                    memcpy(Wc, x->W, sizeof(int) * (size_t)N);
+                    Wc[u] = x->W[v];
+                    Wc[v] = x->W[u];
+                    int c = DECODE(Wc, &work);
+                    ++evaluated;
+                    int tabu = x->T.cache[u * N + v];                /* Alg. 2 */
+                    if (tabu && !(c < Casp)) continue;              /* aspiration, C2 */
+                    if (!found || c < bc) { found = 1; bu = u; bv = v; bc = c; }
+                }
+            if (found) {
+                int t = x->W[bu]; x->W[bu] = x->W[bv]; x->W[bv] = t;
+                x->C = bc;
+            } else {
+                bu = 0; bv = 0;
+            }
+            int uo = x->T.tlU[x->T.widx], vo = x->T.tlV[x->T.widx];  /* Alg. 3 */
+            x->T.cache[uo * N + vo] = 0;
+            x->T.tlU[x->T.widx] = bu;
+            x->T.tlV[x->T.widx] = bv;
+            x->T.cache[bu * N + bv] = 1;
+            x->T.widx = (x->T.widx + 1) % L;
+            if (x->C < x->Cbb) {
+                x->Cbb = x->C;
+                memcpy(x->Wbb, x->W, sizeof(int) * (size_t)N);
+            }
+            x->since += 1;
+        }
+        its += 1;
+        for (int b = 0; b < B; ++b) if (blk[b].Cbb < Cstar) Cstar = blk[b].Cbb;
+        /* C3, C4: writes in block order */
+        for (int b = 0; b < B; ++b) {
+            cblock_t *x = &blk[b];
+            int improved = x->Cbb < x->Cread;
+            exch[b] = (char)(improved || x->since > x->assigned);
+            if (!exch[b]) continue;
+            slot_t *f = &slot[x->slot];
+            if (improved && x->Cbb < f->C) {
+                memcpy(f->W, x->Wbb, sizeof(int) * (size_t)N);
+                tabu_copy(&f->T, &x->T, N, L);
+                f->C = x->Cbb;
+                f->IC = x->ICread + x->since;
+                f->phi = 0;
+                coop_log(log, log_cap, &log_n, its, b, 1, x->slot, f->C, 0, 0, f->phi, f->IC);
+            } else {
+                f->IC += x->since;
+                if (improved)
+                    coop_log(log, log_cap, &log_n, its, b, 3, x->slot, x->Cbb, 0, 0, f->phi, f->IC);
+            }
+        }
+        /* C5: reads in block order */
+        if (its < Ib)
+            for (int b = 0; b < B; ++b)
+                if (exch[b]) READ_SLOT(b, its);
+        for (int b = 0; b < B; ++b) if (blk[b].Cbb < Cstar) Cstar = blk[b].Cbb;
+    }
+    /* C8: the result */
+    {
+        const int *Wb = slot[0].W;
+        int Cb = slot[0].C;
+        for (int k = 1; k < F; ++k)
+            if (slot[k].C < Cb) { Cb = slot[k].C; Wb = slot[k].W; }
+        for (int b = 0; b < B; ++b)
+            if (blk[b].Cbb < Cb) { Cb = blk[b].Cbb; Wb = blk[b].Wbb; }
+        memcpy(res->best_W, Wb, sizeof(int) * (size_t)N);
+        res->best_cmax = mode == ORC_TIME ? decode_time(in, &P, res->best_W, res->best_S, NULL)
+                                          : decode_capacity(in, &P, res->best_W, res->best_S, NULL);
+        if (res->best_cmax != Cb || Cb != Cstar) res->status = -2;   /* self-check */
+    }
+    res->iterations = its * B;
+    res->evaluated = evaluated;
+    res->work = work;
+#undef READ_SLOT
+#undef DECODE
+done:
+    if (log_len) *log_len = log_n;
+    if (slot)
+        for (int k = 0; k < F; ++k) { free(slot[k].W); tabu_free(&slot[k].T); }
+    if (blk)
+        for (int b = 0; b < B; ++b) { free(blk[b].W); free(blk[b].Wbb); tabu_free(&blk[b].T); }
+    free(slot); free(blk); free(Wc); free(S); free(exch);
+    free_preds(&P);
+    return res->status;
 }
 
 /* -------------------- brute force over activity lists -------------------- */

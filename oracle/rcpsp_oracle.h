@@ -85,6 +85,47 @@ int orc_tabu_search(const orc_instance *in, const orc_params *p, orc_result *res
 /* Many independent searches over a pool of nthreads host threads. */
 int orc_tabu_search_batch(const orc_instance *in, int count, const orc_params *p,
                           orc_result *res, int nthreads);
+/* ---- Sec. 6.1: co-operating searches through a working set F ---------- */
+typedef struct {
+    int blocks;            /* B co-operating searches */
+    int working_set;       /* |F| */
+    int phi_max;           /* Phi_max: reads without improvement before diversification */
+    int phi_steps;         /* Phi_steps: random feasible swaps of a diversification */
+    int assign_fixed;      /* iterations per read; 0 = Eq. 8 */
+    int words_per_block;   /* P: random words of each block, used cyclically */
+} orc_coop_params;
+
+/* One exchange event of orc_coop_search (optional log). */
+typedef struct {
+    int iteration;         /* iterations every block had run; -1 = initial reads */
+    int block;
+    int kind;              /* 1 write, 2 read, 3 improved but the slot was better */
+    int slot;
+    int cmax;              /* write: C written; read: C of the block after the read */
+    int assigned;          /* read: I_assigned */
+    int diversified;       /* read: swaps applied */
+    int phi;               /* slot's read count after the event */
+    long long ic;          /* slot's iterations counter after the event */
+} orc_coop_event;
+
+/* e^{-x} for x >= 0 in IEEE double, by the fixed recipe of reading C6. */
+double orc_exp_neg(double x);
+/* Eq. 8 (reading C6): iterations assigned to a read of slot k. */
+int orc_assigned_iterations(int c_k, int c_star, long long ic_k, int i_block);
+/* Diversification (reading C5): up to `steps` random feasible swaps of W;
+ * words are taken cyclically from words[0..P-1] starting at *cursor, which
+ * advances by one per swap.  Returns the swaps applied. */
+int orc_diversify(const orc_instance *in, int *W, int delta, int steps, const unsigned *words,
+                  int P, int *cursor);
+/* B searches co-operating through |F| slots (Sec. 6.1, readings C1-C8).
+ * slot_keys: NULL, or |F| pointers (each NULL or N keys) giving slot k's
+ * initial order.  words: [B*P] (may be NULL when phi_steps == 0).  Result:
+ * best slot / block list, iterations and evaluated summed over blocks.  log
+ * (nullable) receives up to log_cap events, *log_len the number written. */
+int orc_coop_search(const orc_instance *in, const orc_params *p, const orc_coop_params *cp,
+                    const int *const *slot_keys, const unsigned *words, orc_result *res,
+                    orc_coop_event *log, int log_cap, int *log_len);
+
 /* Minimum C_max over every precedence-feasible list (dummies fixed),
  * decoded with `mode`; *lists (nullable) = number of lists.  Small N only. */
 int orc_brute_force_lists(const orc_instance *in, int mode, long long *lists);

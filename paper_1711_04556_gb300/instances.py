@@ -257,6 +257,19 @@ def level_keys(inst: Instance, seed: int) -> np.ndarray:
     return rng.integers(0, 2**31 - 1, inst.n).astype(np.int32)
 
 
+def coop_inputs(inst: Instance, seed: int, working_set: int, blocks: int, words_per_block: int):
+    """Inputs of a co-operative search (Sec. 6.1): the shuffle keys of the
+    working set's initial lists (slot 0 keeps the unshuffled level order,
+    slot k >= 1 uses level_keys(inst, seed + k)) and the random words the
+    blocks draw their diversification swaps from, [blocks, words_per_block]
+    uint32.  Drawn here and passed to both the CUDA path and the CPU
+    reference as inputs."""
+    keys = [None] + [level_keys(inst, seed + k) for k in range(1, working_set)]
+    rng = np.random.Generator(np.random.Philox(key=[seed, 0xD1CE]))
+    words = rng.integers(0, 2**32, (blocks, words_per_block), dtype=np.uint64).astype(np.uint32)
+    return keys, words
+
+
 # --------------------------------------------------------------------------
 # Workload families (instance batches); parameters per family are the
 # search parameters of Table 2 where the paper gives them.

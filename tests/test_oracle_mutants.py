@@ -27,6 +27,15 @@ MUTANTS = {
     "alg4_copy_offset": ("if (copyIdx >= r) newTime", "if (copyIdx > r) newTime"),
     # Alg. 5 window not restarted on an insufficient step
     "alg5_no_restart": ("{ loadTime = 0; sufficient = 0; }", "{ sufficient = 0; }"),
+    # Eq. 8 with the quality and intactness weights swapped
+    "eq8_weights_swapped": ("double a = 0.8 * quality;", "double a = 0.2 * quality;"),
+    # random swap picked by a remainder instead of the scaled draw
+    "diversify_by_remainder": ("int pick = (int)(((unsigned long long)w * (unsigned long long)nf) >> 32);",
+                               "int pick = (int)(w % (unsigned)nf);"),
+    # working-set reads skipping every other slot
+    "reads_skip_slots": ("rp = (rp + 1) % F;", "rp = (rp + 2) % F;"),
+    # a block's improvement not written back to the working set
+    "no_write_back": ("if (improved && x->Cbb < f->C) {", "if (improved && x->Cbb < f->C && 0) {"),
 }
 
 
@@ -39,7 +48,7 @@ def mutant(oracle, tmp_path, name):
     mut.write_text(src.replace(old, new))
     (tmp_path / "rcpsp_oracle.h").write_text(open(oracle.HDR).read())
     so = tmp_path / f"lib{name}.so"
-    subprocess.run(["gcc", "-O1", "-std=c11", "-shared", "-fPIC", "-pthread", "-o", str(so), str(mut)],
+    subprocess.run(["gcc", "-O1", "-std=c11", "-ffp-contract=off", "-shared", "-fPIC", "-pthread", "-o", str(so), str(mut)],
                    check=True)
     saved = oracle._handle
     oracle._handle = oracle.load(str(so))
@@ -80,3 +89,28 @@ def test_mutant_alg5_breaks_earliest_fit_pin(oracle, tmp_path):
     with mutant(oracle, tmp_path, "alg5_no_restart"):
         with pytest.raises(AssertionError):
             pins.test_decoders_on_random_lists(oracle)
+
+
+def test_mutant_eq8_weights_break_closed_forms(oracle, tmp_path):
+    import test_oracle_coop as coop
+    with mutant(oracle, tmp_path, "eq8_weights_swapped"):
+        with pytest.raises(AssertionError):
+            coop.test_eq8_prefers_good_and_fresh_solutions(oracle)
+
+
+def test_mutant_diversify_breaks_drawn_swaps(oracle, tmp_path):
+    import test_oracle_coop as coop
+    with mutant(oracle, tmp_path, "diversify_by_remainder"):
+        with pytest.raises(AssertionError):
+            coop.test_diversify_takes_the_drawn_feasible_swaps(oracle)
+
+
+@pytest.mark.parametrize("name", ["reads_skip_slots", "no_write_back"])
+def test_mutant_exchange_breaks_rules(oracle, tmp_path, name):
+    import test_oracle_coop as coop
+    with mutant(oracle, tmp_path, name):
+        with pytest.raises(AssertionError):
+            if name == "reads_skip_slots":
+                coop.test_exchange_rules(oracle, 4, 8, 1)
+            else:
+                coop.test_single_block_without_exchanges_is_the_plain_search(oracle, 1)
