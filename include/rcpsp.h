@@ -152,6 +152,49 @@ int rcpsp_free_instances(rcpsp_ctx *ctx, const int32_t *ids, int32_t count);
 int rcpsp_tabu_search(rcpsp_ctx *ctx, const int32_t *ids, int32_t count,
                       const rcpsp_params *params, void *cuda_stream);
 
+/* Co-operating searches (Sec. 6.1, Eq. 8).  Each instance is searched by
+ * `blocks` tabu searches -- one CTA each, the CTAs of one thread-block
+ * cluster -- that exchange solutions through a working set F of
+ * `working_set` slots in device memory.  Slot k starts from the level order
+ * of Sec. 4.1 with slot k's shuffle keys.  Every block reads a slot, then
+ * runs the search of rcpsp_tabu_search on it; when its best list since the
+ * read is better than the slot it read, or after more than I_assigned
+ * iterations without that (Eq. 8, quantity factor read as I_block / 5), it
+ * writes its best list and tabu state back to that slot (only if better
+ * than what the slot now holds) and reads the next slot round robin.  A
+ * slot read more than phi_max times since its last improvement is
+ * diversified on reading by phi_steps random feasible swaps.  The blocks
+ * advance in lockstep and exchange in block order (writes, then reads) after
+ * every iteration, so the result is deterministic and independent of the
+ * launch; the paper's blocks exchange asynchronously under locks.
+ * params->iterations = I_block, the iterations of each block; the result
+ * (rcpsp_get_schedules) is the best list found, with iterations and
+ * evaluated schedules summed over the blocks.  */
+typedef struct {
+    int32_t blocks;            /* B, 1..16: searches per instance (CTAs per cluster) */
+    int32_t working_set;       /* |F|, 1..64 (the paper: 16)                         */
+    int32_t phi_max;           /* Phi_max (the paper: 3)                             */
+    int32_t phi_steps;         /* Phi_steps (the paper: 20); 0 = no diversification  */
+    int32_t assign_fixed;      /* iterations per read; 0 = Eq. 8                     */
+    int32_t words_per_block;   /* P: random words per block in random_words          */
+} rcpsp_coop_params;
+
+/* Runs co-operating searches of the loaded instances `ids` (asynchronous on
+ * cuda_stream, like rcpsp_tabu_search; no trace, no graph capture:
+ * record_trace / use_graph = 1 give RCPSP_E_INVALID_ARG).  slot_keys (host,
+ * copied, may be NULL = every slot unshuffled): for each id in order,
+ * working_set rows of N shuffle keys (Sec. 4.1; all zeros = unshuffled).
+ * random_words (host, copied; NULL allowed when phi_steps == 0): for each id
+ * in order, blocks rows of words_per_block uint32, the words block b draws
+ * its swaps from, used cyclically: each swap takes the next word w and
+ * applies the floor(w * n_f / 2^32)-th of the n_f feasible swaps
+ * (1 <= u < v <= N-2, v - u <= delta, Eqs. 5-6), in u-major order.  Errors:
+ * RCPSP_E_INVALID_ARG (parameters), RCPSP_E_NOT_FOUND (id),
+ * RCPSP_E_TOO_LARGE (state or cluster does not fit), RCPSP_E_CUDA. */
+int rcpsp_coop_search(rcpsp_ctx *ctx, const int32_t *ids, int32_t count, const rcpsp_params *params,
+                      const rcpsp_coop_params *coop, const int32_t *slot_keys,
+                      const uint32_t *random_words, void *cuda_stream);
+
 /* The same search as rcpsp_tabu_search, for callers that cannot allocate
  * device memory when they search: for example a serving process whose
  * device memory is owned by another allocator with a fixed budget, or a

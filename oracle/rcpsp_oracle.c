@@ -204,7 +204,7 @@ static int decode_time(const orc_instance *in, const preds_t *P, const int *W, i
     for (int k = 0; k < M; ++k)
         for (int t = 0; t < UB; ++t) tau[k * UB + t] = in->cap[k];
     long long steps = 0;
-    int Cmax = 0;                                                /* Alg. 7 l.1 */
+    int Cmax = 0;                                                /* Alg. 7: C_max from 0 */
     for (int u = 0; u < N; ++u) {
         int i = W[u];
         int es_prec = 0;

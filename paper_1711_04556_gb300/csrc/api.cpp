@@ -79,6 +79,11 @@ struct rcpsp_ctx {
     cudaStream_t aux[kAuxStreams] = {};
     cudaEvent_t fork = nullptr, join[kAuxStreams] = {};
     std::vector<int> g_launch_sig;
+    // co-operative searches: plan, initial lists, random words and working sets
+    void *coop_dev = nullptr;
+    size_t coop_cap = 0;
+    char *coop_host = nullptr;          // pinned staging of the uploaded part
+    size_t coop_host_cap = 0;
     // measured launch shapes: workload signature -> (G, warps, CTAs per search)
     std::vector<std::pair<std::string, std::array<int, 3>>> tuned;
 };
@@ -331,7 +336,9 @@ int rcpsp_destroy(rcpsp_ctx *c) {
     for (Block &b : c->blocks) dev_free(c, b.ptr, b.bytes, nullptr);
     dev_free(c, c->items_dev, c->items_cap, nullptr);
     dev_free(c, c->queue_dev, 64, nullptr);
+    dev_free(c, c->coop_dev, c->coop_cap, nullptr);
     if (c->items_host) cudaFreeHost(c->items_host);
+    if (c->coop_host) cudaFreeHost(c->coop_host);
     cudaEventDestroy(c->done);
     cudaEventDestroy(c->fork);
     for (int q = 0; q < kAuxStreams; ++q) {
@@ -647,6 +654,147 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
         if (e != cudaSuccess) return cuda_err(c, e, "search launch");
     }
     c->kernels += static_cast<long long>(launches.size());
+    e = cudaEventRecord(c->done, st);
+    if (e != cudaSuccess) return cuda_err(c, e, "event record");
+    c->pending = true;
+    return RCPSP_OK;
+}
+
+int rcpsp_coop_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcpsp_params *p,
+                      const rcpsp_coop_params *cp, const int32_t *slot_keys, const uint32_t *random_words,
+                      void *stream) {
+    if (!c) return RCPSP_E_INVALID_ARG;
+    if (!p || !cp || count < 0 || (count > 0 && !ids)) return set_err(c, RCPSP_E_INVALID_ARG, "bad arguments");
+    if (p->iterations < 0 || p->max_swap_dist < 0 || p->tabu_len < 0 || p->tabu_len > RCPSP_MAX_TABU ||
+        p->eval_mode < 0 || p->eval_mode > 2 || p->warps_per_cta < 0 || p->warps_per_cta > 16)
+        return set_err(c, RCPSP_E_INVALID_ARG, "bad search parameters");
+    const int gs = p->group_size;
+    if (gs != 0 && gs != 1 && gs != 2 && gs != 4 && gs != 8 && gs != 16 && gs != 32)
+        return set_err(c, RCPSP_E_INVALID_ARG, "group_size must be 0, 1, 2, 4, 8, 16 or 32");
+    if (p->record_trace || p->use_graph)
+        return set_err(c, RCPSP_E_INVALID_ARG, "co-operative searches keep no trace and capture no graph");
+    const int B = cp->blocks, F = cp->working_set, P = cp->words_per_block;
+    if (B < 1 || B > rcpsp::kMaxCoopBlocks || F < 1 || F > rcpsp::kMaxWorkingSet || cp->phi_max < 0 ||
+        cp->phi_steps < 0 || cp->assign_fixed < 0 || P < 0)
+        return set_err(c, RCPSP_E_INVALID_ARG, "bad co-operation parameters");
+    if (cp->phi_steps > 0 && (!random_words || P < 1))
+        return set_err(c, RCPSP_E_INVALID_ARG, "diversification needs random words");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaSetDevice(c->device);
+    int rc = wait_done(c);
+    if (rc != RCPSP_OK) return rc;
+    if (count == 0) return RCPSP_OK;
+    std::vector<LaunchItem> items(count);
+    std::vector<double> cost(count);
+    std::vector<size_t> key_off(count);
+    size_t keys_total = 0;
+    for (int k = 0; k < count; ++k) {
+        const int id = ids[k];
+        if (id < 0 || id >= static_cast<int>(c->insts.size()) || !c->insts[id].alive)
+            return set_err(c, RCPSP_E_NOT_FOUND, "unknown instance id");
+        Inst &in = c->insts[id];
+        LaunchItem &it = items[k];
+        std::memset(&it, 0, sizeof(it));
+        it.h = in.h;
+        it.record = in.record;
+        it.out = in.out;
+        it.mode = p->eval_mode == RCPSP_EVAL_AUTO ? in.h.sel_mode : p->eval_mode;
+        int dd, tl;
+        rcpsp::default_search_params(in.h.n, &dd, &tl);
+        it.delta = std::max(1, std::min(p->max_swap_dist ? p->max_swap_dist : dd, in.h.n - 3));
+        it.tabu_len = p->tabu_len ? p->tabu_len : tl;
+        it.iterations = p->iterations;
+        it.stop_at_cp = p->stop_at_cp ? 1 : 0;
+        in.trace_iters = -1;
+        cost[k] = B * rcpsp::estimate_cost(in.h, it.mode, it.iterations, it.delta);
+        key_off[k] = keys_total;
+        keys_total += static_cast<size_t>(F) * in.h.n;
+    }
+    // launch shape: one for the call, every CTA of a cluster alike
+    int G = gs, warps = p->warps_per_cta, dG, dW;
+    default_shape(items, &dG, &dW);
+    if (!G) G = dG;
+    if (!warps) warps = std::max(dW, (G + 31) / 32);
+    const int move_cap = launch_move_cap(items);
+    const size_t static_smem = 3072;                       // the kernel's own bookkeeping
+    const size_t smem_limit =
+        c->prop.sharedMemPerBlockOptin > static_smem ? c->prop.sharedMemPerBlockOptin - static_smem : 0;
+    size_t smem = smem_bytes(items, warps * (32 / G), move_cap);
+    while (smem > smem_limit && p->warps_per_cta == 0 && warps > 1) {
+        --warps;
+        smem = smem_bytes(items, warps * (32 / G), move_cap);
+    }
+    if (smem > smem_limit)
+        return set_err(c, RCPSP_E_TOO_LARGE, "instance state does not fit in shared memory at this launch shape");
+    int clusters = 0;
+    cudaError_t e = rcpsp::coop_occupancy(G, warps * 32, smem, B, &clusters);
+    if (e != cudaSuccess) return cuda_err(c, e, "co-operative occupancy");
+    if (clusters < 1) return set_err(c, RCPSP_E_TOO_LARGE, "a cluster of this many CTAs does not fit at this shape");
+    // device block: [plan][initial lists][random words][working sets]; the
+    // first three are uploaded, the working sets are written by the kernel
+    std::vector<int> order(count);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    auto up16 = [](size_t x) { return (x + 15) & ~static_cast<size_t>(15); };
+    const size_t plan_bytes = up16(sizeof(rcpsp::CoopItem) * count);
+    const size_t lists_bytes = up16(keys_total * 4);
+    const size_t words_bytes = up16(random_words ? static_cast<size_t>(count) * B * P * 4 : 0);
+    size_t slots_bytes = 0;
+    std::vector<size_t> slot_off(count);
+    for (int k = 0; k < count; ++k) {
+        slot_off[k] = slots_bytes;
+        const rcpsp::SlotLayout SL = rcpsp::slot_layout(items[k].h.n, items[k].tabu_len, items[k].delta);
+        slots_bytes += up16(static_cast<size_t>(F) * SL.words * 4);
+    }
+    const size_t up_bytes = plan_bytes + lists_bytes + words_bytes;
+    const size_t total = up_bytes + slots_bytes;
+    if (c->coop_cap < total) {
+        dev_free(c, c->coop_dev, c->coop_cap, nullptr);
+        c->coop_dev = dev_alloc(c, total, nullptr);
+        c->coop_cap = c->coop_dev ? total : 0;
+        if (!c->coop_dev) return set_err(c, RCPSP_E_CUDA, "working-set allocation failed");
+    }
+    if (c->coop_host_cap < up_bytes) {
+        if (c->coop_host) cudaFreeHost(c->coop_host);
+        c->coop_host = nullptr;
+        c->coop_host_cap = 0;
+        e = cudaMallocHost(reinterpret_cast<void **>(&c->coop_host), up_bytes);
+        if (e != cudaSuccess) return cuda_err(c, e, "pinned staging");
+        c->coop_host_cap = up_bytes;
+    }
+    char *hb = c->coop_host, *db = static_cast<char *>(c->coop_dev);
+    std::memset(hb, 0, up_bytes);
+    auto *plan = reinterpret_cast<rcpsp::CoopItem *>(hb);
+    auto *lists = reinterpret_cast<int32_t *>(hb + plan_bytes);
+    for (int q = 0; q < count; ++q) {
+        const int k = order[q];
+        const Inst &in = c->insts[ids[k]];
+        const int n = in.h.n;
+        for (int f = 0; f < F; ++f)
+            rcpsp::level_order(n, in.succ_off.data(), in.succ.data(),
+                               slot_keys ? slot_keys + key_off[k] + static_cast<size_t>(f) * n : nullptr,
+                               lists + key_off[k] + static_cast<size_t>(f) * n);
+        rcpsp::CoopItem &ci = plan[q];
+        ci.base = items[k];
+        ci.slots = reinterpret_cast<int32_t *>(db + up_bytes + slot_off[k]);
+        ci.init_lists = reinterpret_cast<const int32_t *>(db + plan_bytes) + key_off[k];
+        ci.words = random_words ? reinterpret_cast<const uint32_t *>(db + plan_bytes + lists_bytes) +
+                                      static_cast<size_t>(k) * B * P
+                                : nullptr;
+        ci.slot_words = rcpsp::slot_layout(n, items[k].tabu_len, items[k].delta).words;
+    }
+    if (random_words)
+        std::memcpy(hb + plan_bytes + lists_bytes, random_words, static_cast<size_t>(count) * B * P * 4);
+    e = cudaMemcpyAsync(db, hb, up_bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->queue_dev, 0, sizeof(int), st);
+    rcpsp::CoopConfig cfg{B, F, cp->phi_max, cp->phi_steps, cp->assign_fixed, P};
+    const int nclusters = std::max(1, std::min(count, clusters));
+    if (e == cudaSuccess)
+        e = rcpsp::launch_coop(G, reinterpret_cast<const rcpsp::CoopItem *>(db), count, c->queue_dev, move_cap, cfg,
+                               nclusters * B, warps * 32, smem, st);
+    if (e != cudaSuccess) return cuda_err(c, e, "co-operative search launch");
+    c->h2d += static_cast<long long>(up_bytes);
+    c->kernels += 1;
     e = cudaEventRecord(c->done, st);
     if (e != cudaSuccess) return cuda_err(c, e, "event record");
     c->pending = true;

@@ -32,6 +32,31 @@ int fail(std::string &err, int code, const std::string &msg) {
 
 }  // namespace
 
+void level_order(int n, const int32_t *succ_off, const int32_t *succ, const int32_t *keys, int32_t *W) {
+    std::vector<int> indeg(n, 0), order, level(n, 0);
+    for (int e = 0; e < succ_off[n]; ++e) ++indeg[succ[e]];
+    order.reserve(n);
+    for (int i = 0; i < n; ++i)
+        if (indeg[i] == 0) order.push_back(i);
+    for (size_t h = 0; h < order.size(); ++h) {
+        const int i = order[h];
+        for (int e = succ_off[i]; e < succ_off[i + 1]; ++e) {
+            const int j = succ[e];
+            level[j] = std::max(level[j], level[i] + 1);
+            if (--indeg[j] == 0) order.push_back(j);
+        }
+    }
+    std::vector<int> w(n);
+    std::iota(w.begin(), w.end(), 0);
+    std::stable_sort(w.begin(), w.end(), [&](int a, int b) {
+        if (level[a] != level[b]) return level[a] < level[b];
+        const int ka = keys ? keys[a] : 0, kb = keys ? keys[b] : 0;
+        if (ka != kb) return ka < kb;
+        return a < b;
+    });
+    for (int i = 0; i < n; ++i) W[i] = w[i];
+}
+
 int select_evaluator(int m, const int32_t *cap, int critical_path) {
     long long sum_r = 0;
     for (int k = 0; k < m; ++k) sum_r += cap[k];

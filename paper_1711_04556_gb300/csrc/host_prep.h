@@ -19,6 +19,10 @@ struct PackedInstance {
 // with a message in `err`.
 int prepare_instance(const rcpsp_instance &in, PackedInstance &out, std::string &err);
 
+// Initial list of a validated precedence graph (Sec. 4.1): activities by
+// (level, key, label), key 0 when `keys` is null.
+void level_order(int n, const int32_t *succ_off, const int32_t *succ, const int32_t *keys, int32_t *W);
+
 // Evaluator chosen by the selection rule (Sec. 5.4) from the capacities and
 // the critical-path length.
 int select_evaluator(int m, const int32_t *cap, int critical_path);

@@ -49,6 +49,31 @@ struct LaunchItem {
 };
 static_assert(sizeof(LaunchItem) == 112, "LaunchItem is 112 bytes");
 
+// One entry of a co-operative launch (160 bytes): the search of `base` run
+// by a cluster of CTAs that exchange solutions through a working set F
+// (Sec. 6.1) in device memory.
+struct CoopItem {
+    LaunchItem base;                 // instance, outputs, search parameters (no trace)
+    int32_t *slots;                  // F: working_set slots of slot_words words (SlotLayout)
+    const int32_t *init_lists;       // [working_set][N] initial list of every slot
+    const uint32_t *words;           // [blocks][words_per_block] random words
+    int32_t slot_words;
+    int32_t pad[5];
+};
+static_assert(sizeof(CoopItem) == 160, "CoopItem is 160 bytes");
+
+// Launch-wide parameters of the co-operation (identical for every item).
+struct CoopConfig {
+    int32_t blocks;                  // B = CTAs per cluster
+    int32_t working_set;             // |F|
+    int32_t phi_max, phi_steps;      // diversification
+    int32_t assign_fixed;            // iterations per read; 0 = Eq. 8
+    int32_t words_per_block;         // P
+};
+
+constexpr int kMaxCoopBlocks = 16;   // largest cluster (non-portable above 8)
+constexpr int kMaxWorkingSet = 64;
+
 // Statistics words after W* and S* in the output block of an instance.
 enum : int {
     kOutEvalLo = 0, kOutEvalHi, kOutWorkLo, kOutWorkHi,
@@ -111,6 +136,24 @@ RC_HD StateLayout state_layout(int inst_words, int n, int tabu_len, int delta, i
     o += ngroups * S.group_words;
     S.total = o;
     return S;
+}
+
+// Words of one working-set slot: the list W, the tabu list (packed pairs),
+// the tabu cache (banded bits, as in shared memory), then the write index
+// and the makespan of the slot's initial list (the kernel keeps the current
+// makespans in shared memory).
+struct SlotLayout {
+    int W, stl, tc, widx, words;
+};
+
+RC_HD SlotLayout slot_layout(int n, int tabu_len, int delta) {
+    SlotLayout L;
+    L.W = 0;
+    L.stl = align4(n);
+    L.tc = L.stl + align4(tabu_len);
+    L.widx = L.tc + align4((n * delta + 31) / 32);
+    L.words = L.widx + 4;
+    return L;
 }
 
 }  // namespace rcpsp

@@ -26,379 +26,11 @@
 //
 // The kernel never spins: the work queue is a single atomicAdd.  Internal
 // inconsistencies set an error word that the host reads as a status.
-#include <cooperative_groups.h>
-#include <cuda_runtime.h>
-#include <limits.h>
-#include <stdint.h>
-
+#include "device_search.cuh"
 #include "kernels.h"
-#include "rcpsp_internal.h"
 
 namespace rcpsp {
 namespace {
-
-namespace cg = cooperative_groups;
-
-constexpr unsigned kFull = 0xffffffffu;
-constexpr int kErrHorizon = 1;     // a profile window ran past UB
-
-// G lanes of a warp that decode one neighbour.  All groups of a warp run in
-// lockstep: a loop whose trip count may differ between groups is driven by a
-// warp-wide vote and every warp-synchronous primitive names all 32 lanes, so
-// one instruction serves the 32/G neighbours of the warp at once.
-template <int G>
-struct Group {
-    int lane;        // lane inside the group
-    int gbase;       // first warp lane of the group
-    __device__ Group() {
-        const int wl = threadIdx.x & 31;
-        lane = wl & (G - 1);
-        gbase = wl & ~(G - 1);
-    }
-    // the group's G bits of a warp-wide ballot
-    __device__ unsigned bits(unsigned warp_ballot) const {
-        return G == 32 ? warp_ballot : (warp_ballot >> gbase) & ((1u << G) - 1u);
-    }
-    // maximum over the group; every lane of the warp calls it
-    __device__ int max(int x) const {
-#pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) x = ::max(x, __shfl_xor_sync(kFull, x, o));
-        return x;
-    }
-};
-
-// Shared-memory view of one instance.
-struct SInst {
-    const int *dur;
-    const uint32_t *reqw;
-    const uint32_t *capw;
-    const int *cap;
-    const int *cbase;
-    const int *reqk;
-    const int *poff;
-    const int *plist;
-    const int *soff;
-    const int *slist;
-    int n, m, ub, wps, sum_cap;
-    uint32_t hi;     // high bit of every packed field
-};
-
-__device__ SInst bind_instance(const int *sm, const InstHeader &h) {
-    InstLayout L = inst_layout(h.n, h.m, h.wps, h.n_arcs);
-    SInst I;
-    I.dur = sm + L.dur;
-    I.reqw = reinterpret_cast<const uint32_t *>(sm + L.reqw);
-    I.capw = reinterpret_cast<const uint32_t *>(sm + L.capw);
-    I.cap = sm + L.cap;
-    I.cbase = sm + L.cbase;
-    I.reqk = sm + L.reqk;
-    I.poff = sm + L.poff;
-    I.plist = sm + L.plist;
-    I.soff = sm + L.soff;
-    I.slist = sm + L.slist;
-    I.n = h.n;
-    I.m = h.m;
-    I.ub = h.ub;
-    I.wps = h.wps;
-    I.sum_cap = h.sum_cap;
-    I.hi = h.lane_bits == 8 ? 0x80808080u : 0x80008000u;
-    return I;
-}
-
-// Copies the instance image (a multiple of 16 bytes) into shared memory.
-__device__ void stage_instance(int *sm, const int32_t *record, int words) {
-    const int4 *src = reinterpret_cast<const int4 *>(record);
-    int4 *dst = reinterpret_cast<int4 *>(sm);
-    for (int x = threadIdx.x; x < words / 4; x += blockDim.x) dst[x] = __ldg(src + x);
-}
-
-// ---------------------------------------------------------------------------
-// Serial SGS (Alg. 7) of the list W with positions u and v swapped
-// (u == v leaves W unchanged), decoded by one group in lockstep with the
-// other groups of its warp.  A group with active == false follows the loops
-// without writing its scratch.  `area` is the group's interleaved scratch:
-// element e at area[e*NG]; the profile (or capacity state) comes first, then
-// es[i], the precedence earliest start of every activity.  Instead of
-// reading the finish times of i's predecessors when i is placed (Alg. 7,
-// lines 3-6), every placed activity raises es[] of its successors, so the
-// placement of i starts from one broadcast load; the value is the same
-// maximum.  Returns C_max; `work` gets the Alg. 5 (time-indexed) or Alg. 4
-// (capacity-indexed) loop steps; S_out (may be null) gets start times.
-// ---------------------------------------------------------------------------
-template <int G>
-__device__ __forceinline__ int activity_at(const int *W, int p, int u, int v) {
-    return p == u ? W[v] : (p == v ? W[u] : W[p]);
-}
-
-// es of every successor of i := max(es, f); inactive groups write nothing.
-template <int G>
-__device__ __forceinline__ void push_finish(const SInst &I, int i, int f, int *es, int NG, const Group<G> &g,
-                                            bool active) {
-    const int e0 = I.soff[i], ns = active ? I.soff[i + 1] - e0 : 0;
-    for (int b = g.lane; b < ns; b += G) {
-        int *x = es + I.slist[e0 + b] * NG;
-        *x = ::max(*x, f);
-    }
-}
-
-template <int G>
-__device__ __forceinline__ void clear_es(int *es, int n, int NG, bool active, const Group<G> &g) {
-    if (active)
-        for (int x = g.lane; x < n; x += G) es[x * NG] = 0;
-    __syncwarp();
-}
-
-// Time-indexed decode, WPS = 32-bit words per time step of the packed profile.
-template <int G, int WPS>
-__device__ int decode_time(const SInst &I, const int *W, int u, int v, bool active, int *area, int NG,
-                           const Group<G> &g, int &work, int &err, int *S_out) {
-    constexpr int U = G >= 32 ? 1 : (G >= 16 ? 2 : 4);   // steps a lane tests per round
-    constexpr int R = G * U;                               // steps a group tests per round (<= 32)
-    const int n = I.n, ub = I.ub;
-    const int ubs = ub > 0 ? ub : 1;              // stride of one resource-word plane
-    uint32_t *prof = reinterpret_cast<uint32_t *>(area);
-    int *esa = area + WPS * ubs * NG;
-    const uint32_t hi = I.hi;
-    uint32_t capw[WPS];
-#pragma unroll
-    for (int w = 0; w < WPS; ++w) capw[w] = I.capw[w];
-    clear_es<G>(esa, n, NG, active, g);
-    // Every step starts with R_k free units (Sec. 5.2.1).  Steps at or after
-    // the frontier F have not been touched by this decode, so they are not
-    // stored: they are written the first time an activity covers them.
-    int F = 0;
-    int cmax = 0;
-    int i = activity_at<G>(W, 0, u, v);
-    for (int p = 0; p < n; ++p) {
-        const int inext = activity_at<G>(W, p + 1 < n ? p + 1 : p, u, v);
-        const int es = esa[i * NG];
-        const int d = I.dur[i];
-        uint32_t rq[WPS];
-#pragma unroll
-        for (int w = 0; w < WPS; ++w) rq[w] = I.reqw[i * WPS + w];
-        // Alg. 5: the first window [s, s+d), s >= es, whose steps all fit,
-        // read off bit masks.  [s, s+k) is known to fit; a round tests the R
-        // steps s+k .. s+k+R-1 (step s+k+lane+G*j in lane `lane`; steps at or
-        // after F always fit) and either finds the first run of d fitting
-        // steps, or keeps the trailing run of fitting steps as the new
-        // verified prefix -- the same window as Alg. 5's loadTime count.
-        int s = es, k = 0;
-        bool done = !active || d == 0;
-        while (__any_sync(kFull, !done)) {
-            if (!done && s + k >= F) done = true;
-            const int tlim = done ? INT_MIN : F;
-            const int t0 = s + k + g.lane;
-            const uint32_t *a0 = prof + t0 * NG;
-            bool fit[U];
-#pragma unroll
-            for (int j = 0; j < U; ++j) {
-                fit[j] = true;
-                if (t0 + G * j < tlim) {
-#pragma unroll
-                    for (int w = 0; w < WPS; ++w) {
-                        const uint32_t x = a0[(w * ubs + G * j) * NG];
-                        fit[j] = fit[j] && (((x | hi) - rq[w]) & hi) == hi;
-                    }
-                }
-            }
-            unsigned x = 0;                                       // bit o: step s+k+o fits
-#pragma unroll
-            for (int j = 0; j < U; ++j) {
-                if (G == 1) x |= static_cast<unsigned>(fit[j]) << j;
-                else x |= g.bits(__ballot_sync(kFull, fit[j])) << (G * j);
-            }
-            if (!done) {
-                const unsigned full = R == 32 ? 0xffffffffu : ((1u << R) - 1u);
-                const int need = d - k;                           // >= 1
-                const unsigned lowneed = need >= 32 ? 0xffffffffu : ((1u << need) - 1u);
-                if (need <= R && (x & lowneed) == lowneed) {
-                    done = true;                                  // [s, s+d) fits
-                } else if (x == full) {
-                    k += R;                                       // all fit, the window needs more
-                } else {
-                    const int b = __ffs(~x) - 1;                  // first failing step of the round
-                    const int avail = R - b - 1;                  // steps after it in the round
-                    const unsigned xs = b + 1 >= 32 ? 0u : (x >> (b + 1));
-                    int w = -1;
-                    if (d <= avail) {
-                        unsigned y = xs;                          // y bit w: steps w..w+d-1 fit
-                        int len = 1;
-                        while (2 * len <= d) {
-                            y &= y >> len;
-                            len *= 2;
-                        }
-                        if (len < d) y &= y >> (d - len);
-                        if (y) w = __ffs(y) - 1;
-                    }
-                    if (w >= 0) {
-                        s += k + b + 1 + w;
-                        done = true;
-                    } else {
-                        const int h = 31 - __clz(~x & full);      // last failing step of the round
-                        s += k + h + 1;
-                        k = R - h - 1;
-                    }
-                }
-            }
-        }
-        const int f = s + d;
-        if (active) {
-            // Alg. 6: take r_{i,k} units over [s, s+d) (fields never borrow);
-            // untouched steps in [F, s) get R_k, those in [F, s+d) R_k - r.
-            if (d > 0) {
-                const int fe = ::min(f, ub);
-                if (f > ub) err |= kErrHorizon;
-#pragma unroll 2
-                for (int t = ::min(s, F) + g.lane; t < fe; t += G) {
-                    uint32_t *x = prof + t * NG;
-#pragma unroll
-                    for (int w = 0; w < WPS; ++w) {
-                        uint32_t *xw = x + w * ubs * NG;
-                        *xw = (t >= F ? capw[w] : *xw) - (t >= s ? rq[w] : 0u);
-                    }
-                }
-                F = ::max(F, fe);
-            }
-            if (S_out && g.lane == 0) S_out[i] = s;
-            work += f - es;
-            cmax = ::max(cmax, f);
-        }
-        push_finish<G>(I, i, f, esa, NG, g, active);
-        __syncwarp();
-        i = inext;
-    }
-    return cmax;
-}
-
-template <int G>
-__device__ int decode_capacity(const SInst &I, const int *W, int u, int v, bool active, int *area, int NG,
-                               const Group<G> &g, int &work, int &err, int *S_out) {
-    const int n = I.n, m = I.m;
-    int *cst = area;                                   // c_k, concatenated
-    int *esa = area + I.sum_cap * NG;
-    if (active)
-        for (int j = g.lane; j < I.sum_cap; j += G) cst[j * NG] = 0;   // Sec. 5.1.1
-    clear_es<G>(esa, n, NG, active, g);
-    int cmax = 0;
-    int i = activity_at<G>(W, 0, u, v);
-    for (int p = 0; p < n; ++p) {
-        const int inext = activity_at<G>(W, p + 1 < n ? p + 1 : p, u, v);
-        const int es = esa[i * NG];
-        // Eq. 7: es_res = max over used resources of c_k[R_k - r_{i,k}]
-        int er = 0;
-        if (active)
-            for (int k = g.lane; k < m; k += G) {
-                const int r = I.reqk[i * m + k];
-                if (r > 0) er = ::max(er, cst[(I.cbase[k] + I.cap[k] - r) * NG]);
-            }
-        er = g.max(er);
-        const int s = ::max(es, er);
-        const int d = I.dur[i];
-        for (int k = 0; k < m; ++k) {
-            const int r = I.reqk[i * m + k];
-            const bool upd = active && d > 0 && r > 0;
-            int last = -1;
-            if (__any_sync(kFull, upd)) {
-                // Alg. 4 as a per-index closed form of its result:
-                //   j <  r : c'[j] = max(c[j], s+d)
-                //   j >= r : c'[j] = c[j-r] <= s ? c[j] : max(c[j], min(c[j-r], s+d))
-                // c_k is non-increasing, so with a = #{j : c[j] > s} nothing at
-                // j >= r + a changes (there c[j-r] <= s).  a is found chunk by
-                // chunk; the update then runs from the top chunk down so that
-                // c[j-r] is still old when it is read.
-                const int R = I.cap[k];
-                int *ck = cst + I.cbase[k] * NG;
-                int a = 0;
-                bool more = upd;
-                for (int J = 0; __any_sync(kFull, more); J += G) {
-                    const int j = J + g.lane;
-                    const bool above = more && j < R && ck[j * NG] > s;
-                    const unsigned m = g.bits(__ballot_sync(kFull, above));
-                    if (more) {
-                        a += __popc(m);
-                        more = m == (G == 32 ? 0xffffffffu : ((1u << G) - 1u)) && J + G < R;
-                    }
-                }
-                const int top = ::min(R, r + a);            // indices that can change: [0, top)
-                const int topmax = __reduce_max_sync(kFull, upd ? top : 0);
-                for (int J = ((topmax - 1) / G) * G; J >= 0; J -= G) {
-                    const int j = J + g.lane;
-                    int old = 0, prev = 0;
-                    if (upd && j < top) {
-                        old = ck[j * NG];
-                        if (j >= r) prev = ck[(j - r) * NG];
-                    }
-                    __syncwarp();
-                    if (upd && j < top) {
-                        const int nv = j < r ? ::max(old, s + d)
-                                             : (prev <= s ? old : ::max(old, ::min(prev, s + d)));
-                        if (nv != old) {
-                            ck[j * NG] = nv;
-                            last = ::max(last, j);
-                        }
-                    }
-                    __syncwarp();
-                }
-            }
-            last = g.max(last);
-            if (upd) work += last + 1;                 // Alg. 4 stops after its last change
-        }
-        if (active) {
-            if (S_out && g.lane == 0) S_out[i] = s;
-            cmax = ::max(cmax, s + d);
-        }
-        push_finish<G>(I, i, s + d, esa, NG, g, active);
-        __syncwarp();
-        i = inext;
-    }
-    (void)err;
-    return cmax;
-}
-
-template <int G>
-__device__ __forceinline__ int decode(const SInst &I, int mode, const int *W, int u, int v, bool active,
-                                      int *area, int NG, const Group<G> &g, long long &work, int &err,
-                                      int *S_out = nullptr) {
-    int wk = 0, c;
-    if (mode == RCPSP_EVAL_CAPACITY) c = decode_capacity<G>(I, W, u, v, active, area, NG, g, wk, err, S_out);
-    else if (I.wps == 1) c = decode_time<G, 1>(I, W, u, v, active, area, NG, g, wk, err, S_out);
-    else if (I.wps == 2) c = decode_time<G, 2>(I, W, u, v, active, area, NG, g, wk, err, S_out);
-    else c = decode_time<G, 4>(I, W, u, v, active, area, NG, g, wk, err, S_out);
-    work += wk;
-    return c;
-}
-
-__device__ __forceinline__ unsigned long long global_timer_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long x) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        unsigned long long y = __shfl_xor_sync(kFull, x, o);
-        x = y < x ? y : x;
-    }
-    return x;
-}
-
-__device__ __forceinline__ long long warp_sum_i64(long long x) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
-    return x;
-}
-
-__device__ __forceinline__ bool tc_get(const unsigned *tc, int u, int v, int delta) {
-    const int b = u * delta + (v - u - 1);
-    return (tc[b >> 5] >> (b & 31)) & 1u;
-}
-
-__device__ __forceinline__ void tc_put(unsigned *tc, int u, int v, int delta, bool on) {
-    const int b = u * delta + (v - u - 1);
-    if (on) tc[b >> 5] |= 1u << (b & 31);
-    else tc[b >> 5] &= ~(1u << (b & 31));
-}
 
 // ---------------------------------------------------------------------------
 // Persistent search kernel.  With csize > 1 it runs as clusters of csize
@@ -482,72 +114,15 @@ __global__ void __launch_bounds__(512, 2) search_kernel(const LaunchItem *__rest
         }
         __syncthreads();
         const int nslots = n > 3 ? (n - 3) * delta : 0;
-        // slot / delta by a multiply-high: exact while slot * delta < 2^32,
-        // which holds because the host clamps delta to N - 3 (same moves)
-        const unsigned dmagic = delta > 1 ? 0xffffffffu / static_cast<unsigned>(delta) + 1u : 0u;
+        const unsigned dmagic = slot_magic(delta);
         long long my_work = 0;
         for (;;) {
             if (s_it >= it.iterations || (it.stop_at_cp && s_Cbest == h.cp)) break;
-            // 1. first successor / last predecessor position of every position
-            for (int p = tid; p < n; p += nthr) {
-                const int a = W[p];
-                int f = n, l = -1;
-                for (int e = I.soff[a]; e < I.soff[a + 1]; ++e) f = ::min(f, pos[I.slist[e]]);
-                for (int e = I.poff[a]; e < I.poff[a + 1]; ++e) l = ::max(l, pos[I.plist[e]]);
-                fsp[p] = f;
-                lpp[p] = l;
-            }
             const int par = s_it & 1;
             if (tid == 0) s_bestp[par] = ~0ull;
-            __syncthreads();
-            const int cbest = s_Cbest;
-            unsigned long long my_key = ~0ull;
-            for (int base = 0; base < nslots; base += move_cap) {
-                const int stripe = ::min(move_cap, nslots - base);
-                if (tid == 0) s_nmoves = 0;
-                __syncthreads();
-                // 2. feasible moves of the stripe, compacted
-                for (int k0 = 0; k0 < stripe; k0 += nthr) {
-                    const int k = k0 + tid;
-                    bool ok = false;
-                    int code = 0;
-                    if (k < stripe) {
-                        const int slot = base + k;
-                        const int q = delta > 1 ? static_cast<int>(__umulhi(static_cast<unsigned>(slot), dmagic)) : slot;
-                        const int u = 1 + q;
-                        const int v = u + 1 + (slot - q * delta);
-                        const bool mine = csize == 1 || static_cast<unsigned>((slot >> 5) % csize) == crank;
-                        if (mine && v <= n - 2 && fsp[u] > v && lpp[v] < u) {
-                            ok = true;
-                            code = u | (v << 16);
-                        }
-                    }
-                    const unsigned b = __ballot_sync(kFull, ok);
-                    int wb = 0;
-                    if (wl == 0 && b) wb = atomicAdd(&s_nmoves, __popc(b));
-                    wb = __shfl_sync(kFull, wb, 0);
-                    if (ok) moves[wb + __popc(b & ((1u << wl) - 1u))] = code;
-                }
-                __syncthreads();
-                const int nm = s_nmoves;
-                // 3. decode the neighbours
-                // (the groups of a warp take consecutive moves and decode them in lockstep)
-                for (int q0 = warp * NG; q0 < nm; q0 += ngroups) {
-                    const int q = q0 + gw;
-                    const bool act = q < nm;
-                    const int code = act ? moves[q] : 0;
-                    const int u = code & 0xffff, v = code >> 16;
-                    const int c = decode<G>(I, mode, W, u, v, act, area, NG, g, my_work, err);
-                    if (act && (!tc_get(tc, u, v, delta) || c < cbest)) {
-                        const unsigned long long key =
-                            (static_cast<unsigned long long>(c) << 32) | static_cast<unsigned>(code & 0xffff) << 16 |
-                            static_cast<unsigned>(v);
-                        my_key = key < my_key ? key : my_key;
-                    }
-                }
-                if (tid == 0) s_eval += nm;
-                __syncthreads();
-            }
+            const unsigned long long my_key =
+                best_admissible_key<G>(I, mode, W, pos, fsp, lpp, tc, moves, area, n, delta, nslots, dmagic,
+                                       move_cap, s_Cbest, csize, crank, &s_nmoves, &s_eval, my_work, err);
             // 4. best admissible move of the block, then of the cluster
             const unsigned long long wk = warp_min_u64(my_key);
             if (wl == 0 && wk != ~0ull) atomicMin(&s_bestp[par], wk);

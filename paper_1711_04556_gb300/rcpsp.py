@@ -20,7 +20,7 @@ EVAL_AUTO, EVAL_TIME, EVAL_CAPACITY = 0, 1, 2
 ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "CYCLE", -3: "DUMMY", -4: "DEMAND_EXCEEDS_CAP",
           -5: "TOO_LARGE", -6: "CUDA", -7: "TIMEOUT", -8: "NOT_FOUND", -9: "DEVICE"}
 EXPORTS = ("rcpsp_create", "rcpsp_destroy", "rcpsp_load_instances", "rcpsp_free_instances",
-           "rcpsp_tabu_search", "rcpsp_tabu_search_noalloc", "rcpsp_autotune", "rcpsp_get_schedules", "rcpsp_get_trace", "rcpsp_evaluate_lists",
+           "rcpsp_tabu_search", "rcpsp_tabu_search_noalloc", "rcpsp_coop_search", "rcpsp_autotune", "rcpsp_get_schedules", "rcpsp_get_trace", "rcpsp_evaluate_lists",
            "rcpsp_prepare_instance", "rcpsp_transfer_bytes", "rcpsp_kernel_launches", "rcpsp_server_create", "rcpsp_server_destroy",
            "rcpsp_server_submit", "rcpsp_server_poll", "rcpsp_server_get_stats", "rcpsp_last_error")
 
@@ -43,6 +43,11 @@ class Params(C.Structure):
                 ("eval_mode", C.c_int32), ("stop_at_cp", C.c_int32), ("group_size", C.c_int32),
                 ("warps_per_cta", C.c_int32), ("record_trace", C.c_int32), ("use_graph", C.c_int32),
                 ("cluster_size", C.c_int32)]
+
+
+class CoopParams(C.Structure):
+    _fields_ = [("blocks", C.c_int32), ("working_set", C.c_int32), ("phi_max", C.c_int32),
+                ("phi_steps", C.c_int32), ("assign_fixed", C.c_int32), ("words_per_block", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -98,6 +103,8 @@ def library(path: Optional[str] = None):
         "rcpsp_free_instances": (C.c_int, [C.c_void_p, P(C.c_int32), C.c_int32]),
         "rcpsp_tabu_search": (C.c_int, [C.c_void_p, P(C.c_int32), C.c_int32, P(Params), C.c_void_p]),
         "rcpsp_tabu_search_noalloc": (C.c_int, [C.c_void_p, P(C.c_int32), C.c_int32, P(Params), C.c_void_p]),
+        "rcpsp_coop_search": (C.c_int, [C.c_void_p, P(C.c_int32), C.c_int32, P(Params), P(CoopParams),
+                                        P(C.c_int32), P(C.c_uint32), C.c_void_p]),
         "rcpsp_autotune": (C.c_int, [C.c_void_p, P(C.c_int32), C.c_int32, P(Params), C.c_int32, C.c_void_p,
                                      P(C.c_int32), P(C.c_int32), P(C.c_int32)]),
         "rcpsp_get_schedules": (C.c_int, [C.c_void_p, P(C.c_int32), C.c_int32, P(C.c_int32), P(C.c_int32),
@@ -270,6 +277,36 @@ class Solver:
                    int(trace), int(use_graph), cluster_size)
         handle = getattr(stream, "cuda_stream", stream) or None
         self._check(self.lib.rcpsp_tabu_search(self.ctx, _ptr(ids), len(ids), C.byref(p), handle))
+
+    def coop_search(self, ids, iterations: int = 100, delta: int = 0, tabu_len: int = 0, mode: int = EVAL_AUTO,
+                    stop_at_cp: bool = True, blocks: int = 4, working_set: int = 16, phi_max: int = 3,
+                    phi_steps: int = 20, assign_fixed: int = 0, slot_keys=None, words=None,
+                    group_size: int = 0, warps_per_cta: int = 0, stream=None):
+        """rcpsp_coop_search: `blocks` co-operating searches per instance.
+
+        slot_keys: None, or per instance a list of `working_set` entries
+        (None = unshuffled, else N keys).  words: None, or per instance a
+        uint32 array [blocks, P] (required when phi_steps > 0)."""
+        ids = _i32(ids)
+        keys = None
+        if slot_keys is not None:
+            rows = []
+            for i, per in zip(ids, slot_keys):
+                n = self.n_of[int(i)]
+                for f in range(working_set):
+                    k = per[f] if per is not None else None
+                    rows.append(np.zeros(n, np.int32) if k is None else np.asarray(k, np.int32))
+            keys = np.ascontiguousarray(np.concatenate(rows), np.int32)
+        wp, P = None, 0
+        if words is not None:
+            w = np.ascontiguousarray(np.stack([np.asarray(x, np.uint32).reshape(blocks, -1) for x in words]))
+            P = w.shape[2]
+            wp = w.ctypes.data_as(C.POINTER(C.c_uint32))
+        p = Params(iterations, delta, tabu_len, mode, int(stop_at_cp), group_size, warps_per_cta, 0, 0, 0)
+        cp = CoopParams(blocks, working_set, phi_max, phi_steps, assign_fixed, P)
+        handle = getattr(stream, "cuda_stream", stream) or None
+        self._check(self.lib.rcpsp_coop_search(self.ctx, _ptr(ids), len(ids), C.byref(p), C.byref(cp),
+                                               _ptr(keys) if keys is not None else None, wp, handle))
 
     def search_noalloc(self, ids, iterations: int = 100, delta: int = 0, tabu_len: int = 0,
                        mode: int = EVAL_AUTO, stop_at_cp: bool = True, group_size: int = 0,

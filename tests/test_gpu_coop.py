@@ -1,0 +1,139 @@
+"""GPU parity of the co-operating searches (Sec. 6.1, Eq. 8), bit-exact.
+
+Each instance runs B tabu searches in one thread-block cluster exchanging
+through a working set; the CPU reference replays the same lockstep
+co-operation.  Compared per instance: the best list, its schedule and
+makespan, the evaluator, and -- summed over the blocks -- iterations,
+evaluated neighbours and decode work, which agree only if every block's
+trajectory, every exchange, every Eq. 8 budget and every diversification
+agree.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_1711_04556_gb300 import instances as I
+from paper_1711_04556_gb300 import rcpsp as R
+from test_oracle_pins import medium_instances
+
+pytestmark = pytest.mark.gpu
+
+NPROC = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module")
+def solver():
+    from paper_1711_04556_gb300 import build as B
+    B.build()
+    s = R.Solver(0)
+    yield s
+    s.close()
+
+
+def run_both(solver, oracle, insts, iterations, delta, tabu_len, mode=R.EVAL_AUTO, stop_at_cp=True, blocks=4,
+             working_set=16, phi_max=3, phi_steps=20, assign_fixed=0, seed=1, words_per_block=64, **shape):
+    keys, words = [], []
+    for k, x in enumerate(insts):
+        kk, ww = I.coop_inputs(x, seed + k, working_set, blocks, words_per_block)
+        keys.append(kk)
+        words.append(ww)
+    ids = solver.load(insts)
+    solver.coop_search(ids, iterations=iterations, delta=delta, tabu_len=tabu_len, mode=mode,
+                       stop_at_cp=stop_at_cp, blocks=blocks, working_set=working_set, phi_max=phi_max,
+                       phi_steps=phi_steps, assign_fixed=assign_fixed, slot_keys=keys,
+                       words=words if phi_steps > 0 else None, **shape)
+    got = solver.results(ids)
+    solver.free(ids)
+    kw = []
+    for k, x in enumerate(insts):
+        d, t = (delta, tabu_len) if delta else I.search_params(x.n - 2)
+        kw.append(dict(iterations=iterations, delta=min(d, max(1, x.n - 3)), tabu_len=t, mode=mode,
+                       stop_at_cp=int(stop_at_cp), blocks=blocks, working_set=working_set, phi_max=phi_max,
+                       phi_steps=phi_steps, assign_fixed=assign_fixed, slot_keys=keys[k],
+                       words=words[k] if phi_steps > 0 else None))
+    ref = oracle.coop_search_batch(insts, kw, NPROC)
+    for g, r in zip(got, ref):
+        assert r["status"] == 0
+        assert g["status"] == 0
+        for key in ("best_cmax", "iterations", "evaluated", "work", "cp", "mode"):
+            assert g[key] == r[key], key
+        assert g["best_W"].tolist() == r["best_W"].tolist()
+        assert g["best_S"].tolist() == r["best_S"].tolist()
+    return got, ref
+
+
+def test_paper_parameters_on_j30(solver, oracle):
+    """|F| = 16, Phi_max = 3, Phi_steps = 20 (Table 2), 4 blocks."""
+    insts = I.config_batch("j30_batch", 24, first=100)
+    got, _ = run_both(solver, oracle, insts, 120, 20, 60)
+    assert any(g["best_cmax"] > g["cp"] for g in got)          # searches that ran to the limit
+
+
+@pytest.mark.parametrize("blocks,fsize,phi_max", [(1, 1, 3), (2, 3, 0), (8, 4, 1), (3, 16, 3)])
+def test_cluster_shapes(solver, oracle, blocks, fsize, phi_max):
+    insts = medium_instances(10, first=5) + I.config_batch("j30_batch", 6, first=300)
+    run_both(solver, oracle, insts, 50, 8, 15, blocks=blocks, working_set=fsize, phi_max=phi_max,
+             phi_steps=5, stop_at_cp=False)
+
+
+def test_single_block_equals_plain_search(solver, oracle):
+    """B = |F| = 1 without timeouts or diversification is the single search."""
+    insts = I.config_batch("j30_batch", 12, first=40)
+    got, _ = run_both(solver, oracle, insts, 80, 20, 60, blocks=1, working_set=1, phi_max=10**6, phi_steps=0,
+                      assign_fixed=81)
+    ids = solver.load(insts)
+    solver.search(ids, iterations=80, delta=20, tabu_len=60)
+    plain = solver.results(ids)
+    solver.free(ids)
+    for g, p in zip(got, plain):
+        for key in ("best_cmax", "iterations", "evaluated", "work"):
+            assert g[key] == p[key], key
+        assert g["best_W"].tolist() == p["best_W"].tolist()
+
+
+@pytest.mark.parametrize("mode", [R.EVAL_TIME, R.EVAL_CAPACITY])
+def test_j120_both_evaluators(solver, oracle, mode):
+    insts = I.config_batch("j120_batch", 3, first=70)
+    run_both(solver, oracle, insts, 12, 60, 800, mode=mode, blocks=2, working_set=4, phi_max=0, phi_steps=20)
+
+
+def test_mixed_sizes_default_parameters(solver, oracle):
+    insts = [x for x in I.config_batch("mixed_batch", 30) if x.n <= 122][:8]
+    run_both(solver, oracle, insts, 8, 0, 0, blocks=4, working_set=8, phi_max=1)
+
+
+def test_sixteen_blocks(solver, oracle):
+    """The largest cluster (non-portable size 16), if the GPU schedules it."""
+    insts = I.config_batch("j30_batch", 4, first=7)
+    try:
+        run_both(solver, oracle, insts, 30, 20, 60, blocks=16, working_set=16, phi_max=1, phi_steps=20,
+                 group_size=4, warps_per_cta=4)
+    except R.RcpspError as e:
+        if e.code != -5:
+            raise
+        pytest.skip("a 16-CTA cluster does not fit at this shape")
+
+
+def test_shapes_do_not_change_results(solver, oracle):
+    insts = I.config_batch("j30_batch", 8, first=11)
+    base = None
+    for g, w in ((1, 2), (4, 4), (8, 8), (32, 2)):
+        got, _ = run_both(solver, oracle, insts, 40, 20, 60, blocks=2, working_set=6, phi_max=1,
+                          group_size=g, warps_per_cta=w)
+        cm = [x["best_cmax"] for x in got]
+        base = base or cm
+        assert cm == base
+
+
+def test_invalid_parameters(solver):
+    x = I.config_batch("j30_single")
+    ids = solver.load(x)
+    for bad in (dict(blocks=0), dict(blocks=17), dict(working_set=0), dict(working_set=65),
+                dict(phi_max=-1), dict(phi_steps=5, words=None)):
+        kw = dict(iterations=5, blocks=2, working_set=2, phi_steps=0)
+        kw.update(bad)
+        with pytest.raises(R.RcpspError) as e:
+            solver.coop_search(ids, **kw)
+        assert e.value.code == -1
+    solver.free(ids)
