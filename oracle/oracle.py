@@ -55,7 +55,8 @@ class _Params(C.Structure):
 
 class _CoopParams(C.Structure):
     _fields_ = [("blocks", C.c_int), ("working_set", C.c_int), ("phi_max", C.c_int),
-                ("phi_steps", C.c_int), ("assign_fixed", C.c_int), ("words_per_block", C.c_int)]
+                ("phi_steps", C.c_int), ("assign_fixed", C.c_int), ("words_per_block", C.c_int),
+                ("fbi_every", C.c_int)]
 
 
 class _CoopEvent(C.Structure):
@@ -87,6 +88,8 @@ def load(path: str):
         "orc_select_mode": (C.c_int, [P(_Inst)]),
         "orc_tabu_search": (C.c_int, [P(_Inst), P(_Params), P(_Result)]),
         "orc_tabu_search_batch": (C.c_int, [P(_Inst), C.c_int, P(_Params), P(_Result), C.c_int]),
+        "orc_fbi": (C.c_int, [P(_Inst), C.c_int, P(C.c_int), P(C.c_int)]),
+        "orc_fbi_pass": (C.c_int, [P(_Inst), C.c_int, P(C.c_int), P(C.c_int), P(C.c_int), P(C.c_int)]),
         "orc_exp_neg": (C.c_double, [C.c_double]),
         "orc_assigned_iterations": (C.c_int, [C.c_int, C.c_int, C.c_longlong, C.c_int]),
         "orc_diversify": (C.c_int, [P(_Inst), P(C.c_int), C.c_int, C.c_int, P(C.c_uint), C.c_int,
@@ -240,6 +243,24 @@ def brute_force_starts(inst) -> int:
 COOP_EVENT_FIELDS = [f for f, _ in _CoopEvent._fields_]
 
 
+def fbi(inst, W, mode: int) -> tuple:
+    """Forward-backward improvement of W; returns (list, C_max, passes)."""
+    W = np.array(W, np.int32)
+    passes = C.c_int(0)
+    c = _lib().orc_fbi(C.byref(_Marshalled(inst).s), mode, _ip(W), C.byref(passes))
+    return W, c, passes.value
+
+
+def fbi_pass(inst, W, mode: int) -> tuple:
+    """One FBI pass: (forward list, its C_max, backward makespan T, mirrored backward starts)."""
+    W = np.ascontiguousarray(W, np.int32)
+    Wn = np.zeros(inst.n, np.int32)
+    Sb = np.zeros(inst.n, np.int32)
+    T = C.c_int(0)
+    c = _lib().orc_fbi_pass(C.byref(_Marshalled(inst).s), mode, _ip(W), _ip(Wn), C.byref(T), _ip(Sb))
+    return Wn, c, T.value, Sb
+
+
 def exp_neg(x: float) -> float:
     return _lib().orc_exp_neg(float(x))
 
@@ -260,7 +281,7 @@ def diversify(inst, W, delta: int, steps: int, words, cursor: int = 0) -> tuple:
 
 def coop_search(inst, iterations=100, delta=20, tabu_len=60, mode=AUTO, stop_at_cp=1, blocks=4,
                 working_set=16, phi_max=3, phi_steps=20, assign_fixed=0, slot_keys=None, words=None,
-                log_cap=0) -> dict:
+                log_cap=0, fbi_every=2) -> dict:
     """B co-operating searches of one instance through a working set of
     `working_set` slots.  slot_keys: None or a list of |F| entries (None or
     N keys).  words: uint32 [blocks, P] random words (None if phi_steps == 0).
@@ -283,7 +304,7 @@ def coop_search(inst, iterations=100, delta=20, tabu_len=60, mode=AUTO, stop_at_
         keep.append(w)
         P = w.shape[1]
         wptr = w.ctypes.data_as(C.POINTER(C.c_uint))
-    cp = _CoopParams(blocks, working_set, phi_max, phi_steps, assign_fixed, P)
+    cp = _CoopParams(blocks, working_set, phi_max, phi_steps, assign_fixed, P, fbi_every)
     r, W, S, _ = _result_buffers(inst.n, iterations, False)
     ev = (_CoopEvent * max(1, log_cap))()
     n_ev = C.c_int(0)

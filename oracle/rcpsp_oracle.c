@@ -14,6 +14,8 @@
  *   - capacity-indexed ... Alg. 7 with Eq. 7 and Alg. 4 (Sec. 5.1)
  *   - tabu list .......... Algs. 2-3 (Sec. 4.5)
  *   - search loop ........ Sec. 6 (one block's main loop, no working set)
+ *   - FBI ................ Sec. 6 (forward-backward improvement of initial
+ *                          solutions; readings F1-F3 beside the code)
  *   - co-operation ....... Sec. 6.1, Eq. 8 (blocks exchanging through the
  *                          working set F; readings C1-C8 beside the code)
  *
@@ -448,6 +450,102 @@ int orc_tabu_search_batch(const orc_instance *in, int count, const orc_params *p
     return rc;
 }
 
+/* ------------- forward-backward improvement (FBI, Sec. 6) ---------------- */
+/*
+ * The paper improves every second initial solution by the forward-backward
+ * improvement of Li and Willis, "shaking" the schedule right and left while
+ * it gets shorter.  Restated here as the usual justification passes of the
+ * serial SGS, with the readings:
+ *   F1  Backward pass: the activities ordered by non-increasing finish time
+ *       of the forward schedule (ties: later list position first) are
+ *       decoded on the reversed network (successors act as predecessors),
+ *       with the search's evaluator; tau_i is the reversed start and T the
+ *       reversed makespan.  Mirrored, s'_i = T - tau_i - d_i is a schedule
+ *       of the original instance of length T.
+ *   F2  Forward pass: the activities ordered by non-decreasing s'_i (ties:
+ *       earlier position in the current list first) form the new list,
+ *       decoded forward.
+ *   F3  The passes repeat while the forward makespan gets strictly shorter;
+ *       the result is the last list that shortened it (or the input list).
+ */
+static int fbi_decode(const orc_instance *in, const preds_t *P, int mode, const int *W, int *S) {
+    return mode == ORC_TIME ? decode_time(in, P, W, S, NULL) : decode_capacity(in, P, W, S, NULL);
+}
+
+int orc_fbi_pass(const orc_instance *in, int mode, const int *W, int *Wnext, int *T_out, int *S_back) {
+    const int N = in->n;
+    if (mode == ORC_AUTO) mode = orc_select_mode(in);
+    preds_t P, Q;                                  /* Q: predecessors of the reversed network */
+    if (build_preds(in, &P) != 0) return -1;
+    Q.off = (int *)malloc(sizeof(int) * (size_t)(N + 1));
+    Q.list = (int *)malloc(sizeof(int) * (size_t)(in->succ_off[N] > 0 ? in->succ_off[N] : 1));
+    int *S = (int *)malloc(sizeof(int) * (size_t)N);
+    int *tau = (int *)malloc(sizeof(int) * (size_t)N);
+    int *pos = (int *)malloc(sizeof(int) * (size_t)N);
+    int *Wb = (int *)malloc(sizeof(int) * (size_t)N);
+    int C2 = -1;
+    if (!Q.off || !Q.list || !S || !tau || !pos || !Wb) goto out;
+    for (int i = 0; i <= N; ++i) Q.off[i] = in->succ_off[i];
+    for (int e = 0; e < in->succ_off[N]; ++e) Q.list[e] = in->succ[e];
+    if (fbi_decode(in, &P, mode, W, S) < 0) goto out;
+    for (int p = 0; p < N; ++p) pos[W[p]] = p;
+    /* F1: by finish time, largest first; ties: later position first (insertion sort) */
+    for (int p = 0; p < N; ++p) {
+        int a = W[p], q = p;
+        while (q > 0) {
+            int b = Wb[q - 1];
+            int fa = S[a] + in->dur[a], fb = S[b] + in->dur[b];
+            if (fb > fa || (fb == fa && pos[b] > pos[a])) break;
+            Wb[q] = b;
+            --q;
+        }
+        Wb[q] = a;
+    }
+    int T = fbi_decode(in, &Q, mode, Wb, tau);
+    if (T_out) *T_out = T;
+    if (S_back)
+        for (int i = 0; i < N; ++i) S_back[i] = T - tau[i] - in->dur[i];
+    /* F2: by mirrored start T - tau - d, smallest first; ties: earlier position first */
+    for (int p = 0; p < N; ++p) {
+        int a = W[p], q = p;
+        int sa = T - tau[a] - in->dur[a];
+        while (q > 0) {
+            int b = Wnext[q - 1];
+            int sb = T - tau[b] - in->dur[b];
+            if (sb < sa || (sb == sa && pos[b] < pos[a])) break;
+            Wnext[q] = b;
+            --q;
+        }
+        Wnext[q] = a;
+    }
+    C2 = fbi_decode(in, &P, mode, Wnext, S);
+out:
+    free(Q.off); free(Q.list); free(S); free(tau); free(pos); free(Wb);
+    free_preds(&P);
+    return C2;
+}
+
+int orc_fbi(const orc_instance *in, int mode, int *W, int *passes) {
+    const int N = in->n;
+    if (mode == ORC_AUTO) mode = orc_select_mode(in);
+    int *Wf = (int *)malloc(sizeof(int) * (size_t)N);
+    int *S = (int *)malloc(sizeof(int) * (size_t)N);
+    int np = 0, C = -1;
+    if (!Wf || !S) goto out;
+    C = mode == ORC_TIME ? orc_decode_time(in, W, S, NULL) : orc_decode_capacity(in, W, S, NULL);
+    for (;;) {
+        int C2 = orc_fbi_pass(in, mode, W, Wf, NULL, NULL);
+        if (!(C2 >= 0 && C2 < C)) break;           /* F3 */
+        memcpy(W, Wf, sizeof(int) * (size_t)N);
+        C = C2;
+        ++np;
+    }
+out:
+    if (passes) *passes = np;
+    free(Wf); free(S);
+    return C;
+}
+
 /* -------------- Sec. 6.1: co-operation through a working set ------------ */
 /*
  * The paper's blocks run asynchronously and lock the working set, so the
@@ -480,7 +578,8 @@ int orc_tabu_search_batch(const orc_instance *in, int count, const orc_params *p
  *       (sum_{i=0..24} (-x/1024)^i / i!)^(2^10), Horner form, IEEE double
  *       without contraction, 0 for x > 700.  assign_fixed > 0 replaces it.
  *   C7  Slot k starts from the level order with slot k's shuffle keys
- *       (Sec. 4.1); the forward-backward improvement is not applied.
+ *       (Sec. 4.1); with fbi_every = e > 0 the slots k = e-1, 2e-1, ... are
+ *       improved by FBI first (the paper: every second solution, e = 2).
  *   C8  The search ends when the blocks have run I_block iterations each or,
  *       with stop_at_cp, when C* equals the critical path at the start of
  *       an iteration.  The result is the best slot (lowest index), unless a
@@ -623,6 +722,8 @@ int orc_coop_search(const orc_instance *in, const orc_params *p, const orc_coop_
         orc_instance ik = *in;
         if (slot_keys) ik.level_key = slot_keys[k];
         if (orc_initial_order(&ik, slot[k].W) != 0) { res->status = -1; goto done; }
+        if (cp->fbi_every > 0 && k % cp->fbi_every == cp->fbi_every - 1)
+            orc_fbi(in, mode, slot[k].W, NULL);                       /* C7 */
         slot[k].C = DECODE(slot[k].W, NULL);
         slot[k].phi = 0;
         slot[k].IC = 0;

@@ -93,6 +93,7 @@ typedef struct {
     int phi_steps;         /* Phi_steps: random feasible swaps of a diversification */
     int assign_fixed;      /* iterations per read; 0 = Eq. 8 */
     int words_per_block;   /* P: random words of each block, used cyclically */
+    int fbi_every;         /* FBI on slots k with k % e == e-1; 0 = none (paper: 2) */
 } orc_coop_params;
 
 /* One exchange event of orc_coop_search (optional log). */
@@ -108,6 +109,15 @@ typedef struct {
     long long ic;          /* slot's iterations counter after the event */
 } orc_coop_event;
 
+/* Forward-backward improvement (Sec. 6, readings F1-F3) of the list W in
+ * place with evaluator `mode`; returns the final C_max, *passes (nullable)
+ * the passes that shortened it. */
+int orc_fbi(const orc_instance *in, int mode, int *W, int *passes);
+/* One FBI pass (F1-F2): the backward list of W's forward schedule decoded on
+ * the reversed network (*T_out = its makespan T, S_back = the mirrored
+ * starts T - tau_i - d_i, both nullable) and the forward list Wnext; returns
+ * Wnext's forward makespan. */
+int orc_fbi_pass(const orc_instance *in, int mode, const int *W, int *Wnext, int *T_out, int *S_back);
 /* e^{-x} for x >= 0 in IEEE double, by the fixed recipe of reading C6. */
 double orc_exp_neg(double x);
 /* Eq. 8 (reading C6): iterations assigned to a read of slot k. */

@@ -129,10 +129,10 @@ def test_identical_blocks_run_identical_searches(oracle):
     for inst in medium_instances(4, first=40):
         _, words = I.coop_inputs(inst, 9, 1, 1, 32)
         one = coop(oracle, inst, iterations=80, blocks=1, working_set=1, phi_max=1, phi_steps=4,
-                   slot_keys=None, words=words, stop_at_cp=0)
+                   slot_keys=None, words=words, stop_at_cp=0, fbi_every=0)
         for b in (2, 3):
             many = coop(oracle, inst, iterations=80, blocks=b, working_set=b, phi_max=1, phi_steps=4,
-                        slot_keys=None, words=np.repeat(words, b, axis=0), stop_at_cp=0)
+                        slot_keys=None, words=np.repeat(words, b, axis=0), stop_at_cp=0, fbi_every=0)
             assert many["best_cmax"] == one["best_cmax"]
             assert many["best_W"].tolist() == one["best_W"].tolist()
             assert many["evaluated"] == b * one["evaluated"] and many["work"] == b * one["work"]
@@ -191,3 +191,52 @@ def test_cooperation_is_no_worse_than_its_first_slot(oracle):
         assert r["status"] == 0 and r["cp"] <= r["best_cmax"] <= c0
         rc, cm = oracle.check_schedule(inst, r["best_S"])
         assert rc == 0 and cm == r["best_cmax"]
+
+
+# ------------------------------------------------------------------- FBI
+def test_fbi_backward_schedule_is_a_schedule(oracle):
+    """The backward pass, mirrored, is a feasible schedule of the original
+    instance (independent checker) no longer than the forward one (TIME:
+    the serial SGS right-justifies); the forward pass is no longer than it."""
+    rng = np.random.default_rng(17)
+    from test_oracle_pins import random_feasible_list
+    insts = medium_instances(8, first=80) + I.config_batch("j30_batch", 6, first=30)
+    for inst in insts:
+        for _ in range(4):
+            W = random_feasible_list(inst, rng)
+            for mode in (1, 2):
+                c = oracle.decode(inst, W, mode)[0]
+                Wn, c2, T, Sb = oracle.fbi_pass(inst, W, mode)
+                rc, cm = oracle.check_schedule(inst, Sb)
+                assert rc == 0 and cm == T
+                assert list_is_feasible(inst, Wn)
+                assert sorted(Wn.tolist()) == list(range(inst.n))
+                assert [Sb[a] for a in Wn] == sorted(Sb.tolist())      # forward list by backward start
+                if mode == 1:
+                    assert T <= c and c2 <= T
+
+
+def test_fbi_never_worse_and_converged(oracle):
+    rng = np.random.default_rng(5)
+    from test_oracle_pins import random_feasible_list
+    improved = 0
+    for inst in medium_instances(6, first=90) + I.config_batch("j30_batch", 8, first=60):
+        for mode in (1, 2):
+            W = random_feasible_list(inst, rng)
+            c0 = oracle.decode(inst, W, mode)[0]
+            Wf, c, passes = oracle.fbi(inst, W, mode)
+            assert c <= c0 and (passes > 0) == (c < c0)
+            assert oracle.decode(inst, Wf, mode)[0] == c and list_is_feasible(inst, Wf)
+            again, c1, p1 = oracle.fbi(inst, Wf, mode)                  # a fixed point
+            assert p1 == 0 and c1 == c and again.tolist() == Wf.tolist()
+            improved += c < c0
+    assert improved > 0
+
+
+def test_fbi_not_below_the_optimum(oracle):
+    from test_oracle_pins import small_instances
+    for inst in small_instances(12, n=6):
+        opt = oracle.brute_force_starts(inst)
+        W = oracle.initial_order(inst)
+        for mode in (1, 2):
+            assert oracle.fbi(inst, W, mode)[1] >= opt

@@ -34,6 +34,11 @@ MUTANTS = {
                                "int pick = (int)(w % (unsigned)nf);"),
     # working-set reads skipping every other slot
     "reads_skip_slots": ("rp = (rp + 1) % F;", "rp = (rp + 2) % F;"),
+    # FBI's backward pass decoded on the original network instead of the reversed one
+    "fbi_not_reversed": ("int T = fbi_decode(in, &Q, mode, Wb, tau);", "int T = fbi_decode(in, &P, mode, Wb, tau);"),
+    # FBI's backward list by finish time, smallest first
+    "fbi_backward_order": ("if (fb > fa || (fb == fa && pos[b] > pos[a])) break;",
+                           "if (fb < fa || (fb == fa && pos[b] > pos[a])) break;"),
     # a block's improvement not written back to the working set
     "no_write_back": ("if (improved && x->Cbb < f->C) {", "if (improved && x->Cbb < f->C && 0) {"),
 }
@@ -114,3 +119,11 @@ def test_mutant_exchange_breaks_rules(oracle, tmp_path, name):
                 coop.test_exchange_rules(oracle, 4, 8, 1)
             else:
                 coop.test_single_block_without_exchanges_is_the_plain_search(oracle, 1)
+
+
+@pytest.mark.parametrize("name", ["fbi_not_reversed", "fbi_backward_order"])
+def test_mutant_fbi_breaks_backward_schedule(oracle, tmp_path, name):
+    import test_oracle_coop as coop
+    with mutant(oracle, tmp_path, name):
+        with pytest.raises(AssertionError):
+            coop.test_fbi_backward_schedule_is_a_schedule(oracle)
