@@ -156,7 +156,12 @@ int rcpsp_tabu_search(rcpsp_ctx *ctx, const int32_t *ids, int32_t count,
  * `blocks` tabu searches -- one CTA each, the CTAs of one thread-block
  * cluster -- that exchange solutions through a working set F of
  * `working_set` slots in device memory.  Slot k starts from the level order
- * of Sec. 4.1 with slot k's shuffle keys.  Every block reads a slot, then
+ * of Sec. 4.1 with slot k's shuffle keys, improved by the forward-backward
+ * improvement (FBI) when fbi_every says so: the list's schedule decoded
+ * backward on the reversed network in order of decreasing finish time
+ * (ties: later list position first), then forward in order of increasing
+ * mirrored start (ties: earlier position first), repeated while the
+ * makespan gets strictly shorter.  Every block reads a slot, then
  * runs the search of rcpsp_tabu_search on it; when its best list since the
  * read is better than the slot it read, or after more than I_assigned
  * iterations without that (Eq. 8, quantity factor read as I_block / 5), it
@@ -177,6 +182,9 @@ typedef struct {
     int32_t phi_steps;         /* Phi_steps (the paper: 20); 0 = no diversification  */
     int32_t assign_fixed;      /* iterations per read; 0 = Eq. 8                     */
     int32_t words_per_block;   /* P: random words per block in random_words          */
+    int32_t fbi_every;         /* e: slots e-1, 2e-1, ... start improved by the
+                                  forward-backward improvement (Sec. 6: every
+                                  second solution, e = 2); 0 = none              */
 } rcpsp_coop_params;
 
 /* Runs co-operating searches of the loaded instances `ids` (asynchronous on

@@ -675,7 +675,7 @@ int rcpsp_coop_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
         return set_err(c, RCPSP_E_INVALID_ARG, "co-operative searches keep no trace and capture no graph");
     const int B = cp->blocks, F = cp->working_set, P = cp->words_per_block;
     if (B < 1 || B > rcpsp::kMaxCoopBlocks || F < 1 || F > rcpsp::kMaxWorkingSet || cp->phi_max < 0 ||
-        cp->phi_steps < 0 || cp->assign_fixed < 0 || P < 0)
+        cp->phi_steps < 0 || cp->assign_fixed < 0 || P < 0 || cp->fbi_every < 0)
         return set_err(c, RCPSP_E_INVALID_ARG, "bad co-operation parameters");
     if (cp->phi_steps > 0 && (!random_words || P < 1))
         return set_err(c, RCPSP_E_INVALID_ARG, "diversification needs random words");
@@ -787,7 +787,7 @@ int rcpsp_coop_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
         std::memcpy(hb + plan_bytes + lists_bytes, random_words, static_cast<size_t>(count) * B * P * 4);
     e = cudaMemcpyAsync(db, hb, up_bytes, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->queue_dev, 0, sizeof(int), st);
-    rcpsp::CoopConfig cfg{B, F, cp->phi_max, cp->phi_steps, cp->assign_fixed, P};
+    rcpsp::CoopConfig cfg{B, F, cp->phi_max, cp->phi_steps, cp->assign_fixed, P, cp->fbi_every};
     const int nclusters = std::max(1, std::min(count, clusters));
     if (e == cudaSuccess)
         e = rcpsp::launch_coop(G, reinterpret_cast<const rcpsp::CoopItem *>(db), count, c->queue_dev, move_cap, cfg,

@@ -116,6 +116,61 @@ __device__ int diversify_warp(const SInst &I, int *W, int *pos, int *fsp, int *l
     return used;
 }
 
+// Forward-backward improvement of the list W by warp 0 (group 0 decodes):
+// the backward list (finish time descending, later position first) decoded
+// on the reversed network, then the forward list (mirrored start ascending,
+// earlier position first) decoded forward; repeated while the makespan gets
+// strictly shorter.  Scratch: pos, Wx (a list), S and tau (N each).  Ends with
+// W improved (or unchanged).
+template <int G>
+__device__ void fbi_warp(const SInst &I, int mode, int *W, int *Wx, int *pos, int *S, int *tau, int *area, int NG,
+                         const Group<G> &g, int &err) {
+    const int lane = threadIdx.x & 31, gw = lane / G, n = I.n;
+    SInst Ir = I;                                   // the reversed network
+    Ir.soff = I.poff;
+    Ir.slist = I.plist;
+    Ir.poff = I.soff;
+    Ir.plist = I.slist;
+    long long w0 = 0;
+    int C = decode<G>(I, mode, W, 0, 0, gw == 0, area, NG, g, w0, err, S);
+    C = __shfl_sync(kFull, C, 0);
+    for (;;) {
+        __syncwarp();
+        for (int p = lane; p < n; p += 32) pos[W[p]] = p;
+        __syncwarp();
+        for (int a = lane; a < n; a += 32) {          // rank in the backward order
+            const int fa = S[a] + I.dur[a], pa = pos[a];
+            int r = 0;
+            for (int b = 0; b < n; ++b) {
+                const int fb = S[b] + I.dur[b];
+                r += fb > fa || (fb == fa && pos[b] > pa);
+            }
+            Wx[r] = a;
+        }
+        __syncwarp();
+        int T = decode<G>(Ir, mode, Wx, 0, 0, gw == 0, area, NG, g, w0, err, tau);
+        T = __shfl_sync(kFull, T, 0);
+        __syncwarp();
+        for (int a = lane; a < n; a += 32) {          // rank in the forward order
+            const int sa = T - tau[a] - I.dur[a], pa = pos[a];
+            int r = 0;
+            for (int b = 0; b < n; ++b) {
+                const int sb = T - tau[b] - I.dur[b];
+                r += sb < sa || (sb == sa && pos[b] < pa);
+            }
+            Wx[r] = a;
+        }
+        __syncwarp();
+        int C2 = decode<G>(I, mode, Wx, 0, 0, gw == 0, area, NG, g, w0, err, S);
+        C2 = __shfl_sync(kFull, C2, 0);
+        if (!(C2 < C)) break;
+        C = C2;
+        __syncwarp();
+        for (int p = lane; p < n; p += 32) W[p] = Wx[p];
+    }
+    __syncwarp();
+}
+
 template <int G>
 __global__ void __launch_bounds__(512, 2) coop_kernel(const CoopItem *__restrict__ items, int count,
                                                     int *__restrict__ queue, int move_cap, CoopConfig cfg) {
@@ -186,6 +241,10 @@ __global__ void __launch_bounds__(512, 2) coop_kernel(const CoopItem *__restrict
             int32_t *slot = ci.slots + static_cast<long long>(k) * ci.slot_words;
             for (int p = tid; p < n; p += nthr) W[p] = __ldg(ci.init_lists + static_cast<long long>(k) * n + p);
             __syncthreads();
+            if (cfg.fbi_every > 0 && k % cfg.fbi_every == cfg.fbi_every - 1) {
+                if (warp == 0) fbi_warp<G>(I, mode, W, Wbest, pos, fsp, lpp, area, NG, g, err);
+                __syncthreads();
+            }
             if (warp == 0) {
                 long long w0 = 0;
                 const int c0 = decode<G>(I, mode, W, 0, 0, gw == 0, area, NG, g, w0, err);

@@ -69,6 +69,7 @@ struct CoopConfig {
     int32_t phi_max, phi_steps;      // diversification
     int32_t assign_fixed;            // iterations per read; 0 = Eq. 8
     int32_t words_per_block;         // P
+    int32_t fbi_every;               // FBI on slots k with k % e == e-1; 0 = none
 };
 
 constexpr int kMaxCoopBlocks = 16;   // largest cluster (non-portable above 8)

@@ -47,7 +47,8 @@ class Params(C.Structure):
 
 class CoopParams(C.Structure):
     _fields_ = [("blocks", C.c_int32), ("working_set", C.c_int32), ("phi_max", C.c_int32),
-                ("phi_steps", C.c_int32), ("assign_fixed", C.c_int32), ("words_per_block", C.c_int32)]
+                ("phi_steps", C.c_int32), ("assign_fixed", C.c_int32), ("words_per_block", C.c_int32),
+                ("fbi_every", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -281,7 +282,7 @@ class Solver:
     def coop_search(self, ids, iterations: int = 100, delta: int = 0, tabu_len: int = 0, mode: int = EVAL_AUTO,
                     stop_at_cp: bool = True, blocks: int = 4, working_set: int = 16, phi_max: int = 3,
                     phi_steps: int = 20, assign_fixed: int = 0, slot_keys=None, words=None,
-                    group_size: int = 0, warps_per_cta: int = 0, stream=None):
+                    group_size: int = 0, warps_per_cta: int = 0, stream=None, fbi_every: int = 2):
         """rcpsp_coop_search: `blocks` co-operating searches per instance.
 
         slot_keys: None, or per instance a list of `working_set` entries
@@ -303,7 +304,7 @@ class Solver:
             P = w.shape[2]
             wp = w.ctypes.data_as(C.POINTER(C.c_uint32))
         p = Params(iterations, delta, tabu_len, mode, int(stop_at_cp), group_size, warps_per_cta, 0, 0, 0)
-        cp = CoopParams(blocks, working_set, phi_max, phi_steps, assign_fixed, P)
+        cp = CoopParams(blocks, working_set, phi_max, phi_steps, assign_fixed, P, fbi_every)
         handle = getattr(stream, "cuda_stream", stream) or None
         self._check(self.lib.rcpsp_coop_search(self.ctx, _ptr(ids), len(ids), C.byref(p), C.byref(cp),
                                                _ptr(keys) if keys is not None else None, wp, handle))

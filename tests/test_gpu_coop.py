@@ -32,7 +32,8 @@ def solver():
 
 
 def run_both(solver, oracle, insts, iterations, delta, tabu_len, mode=R.EVAL_AUTO, stop_at_cp=True, blocks=4,
-             working_set=16, phi_max=3, phi_steps=20, assign_fixed=0, seed=1, words_per_block=64, **shape):
+             working_set=16, phi_max=3, phi_steps=20, assign_fixed=0, seed=1, words_per_block=64, fbi_every=2,
+             **shape):
     keys, words = [], []
     for k, x in enumerate(insts):
         kk, ww = I.coop_inputs(x, seed + k, working_set, blocks, words_per_block)
@@ -42,7 +43,7 @@ def run_both(solver, oracle, insts, iterations, delta, tabu_len, mode=R.EVAL_AUT
     solver.coop_search(ids, iterations=iterations, delta=delta, tabu_len=tabu_len, mode=mode,
                        stop_at_cp=stop_at_cp, blocks=blocks, working_set=working_set, phi_max=phi_max,
                        phi_steps=phi_steps, assign_fixed=assign_fixed, slot_keys=keys,
-                       words=words if phi_steps > 0 else None, **shape)
+                       words=words if phi_steps > 0 else None, fbi_every=fbi_every, **shape)
     got = solver.results(ids)
     solver.free(ids)
     kw = []
@@ -51,7 +52,7 @@ def run_both(solver, oracle, insts, iterations, delta, tabu_len, mode=R.EVAL_AUT
         kw.append(dict(iterations=iterations, delta=min(d, max(1, x.n - 3)), tabu_len=t, mode=mode,
                        stop_at_cp=int(stop_at_cp), blocks=blocks, working_set=working_set, phi_max=phi_max,
                        phi_steps=phi_steps, assign_fixed=assign_fixed, slot_keys=keys[k],
-                       words=words[k] if phi_steps > 0 else None))
+                       words=words[k] if phi_steps > 0 else None, fbi_every=fbi_every))
     ref = oracle.coop_search_batch(insts, kw, NPROC)
     for g, r in zip(got, ref):
         assert r["status"] == 0
@@ -126,11 +127,22 @@ def test_shapes_do_not_change_results(solver, oracle):
         assert cm == base
 
 
+@pytest.mark.parametrize("fbi_every", [0, 1, 2, 3])
+def test_forward_backward_improved_slots(solver, oracle, fbi_every):
+    """With no iterations the result is the best initial slot, so the
+    improved lists themselves are compared; then a short search on them."""
+    insts = I.config_batch("j30_batch", 10, first=200) + [x for x in I.config_batch("mixed_batch", 24)
+                                                          if x.n <= 92][:4]
+    for mode in (R.EVAL_TIME, R.EVAL_CAPACITY):
+        run_both(solver, oracle, insts, 0, 0, 0, mode=mode, blocks=2, working_set=6, fbi_every=fbi_every)
+    run_both(solver, oracle, insts, 20, 0, 0, blocks=2, working_set=6, fbi_every=fbi_every)
+
+
 def test_invalid_parameters(solver):
     x = I.config_batch("j30_single")
     ids = solver.load(x)
     for bad in (dict(blocks=0), dict(blocks=17), dict(working_set=0), dict(working_set=65),
-                dict(phi_max=-1), dict(phi_steps=5, words=None)):
+                dict(phi_max=-1), dict(phi_steps=5, words=None), dict(fbi_every=-1)):
         kw = dict(iterations=5, blocks=2, working_set=2, phi_steps=0)
         kw.update(bad)
         with pytest.raises(R.RcpspError) as e:
