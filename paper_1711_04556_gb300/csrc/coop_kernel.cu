@@ -285,8 +285,16 @@ __global__ void __launch_bounds__(512, 2) coop_kernel(const CoopItem *__restrict
             s_bRead[b] = 1;
             s_bDiv[b] = s_slotPhi[k] > cfg.phi_max && cfg.phi_steps > 0;
             s_bCbb[b] = s_slotC[k];
-            s_bAssigned[b] = cfg.assign_fixed > 0 ? cfg.assign_fixed
-                                                  : assigned_iterations(s_slotC[k], s_Cstar, s_slotIC[k], Ib);
+        };
+        // Eq. 8 budgets of this phase's reads, one thread per block (the
+        // inputs -- the slot's makespan and IC at the read, and C* -- are
+        // fixed while the reads are planned).  Every thread calls it.
+        auto plan_budgets = [&]() {
+            if (tid < B && s_bRead[tid])
+                s_bAssigned[tid] = cfg.assign_fixed > 0
+                    ? cfg.assign_fixed
+                    : assigned_iterations(s_bCread[tid], s_Cstar, s_bICread[tid], Ib);
+            __syncthreads();
         };
         // This CTA takes the slot its plan names; a diversified read decodes
         // its new list.  Ends with s_C, s_Cbb, Wbest and the tabu state set.
@@ -327,13 +335,12 @@ __global__ void __launch_bounds__(512, 2) coop_kernel(const CoopItem *__restrict
         auto share_diversified = [&](int par) {
             if (tid == 0) s_pub_div[par] = s_Cbb;
             cl.sync();
+            if (tid < B && s_bRead[tid] && s_bDiv[tid])
+                s_bCbb[tid] = tid == crank ? s_Cbb : *cl.map_shared_rank(&s_pub_div[par], tid);
+            __syncthreads();
             if (tid == 0)
                 for (int b = 0; b < B; ++b)
-                    if (s_bRead[b] && s_bDiv[b]) {
-                        const int v = b == crank ? s_Cbb : *cl.map_shared_rank(&s_pub_div[par], b);
-                        s_bCbb[b] = v;
-                        s_Cstar = ::min(s_Cstar, v);
-                    }
+                    if (s_bRead[b] && s_bDiv[b]) s_Cstar = ::min(s_Cstar, s_bCbb[b]);
         };
 
         // initial reads, in block order
@@ -345,6 +352,7 @@ __global__ void __launch_bounds__(512, 2) coop_kernel(const CoopItem *__restrict
             }
         }
         __syncthreads();
+        plan_budgets();
         load_read();
         if (s_anyDiv) share_diversified(1);
         __syncthreads();
@@ -390,14 +398,14 @@ __global__ void __launch_bounds__(512, 2) coop_kernel(const CoopItem *__restrict
             if (s_improved)
                 for (int p = tid; p < n; p += nthr) Wbest[p] = W[p];
             cl.sync();                                      // every block's best published
+            if (tid < B) s_bCbb[tid] = tid == crank ? s_Cbb : *cl.map_shared_rank(&s_pub[par], tid);
+            __syncthreads();
             // replicated exchange plan: writes in block order, then reads
             if (tid == 0) {
                 for (int b = 0; b < B; ++b) {
-                    const int v = b == crank ? s_Cbb : *cl.map_shared_rank(&s_pub[par], b);
-                    s_bCbb[b] = v;
                     s_bSince[b] += 1;
                     s_bRead[b] = 0;
-                    s_Cstar = ::min(s_Cstar, v);
+                    s_Cstar = ::min(s_Cstar, s_bCbb[b]);
                 }
                 for (int k = 0; k < F; ++k) s_winner[k] = -1;
                 s_anyRead = 0;
@@ -426,6 +434,7 @@ __global__ void __launch_bounds__(512, 2) coop_kernel(const CoopItem *__restrict
                 for (int b = 0; b < B; ++b) s_bRead[b] = s_bRead[b] == 1;
             }
             __syncthreads();
+            plan_budgets();
             // the last winning write of a slot stores this CTA's best list and
             // tabu state there (the slot this CTA had read; its new read is
             // already planned)
