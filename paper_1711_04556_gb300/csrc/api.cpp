@@ -713,6 +713,7 @@ int rcpsp_coop_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
     // launch shape: one for the call, every CTA of a cluster alike
     int G = gs, warps = p->warps_per_cta, dG, dW;
     default_shape(items, &dG, &dW);
+    if (!gs && !warps) tuned_shape(c, shape_key(items), &dG, &dW);   // the search's tuned shape, if any
     if (!G) G = dG;
     if (!warps) warps = std::max(dW, (G + 31) / 32);
     const int move_cap = launch_move_cap(items);
@@ -939,8 +940,11 @@ int rcpsp_autotune(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcpsp_
         int bG = 0, bW = 0, bC = 1;
         const int gsz[] = {1, 2, 4, 8, 16, 32};
         const int wcnt[] = {1, 2, 3, 4, 6, 8, 12, 16};
-        // clusters only pay when the class has fewer searches than the GPU has SMs
-        const int cmax = 2 * cn <= c->prop.multiProcessorCount ? 8 : 1;
+        // clusters pay when the class has fewer searches than the GPU has SMs,
+        // or when its searches are large (N > 160: long decode chains and big
+        // neighbourhoods, which would otherwise leave the GPU to a few
+        // long-running CTAs at the end of the call)
+        const int cmax = (2 * cn <= c->prop.multiProcessorCount || cls % 3 == 2) ? 8 : 1;
         for (int C = 1; C <= cmax; C *= 2)
         for (int G : gsz)
             for (int W : wcnt) {

@@ -43,6 +43,12 @@ struct Group {
         for (int o = G / 2; o > 0; o >>= 1) x = ::max(x, __shfl_xor_sync(kFull, x, o));
         return x;
     }
+    // sum over the group; every lane of the warp calls it
+    __device__ int sum(int x) const {
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+        return x;
+    }
 };
 
 // Shared-memory view of one instance.
@@ -258,6 +264,7 @@ __device__ int decode_capacity(const SInst &I, const int *W, int u, int v, bool 
         for (int j = g.lane; j < I.sum_cap; j += G) cst[j * NG] = 0;   // Sec. 5.1.1
     clear_es<G>(esa, n, NG, active, g);
     int cmax = 0;
+    int wk = 0;                                        // this lane's Alg. 4 steps
     int i = activity_at<G>(W, 0, u, v);
     for (int p = 0; p < n; ++p) {
         const int inext = activity_at<G>(W, p + 1 < n ? p + 1 : p, u, v);
@@ -272,55 +279,43 @@ __device__ int decode_capacity(const SInst &I, const int *W, int u, int v, bool 
         er = g.max(er);
         const int s = ::max(es, er);
         const int d = I.dur[i];
-        for (int k = 0; k < m; ++k) {
-            const int r = I.reqk[i * m + k];
-            const bool upd = active && d > 0 && r > 0;
-            int last = -1;
-            if (__any_sync(kFull, upd)) {
-                // Alg. 4 as a per-index closed form of its result:
-                //   j <  r : c'[j] = max(c[j], s+d)
-                //   j >= r : c'[j] = c[j-r] <= s ? c[j] : max(c[j], min(c[j-r], s+d))
-                // c_k is non-increasing, so with a = #{j : c[j] > s} nothing at
-                // j >= r + a changes (there c[j-r] <= s).  a is found chunk by
-                // chunk; the update then runs from the top chunk down so that
-                // c[j-r] is still old when it is read.
+        // Alg. 4, one lane per used resource (resources k = lane, lane+G, ...),
+        // as a per-index closed form of its result:
+        //   j <  r : c'[j] = max(c[j], s+d)
+        //   j >= r : c'[j] = c[j-r] <= s ? c[j] : max(c[j], min(c[j-r], s+d))
+        // c_k is non-increasing, so a = #{j : c[j] > s} is found by binary
+        // search and nothing at j >= r + a changes (there c[j-r] <= s).  The
+        // lane updates [0, r+a) from the top down, so that c[j-r] is still old
+        // when it is read; the first change it meets is Alg. 4's last one.
+        if (active && d > 0)
+            for (int k = g.lane; k < m; k += G) {
+                const int r = I.reqk[i * m + k];
+                if (r == 0) continue;
                 const int R = I.cap[k];
                 int *ck = cst + I.cbase[k] * NG;
-                int a = 0;
-                bool more = upd;
-                for (int J = 0; __any_sync(kFull, more); J += G) {
-                    const int j = J + g.lane;
-                    const bool above = more && j < R && ck[j * NG] > s;
-                    const unsigned m = g.bits(__ballot_sync(kFull, above));
-                    if (more) {
-                        a += __popc(m);
-                        more = m == (G == 32 ? 0xffffffffu : ((1u << G) - 1u)) && J + G < R;
+                int lo = 0, hi = R;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (ck[mid * NG] > s) lo = mid + 1;
+                    else hi = mid;
+                }
+                int last = -1;
+                for (int j = ::min(R, r + lo) - 1; j >= 0; --j) {
+                    const int old = ck[j * NG];
+                    int nv;
+                    if (j < r) {
+                        nv = ::max(old, s + d);
+                    } else {
+                        const int prev = ck[(j - r) * NG];
+                        nv = prev <= s ? old : ::max(old, ::min(prev, s + d));
+                    }
+                    if (nv != old) {
+                        ck[j * NG] = nv;
+                        if (last < 0) last = j;
                     }
                 }
-                const int top = ::min(R, r + a);            // indices that can change: [0, top)
-                const int topmax = __reduce_max_sync(kFull, upd ? top : 0);
-                for (int J = ((topmax - 1) / G) * G; J >= 0; J -= G) {
-                    const int j = J + g.lane;
-                    int old = 0, prev = 0;
-                    if (upd && j < top) {
-                        old = ck[j * NG];
-                        if (j >= r) prev = ck[(j - r) * NG];
-                    }
-                    __syncwarp();
-                    if (upd && j < top) {
-                        const int nv = j < r ? ::max(old, s + d)
-                                             : (prev <= s ? old : ::max(old, ::min(prev, s + d)));
-                        if (nv != old) {
-                            ck[j * NG] = nv;
-                            last = ::max(last, j);
-                        }
-                    }
-                    __syncwarp();
-                }
+                wk += last + 1;                         // Alg. 4 stops after its last change
             }
-            last = g.max(last);
-            if (upd) work += last + 1;                 // Alg. 4 stops after its last change
-        }
         if (active) {
             if (S_out && g.lane == 0) S_out[i] = s;
             cmax = ::max(cmax, s + d);
@@ -329,6 +324,7 @@ __device__ int decode_capacity(const SInst &I, const int *W, int u, int v, bool 
         __syncwarp();
         i = inext;
     }
+    work += g.sum(wk);
     (void)err;
     return cmax;
 }
