@@ -384,9 +384,14 @@ def run_ours(args):
     barrier()
     t_e2e = time.perf_counter()
     ev_e2e = 0
-    for _ in range(e2e_steps):
-        ids2 = solver.load(insts)
+    # a client that loads the next batch while the current one is searched:
+    # every step still uploads its instances and reads its results back
+    nxt = solver.load(insts)
+    for k in range(e2e_steps):
+        ids2 = nxt
         solver.search(ids2, use_graph=False, stream=st, **kw)
+        if k + 1 < e2e_steps:
+            nxt = solver.load(insts)
         out = solver.results(ids2)
         ev_e2e += sum(r["evaluated"] for r in out)
         solver.free(ids2)

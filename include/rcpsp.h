@@ -131,7 +131,10 @@ int rcpsp_destroy(rcpsp_ctx *ctx);
  * device.  Writes one id per instance to out_ids (host).  On any validation
  * error nothing is loaded and the code of the first bad instance is
  * returned (RCPSP_E_CYCLE, RCPSP_E_DUMMY, RCPSP_E_DEMAND_EXCEEDS_CAP,
- * RCPSP_E_TOO_LARGE, RCPSP_E_INVALID_ARG). */
+ * RCPSP_E_TOO_LARGE, RCPSP_E_INVALID_ARG).  The copy goes through pinned
+ * staging on a stream of the context; the call returns when the data is on
+ * the device, without waiting for searches still running, so loading the
+ * next batch overlaps the current search. */
 int rcpsp_load_instances(rcpsp_ctx *ctx, const rcpsp_instance *inst, int32_t count,
                          int32_t *out_ids);
 

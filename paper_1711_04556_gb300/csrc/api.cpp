@@ -80,6 +80,11 @@ struct rcpsp_ctx {
     cudaEvent_t fork = nullptr, join[kAuxStreams] = {};
     std::vector<int> g_launch_sig;
     // co-operative searches: plan, initial lists, random words and working sets
+    // instance upload: pinned staging and a stream of its own, so that a
+    // load overlaps a search that is still running on the caller's stream
+    cudaStream_t copy_stream = nullptr;
+    char *load_host = nullptr;
+    size_t load_host_cap = 0;
     void *coop_dev = nullptr;
     size_t coop_cap = 0;
     char *coop_host = nullptr;          // pinned staging of the uploaded part
@@ -311,6 +316,7 @@ int rcpsp_create(rcpsp_ctx **ctx, int device, const rcpsp_allocator *alloc) {
         e = cudaStreamCreateWithFlags(&c->aux[q], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join[q], cudaEventDisableTiming);
     }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         delete c;
         return RCPSP_E_CUDA;
@@ -339,6 +345,8 @@ int rcpsp_destroy(rcpsp_ctx *c) {
     dev_free(c, c->coop_dev, c->coop_cap, nullptr);
     if (c->items_host) cudaFreeHost(c->items_host);
     if (c->coop_host) cudaFreeHost(c->coop_host);
+    if (c->load_host) cudaFreeHost(c->load_host);
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     cudaEventDestroy(c->done);
     cudaEventDestroy(c->fork);
     for (int q = 0; q < kAuxStreams; ++q) {
@@ -414,15 +422,29 @@ int rcpsp_load_instances(rcpsp_ctx *c, const rcpsp_instance *inst, int32_t count
     b.bytes = b.out_offset + b.out_bytes;
     b.ptr = dev_alloc(c, b.bytes, nullptr);
     if (!b.ptr) return set_err(c, RCPSP_E_CUDA, "device allocation failed");
-    std::vector<int32_t> host(rec_words);
+    cudaError_t e = cudaSuccess;
+    if (c->load_host_cap < rec_words * 4) {
+        if (c->load_host) cudaFreeHost(c->load_host);
+        c->load_host = nullptr;
+        c->load_host_cap = 0;
+        e = cudaMallocHost(reinterpret_cast<void **>(&c->load_host), rec_words * 4);
+        if (e != cudaSuccess) {
+            dev_free(c, b.ptr, b.bytes, nullptr);
+            return cuda_err(c, e, "pinned staging");
+        }
+        c->load_host_cap = rec_words * 4;
+    }
+    int32_t *host = reinterpret_cast<int32_t *>(c->load_host);
     size_t ro = 0;
     for (int k = 0; k < count; ++k) {
-        std::memcpy(host.data() + ro, packed[k].record.data(), packed[k].record.size() * 4);
+        std::memcpy(host + ro, packed[k].record.data(), packed[k].record.size() * 4);
         ro += packed[k].record.size();
     }
-    cudaError_t e = cudaMemcpy(b.ptr, host.data(), rec_words * 4, cudaMemcpyHostToDevice);
+    e = cudaMemcpyAsync(b.ptr, host, rec_words * 4, cudaMemcpyHostToDevice, c->copy_stream);
     c->h2d += static_cast<long long>(rec_words) * 4;
-    if (e == cudaSuccess) e = cudaMemset(static_cast<char *>(b.ptr) + b.out_offset, 0, b.out_bytes);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(static_cast<char *>(b.ptr) + b.out_offset, 0, b.out_bytes, c->copy_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->copy_stream);   // staging free again, data in place
     if (e != cudaSuccess) {
         dev_free(c, b.ptr, b.bytes, nullptr);
         return cuda_err(c, e, "instance upload");

@@ -57,6 +57,12 @@ class Stats(C.Structure):
                 ("t_start_ns", C.c_int64), ("t_end_ns", C.c_int64)]
 
 
+# numpy image of rcpsp_stats, for reading many at once
+_STATS_DTYPE = np.dtype([("evaluated", "<i8"), ("work", "<i8"), ("iterations", "<i4"), ("eval_mode", "<i4"),
+                         ("critical_path", "<i4"), ("status", "<i4"), ("t_start_ns", "<i8"), ("t_end_ns", "<i8")])
+assert _STATS_DTYPE.itemsize == C.sizeof(Stats)
+
+
 class ServerConfig(C.Structure):
     _fields_ = [("slots", C.c_int32), ("max_batch", C.c_int32), ("memory_budget", C.c_int64),
                 ("poll_us", C.c_int32)]
@@ -337,16 +343,16 @@ class Solver:
         order = np.zeros(tot, np.int32)
         start = np.zeros(tot, np.int32)
         cmax = np.zeros(len(ids), np.int32)
-        stats = (Stats * len(ids))()
+        st = np.zeros(len(ids), _STATS_DTYPE)
         self._check(self.lib.rcpsp_get_schedules(self.ctx, _ptr(ids), len(ids), _ptr(order), _ptr(start),
-                                                 _ptr(cmax), stats))
+                                                 _ptr(cmax), st.ctypes.data_as(C.POINTER(Stats))))
+        cols = [st[f].tolist() for f in _STATS_DTYPE.names]
+        cm = cmax.tolist()
         out, at = [], 0
         for k, n in enumerate(ns):
-            s = stats[k]
-            out.append(dict(best_W=order[at:at + n], best_S=start[at:at + n], best_cmax=int(cmax[k]),
-                            evaluated=int(s.evaluated), work=int(s.work), iterations=int(s.iterations),
-                            mode=int(s.eval_mode), cp=int(s.critical_path), status=int(s.status),
-                            t_start_ns=int(s.t_start_ns), t_end_ns=int(s.t_end_ns)))
+            ev, wk, it, md, cp, stt, t0, t1 = (c[k] for c in cols)
+            out.append(dict(best_W=order[at:at + n], best_S=start[at:at + n], best_cmax=cm[k], evaluated=ev,
+                            work=wk, iterations=it, mode=md, cp=cp, status=stt, t_start_ns=t0, t_end_ns=t1))
             at += n
         return out
 
