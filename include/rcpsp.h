@@ -92,6 +92,18 @@ typedef struct {
                                    split its neighbourhood and exchange the best
                                    move through distributed shared memory;
                                    0 = choose automatically                      */
+    int32_t checkpoint;         /* 1: keep each search's state on the device when
+                                   the call ends (lists, tabu list and cache,
+                                   iteration, counters), for `resume` or
+                                   rcpsp_get_state                               */
+    int32_t resume;             /* 1: continue each instance from its kept state
+                                   for `iterations` more iterations; it must have
+                                   been kept with the same swap distance, tabu
+                                   length and evaluator.  Counters and the
+                                   iteration count continue, so k1 iterations
+                                   then k2 resumed equal k1+k2 in one call.  The
+                                   trace of a resumed call holds its own
+                                   iterations.                                    */
 } rcpsp_params;
 
 /* Result statistics of one instance. */
@@ -192,7 +204,8 @@ typedef struct {
 
 /* Runs co-operating searches of the loaded instances `ids` (asynchronous on
  * cuda_stream, like rcpsp_tabu_search; no trace, no graph capture:
- * record_trace / use_graph = 1 give RCPSP_E_INVALID_ARG).  slot_keys (host,
+ * record_trace / use_graph / checkpoint / resume = 1 give
+ * RCPSP_E_INVALID_ARG).  slot_keys (host,
  * copied, may be NULL = every slot unshuffled): for each id in order,
  * working_set rows of N shuffle keys (Sec. 4.1; all zeros = unshuffled).
  * random_words (host, copied; NULL allowed when phi_steps == 0): for each id
@@ -216,8 +229,9 @@ int rcpsp_coop_search(rcpsp_ctx *ctx, const int32_t *ids, int32_t count, const r
  * process exits.  Instances must already be loaded (rcpsp_load_instances
  * is where device memory is taken); results are read as usual with
  * rcpsp_get_schedules.  Limits: at most as many instances per call as the
- * array holds (9360; more gives RCPSP_E_TOO_LARGE), no trace and no graph
- * capture (record_trace or use_graph = 1 gives RCPSP_E_INVALID_ARG).  The
+ * array holds (8190; more gives RCPSP_E_TOO_LARGE), no trace, no graph
+ * capture and no checkpoints (record_trace, use_graph, checkpoint or resume
+ * = 1 gives RCPSP_E_INVALID_ARG).  The
  * first call on a device also looks up the array's device address with
  * that device current; make that first call before any stream capture.
  * Every call shares the one array and resets its counter: calls whose
@@ -258,7 +272,8 @@ int rcpsp_get_schedules(rcpsp_ctx *ctx, const int32_t *ids, int32_t count,
 /* Copies the iteration trace of the last search of an instance run with
  * record_trace = 1: [iterations][3] = (u, v, C_max after the move), (0, 0)
  * for an iteration without an admissible move.  `capacity` is the number of
- * int32 elements of `trace` (host); *written gets the number of iterations. */
+ * int32 elements of `trace` (host); *written gets the number of iterations
+ * of that call (for a resumed search: the iterations it added). */
 int rcpsp_get_trace(rcpsp_ctx *ctx, int32_t id, int32_t *trace, int32_t capacity,
                     int32_t *written);
 
@@ -280,6 +295,19 @@ int rcpsp_evaluate_lists(rcpsp_ctx *ctx, int32_t id, const int32_t *lists, int32
  * gets the reason of a failure.  Returns the same codes as loading. */
 int rcpsp_prepare_instance(const rcpsp_instance *inst, int32_t *critical_path, int32_t *horizon,
                            int32_t *initial_order, int32_t *eval_mode, char *msg, int32_t msg_len);
+
+/* Saved search state of a loaded instance (see rcpsp_params.checkpoint),
+ * for keeping a search outside the context or moving it to another one.
+ * rcpsp_get_state waits for the context's search, then copies the state to
+ * `buf` (host, `capacity` bytes); *bytes gets its size (call with buf = NULL
+ * to ask for it).  rcpsp_set_state gives the instance a state from `buf`
+ * (as written by rcpsp_get_state for an instance with the same N); the next
+ * search with resume = 1 continues it.  Errors: RCPSP_E_NOT_FOUND (id),
+ * RCPSP_E_INVALID_ARG (no kept state, or a state that is not for this
+ * instance), RCPSP_E_TOO_LARGE (capacity too small).  The paper has no
+ * counterpart (its working set keeps lists and tabu lists, Sec. 6.1). */
+int rcpsp_get_state(rcpsp_ctx *ctx, int32_t id, void *buf, size_t capacity, size_t *bytes);
+int rcpsp_set_state(rcpsp_ctx *ctx, int32_t id, const void *buf, size_t bytes);
 
 /* Bytes the context has copied host->device and device->host since it was
  * created (instance records, launch plans, results, traces); host. */
@@ -336,8 +364,8 @@ int rcpsp_server_create(rcpsp_server **srv, int device, const rcpsp_server_confi
 /* Stops the worker after the batches in flight and frees everything. */
 int rcpsp_server_destroy(rcpsp_server *srv);
 /* Validates one instance (as rcpsp_load_instances does; the same error
- * codes), copies it and queues it with its search parameters (record_trace
- * and use_graph must be 0).  Requests of one launch class with identical
+ * codes), copies it and queues it with its search parameters (record_trace,
+ * use_graph, checkpoint and resume must be 0).  Requests of one launch class with identical
  * parameters share batches, in arrival order; the class whose oldest
  * request is oldest is served first.  Returns at once. */
 int rcpsp_server_submit(rcpsp_server *srv, const rcpsp_instance *inst, const rcpsp_params *params,

@@ -44,6 +44,10 @@ struct Inst {
     int trace_iters = -1;    // iterations recorded by the last traced search, -1 = none
     bool alive = false;
     std::vector<int32_t> succ_off, succ;   // host copy of the arcs, to check caller lists
+    int32_t *ckpt = nullptr;               // kept search state (CkptLayout), device
+    size_t ckpt_bytes = 0;
+    bool ckpt_valid = false;               // holds a state for the parameters below
+    int ckpt_delta = 0, ckpt_tl = 0, ckpt_mode = 0;
 };
 
 int out_words(int n) { return rcpsp::align4(2 * n + rcpsp::kOutStats); }
@@ -338,7 +342,10 @@ int rcpsp_destroy(rcpsp_ctx *c) {
     wait_done(c);
     cudaDeviceSynchronize();
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
-    for (Inst &in : c->insts) dev_free(c, in.trace, in.trace_bytes, nullptr);
+    for (Inst &in : c->insts) {
+        dev_free(c, in.trace, in.trace_bytes, nullptr);
+        dev_free(c, in.ckpt, in.ckpt_bytes, nullptr);
+    }
     for (Block &b : c->blocks) dev_free(c, b.ptr, b.bytes, nullptr);
     dev_free(c, c->items_dev, c->items_cap, nullptr);
     dev_free(c, c->queue_dev, 64, nullptr);
@@ -487,6 +494,10 @@ int rcpsp_free_instances(rcpsp_ctx *c, const int32_t *ids, int32_t count) {
         dev_free(c, in.trace, in.trace_bytes, nullptr);
         in.trace = nullptr;
         in.trace_bytes = 0;
+        dev_free(c, in.ckpt, in.ckpt_bytes, nullptr);
+        in.ckpt = nullptr;
+        in.ckpt_bytes = 0;
+        in.ckpt_valid = false;
         Block &b = c->blocks[in.block];
         if (--b.live == 0) {
             dev_free(c, b.ptr, b.bytes, nullptr);
@@ -500,7 +511,8 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
     if (!c) return RCPSP_E_INVALID_ARG;
     if (!p || count < 0 || (count > 0 && !ids)) return set_err(c, RCPSP_E_INVALID_ARG, "bad arguments");
     if (p->iterations < 0 || p->max_swap_dist < 0 || p->tabu_len < 0 || p->tabu_len > RCPSP_MAX_TABU ||
-        p->eval_mode < 0 || p->eval_mode > 2 || p->warps_per_cta < 0 || p->warps_per_cta > 16)
+        p->eval_mode < 0 || p->eval_mode > 2 || p->warps_per_cta < 0 || p->warps_per_cta > 16 ||
+        p->checkpoint < 0 || p->checkpoint > 1 || p->resume < 0 || p->resume > 1)
         return set_err(c, RCPSP_E_INVALID_ARG, "bad search parameters");
     const int gs = p->group_size;
     if (gs != 0 && gs != 1 && gs != 2 && gs != 4 && gs != 8 && gs != 16 && gs != 32)
@@ -535,6 +547,22 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
         it.tabu_len = p->tabu_len ? p->tabu_len : tl;
         it.iterations = p->iterations;
         it.stop_at_cp = p->stop_at_cp ? 1 : 0;
+        if (p->checkpoint || p->resume) {
+            if (p->resume && !(in.ckpt_valid && in.ckpt_delta == it.delta && in.ckpt_tl == it.tabu_len &&
+                               in.ckpt_mode == it.mode))
+                return set_err(c, RCPSP_E_INVALID_ARG,
+                               "instance " + std::to_string(id) + " has no kept state for these parameters");
+            const size_t need = static_cast<size_t>(rcpsp::ckpt_layout(in.h.n, it.tabu_len, it.delta).words) * 4;
+            if (in.ckpt_bytes < need) {                   // (a kept state of these parameters has this size)
+                dev_free(c, in.ckpt, in.ckpt_bytes, nullptr);
+                in.ckpt = static_cast<int32_t *>(dev_alloc(c, need, nullptr));
+                in.ckpt_bytes = in.ckpt ? need : 0;
+                in.ckpt_valid = false;
+                if (!in.ckpt) return set_err(c, RCPSP_E_CUDA, "state allocation failed");
+            }
+            it.state = in.ckpt;
+            it.ckpt = (p->resume ? rcpsp::kCkptResume : 0) | (p->checkpoint ? rcpsp::kCkptSave : 0);
+        }
         if (p->record_trace) {
             const size_t need = static_cast<size_t>(std::max(1, p->iterations)) * 3 * 4;
             if (in.trace_bytes < need) {
@@ -676,9 +704,71 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
         if (e != cudaSuccess) return cuda_err(c, e, "search launch");
     }
     c->kernels += static_cast<long long>(launches.size());
+    if (p->checkpoint)
+        for (const LaunchItem &it : items) {
+            // items[] holds the ids' searches in call order
+            Inst &in = c->insts[ids[&it - items.data()]];
+            in.ckpt_valid = true;
+            in.ckpt_delta = it.delta;
+            in.ckpt_tl = it.tabu_len;
+            in.ckpt_mode = it.mode;
+        }
     e = cudaEventRecord(c->done, st);
     if (e != cudaSuccess) return cuda_err(c, e, "event record");
     c->pending = true;
+    return RCPSP_OK;
+}
+
+int rcpsp_get_state(rcpsp_ctx *c, int32_t id, void *buf, size_t capacity, size_t *bytes) {
+    if (!c) return RCPSP_E_INVALID_ARG;
+    if (id < 0 || id >= static_cast<int>(c->insts.size()) || !c->insts[id].alive)
+        return set_err(c, RCPSP_E_NOT_FOUND, "unknown instance id");
+    const Inst &in = c->insts[id];
+    if (!in.ckpt_valid) return set_err(c, RCPSP_E_INVALID_ARG, "instance has no kept state");
+    const size_t need = static_cast<size_t>(rcpsp::ckpt_layout(in.h.n, in.ckpt_tl, in.ckpt_delta).words) * 4;
+    if (bytes) *bytes = need;
+    if (!buf) return RCPSP_OK;
+    if (capacity < need) return set_err(c, RCPSP_E_TOO_LARGE, "state buffer too small");
+    cudaSetDevice(c->device);
+    int rc = wait_done(c);
+    if (rc != RCPSP_OK) return rc;
+    const cudaError_t e = cudaMemcpy(buf, in.ckpt, need, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_err(c, e, "state copy");
+    c->d2h += static_cast<long long>(need);
+    return RCPSP_OK;
+}
+
+int rcpsp_set_state(rcpsp_ctx *c, int32_t id, const void *buf, size_t bytes) {
+    if (!c) return RCPSP_E_INVALID_ARG;
+    if (id < 0 || id >= static_cast<int>(c->insts.size()) || !c->insts[id].alive)
+        return set_err(c, RCPSP_E_NOT_FOUND, "unknown instance id");
+    Inst &in = c->insts[id];
+    const int32_t *m = static_cast<const int32_t *>(buf);
+    if (!buf || bytes < static_cast<size_t>(rcpsp::kCkMeta) * 4 || m[rcpsp::kCkMagic] != rcpsp::kCkptMagic ||
+        m[rcpsp::kCkN] != in.h.n)
+        return set_err(c, RCPSP_E_INVALID_ARG, "not a kept state of this instance");
+    const int delta = m[rcpsp::kCkDelta], tl = m[rcpsp::kCkTabu], mode = m[rcpsp::kCkMode];
+    if (delta < 1 || delta > std::max(1, in.h.n - 3) || tl < 1 || tl > RCPSP_MAX_TABU ||
+        (mode != RCPSP_EVAL_TIME && mode != RCPSP_EVAL_CAPACITY) ||
+        bytes != static_cast<size_t>(rcpsp::ckpt_layout(in.h.n, tl, delta).words) * 4)
+        return set_err(c, RCPSP_E_INVALID_ARG, "not a kept state of this instance");
+    cudaSetDevice(c->device);
+    int rc = wait_done(c);
+    if (rc != RCPSP_OK) return rc;
+    if (in.ckpt_bytes < bytes) {
+        dev_free(c, in.ckpt, in.ckpt_bytes, nullptr);
+        in.ckpt = static_cast<int32_t *>(dev_alloc(c, bytes, nullptr));
+        in.ckpt_bytes = in.ckpt ? bytes : 0;
+        in.ckpt_valid = false;
+        if (!in.ckpt) return set_err(c, RCPSP_E_CUDA, "state allocation failed");
+    }
+    const cudaError_t e = cudaMemcpy(in.ckpt, buf, bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_err(c, e, "state copy");
+    c->h2d += static_cast<long long>(bytes);
+    in.ckpt_valid = true;
+    in.ckpt_delta = delta;
+    in.ckpt_tl = tl;
+    in.ckpt_mode = mode;
     return RCPSP_OK;
 }
 
@@ -693,8 +783,9 @@ int rcpsp_coop_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
     const int gs = p->group_size;
     if (gs != 0 && gs != 1 && gs != 2 && gs != 4 && gs != 8 && gs != 16 && gs != 32)
         return set_err(c, RCPSP_E_INVALID_ARG, "group_size must be 0, 1, 2, 4, 8, 16 or 32");
-    if (p->record_trace || p->use_graph)
-        return set_err(c, RCPSP_E_INVALID_ARG, "co-operative searches keep no trace and capture no graph");
+    if (p->record_trace || p->use_graph || p->checkpoint || p->resume)
+        return set_err(c, RCPSP_E_INVALID_ARG,
+                       "co-operative searches keep no trace or state and capture no graph");
     const int B = cp->blocks, F = cp->working_set, P = cp->words_per_block;
     if (B < 1 || B > rcpsp::kMaxCoopBlocks || F < 1 || F > rcpsp::kMaxWorkingSet || cp->phi_max < 0 ||
         cp->phi_steps < 0 || cp->assign_fixed < 0 || P < 0 || cp->fbi_every < 0)
@@ -834,8 +925,9 @@ int rcpsp_tabu_search_noalloc(rcpsp_ctx *c, const int32_t *ids, int32_t count, c
     const int gs = p->group_size;
     if (gs != 0 && gs != 1 && gs != 2 && gs != 4 && gs != 8 && gs != 16 && gs != 32)
         return set_err(c, RCPSP_E_INVALID_ARG, "group_size must be 0, 1, 2, 4, 8, 16 or 32");
-    if (p->record_trace || p->use_graph)
-        return set_err(c, RCPSP_E_INVALID_ARG, "the no-allocation search keeps no trace and captures no graph");
+    if (p->record_trace || p->use_graph || p->checkpoint || p->resume)
+        return set_err(c, RCPSP_E_INVALID_ARG,
+                       "the no-allocation search keeps no trace or state and captures no graph");
     if (count > rcpsp::noalloc_max_items())
         return set_err(c, RCPSP_E_TOO_LARGE, "the no-allocation search takes at most " +
                                                  std::to_string(rcpsp::noalloc_max_items()) + " instances per call");
@@ -944,6 +1036,8 @@ int rcpsp_autotune(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcpsp_
     q.iterations = std::min(p->iterations, trial_iterations);
     q.record_trace = 0;
     q.use_graph = 0;
+    q.checkpoint = 0;
+    q.resume = 0;
     int ret_G = 0, ret_W = 0, ret_C = 0, ret_count = -1;
     // each footprint class is tuned on its own (searches launch them apart)
     for (int cls = 0; cls < kClasses; ++cls) {
@@ -1094,9 +1188,10 @@ int rcpsp_get_trace(rcpsp_ctx *c, int32_t id, int32_t *trace, int32_t capacity, 
         return set_err(c, RCPSP_E_NOT_FOUND, "unknown instance id");
     const Inst &in = c->insts[id];
     if (in.trace_iters < 0 || !in.trace) return set_err(c, RCPSP_E_INVALID_ARG, "no trace recorded");
-    int32_t iters = 0;
-    cudaError_t e = cudaMemcpy(&iters, in.out + 2 * in.h.n + rcpsp::kOutIters, 4, cudaMemcpyDeviceToHost);
+    int32_t words[rcpsp::kOutStats];
+    cudaError_t e = cudaMemcpy(words, in.out + 2 * in.h.n, sizeof(words), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_err(c, e, "trace copy");
+    const int32_t iters = words[rcpsp::kOutIters] - words[rcpsp::kOutIters0];   // this call's iterations
     if (static_cast<long long>(iters) * 3 > capacity) return set_err(c, RCPSP_E_INVALID_ARG, "trace buffer too small");
     if (iters > 0) {
         e = cudaMemcpy(trace, in.trace, static_cast<size_t>(iters) * 3 * 4, cudaMemcpyDeviceToHost);

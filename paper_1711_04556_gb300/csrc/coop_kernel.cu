@@ -513,6 +513,7 @@ __global__ void __launch_bounds__(512, 2) coop_kernel(const CoopItem *__restrict
             st[kOutWorkLo] = static_cast<int32_t>(wsum & 0xffffffffll);
             st[kOutWorkHi] = static_cast<int32_t>(wsum >> 32);
             st[kOutIters] = s_it * B;
+            st[kOutIters0] = 0;
             st[kOutMode] = mode;
             st[kOutStatus] = e ? RCPSP_E_DEVICE : 0;
             const unsigned long long t1 = global_timer_ns();

@@ -34,20 +34,24 @@ struct InstHeader {
 };
 static_assert(sizeof(InstHeader) == 64, "InstHeader is 64 bytes");
 
-// One entry of a launch (112 bytes), ordered by estimated cost on the host.
+// One entry of a launch (128 bytes), ordered by estimated cost on the host.
 struct LaunchItem {
     InstHeader h;
     const int32_t *record;      // packed record in device memory
     int32_t *out;               // outputs: W*[N], S*[N], then kOutStats words
     int32_t *trace;             // [iterations*3] or nullptr
+    int32_t *state;             // saved search state (CkptLayout) or nullptr
     int32_t mode;               // evaluator for this search
-    int32_t iterations;         // iteration limit
+    int32_t iterations;         // iterations of this call
     int32_t delta;              // max swap distance
     int32_t tabu_len;           // tabu list length
     int32_t stop_at_cp;
-    int32_t pad;
+    int32_t ckpt;               // kCkpt* bits: resume from / save to `state`
+    int32_t pad[2];
 };
-static_assert(sizeof(LaunchItem) == 112, "LaunchItem is 112 bytes");
+static_assert(sizeof(LaunchItem) == 128, "LaunchItem is 128 bytes");
+
+enum : int { kCkptResume = 1, kCkptSave = 2 };
 
 // One entry of a co-operative launch (160 bytes): the search of `base` run
 // by a cluster of CTAs that exchange solutions through a working set F
@@ -58,7 +62,7 @@ struct CoopItem {
     const int32_t *init_lists;       // [working_set][N] initial list of every slot
     const uint32_t *words;           // [blocks][words_per_block] random words
     int32_t slot_words;
-    int32_t pad[5];
+    int32_t pad;
 };
 static_assert(sizeof(CoopItem) == 160, "CoopItem is 160 bytes");
 
@@ -79,7 +83,9 @@ constexpr int kMaxWorkingSet = 64;
 enum : int {
     kOutEvalLo = 0, kOutEvalHi, kOutWorkLo, kOutWorkHi,
     kOutIters, kOutCmax, kOutMode, kOutStatus,
-    kOutT0Lo, kOutT0Hi, kOutT1Lo, kOutT1Hi, kOutStats
+    kOutT0Lo, kOutT0Hi, kOutT1Lo, kOutT1Hi,
+    kOutIters0,                 // iterations before the call (a resumed search)
+    kOutStats
 };
 
 RC_HD int align4(int x) { return (x + 3) & ~3; }
@@ -137,6 +143,31 @@ RC_HD StateLayout state_layout(int inst_words, int n, int tabu_len, int delta, i
     o += ngroups * S.group_words;
     S.total = o;
     return S;
+}
+
+// Saved state of one search (checkpoint): a meta block, then the current
+// list W, the best list W*, the tabu list and the tabu cache, in the
+// kernel's shared-memory representation.  Meta words: magic, N, delta,
+// |TL|, evaluator, iterations done, C, C*, tabu write index, evaluated
+// (lo, hi), work (lo, hi).
+enum : int {
+    kCkMagic = 0, kCkN, kCkDelta, kCkTabu, kCkMode, kCkIters, kCkC, kCkCbest, kCkWidx,
+    kCkEvalLo, kCkEvalHi, kCkWorkLo, kCkWorkHi, kCkMeta = 16
+};
+constexpr int32_t kCkptMagic = 0x52435053;
+
+struct CkptLayout {
+    int W, Wbest, stl, tc, words;
+};
+
+RC_HD CkptLayout ckpt_layout(int n, int tabu_len, int delta) {
+    CkptLayout L;
+    L.W = kCkMeta;
+    L.Wbest = L.W + align4(n);
+    L.stl = L.Wbest + align4(n);
+    L.tc = L.stl + align4(tabu_len);
+    L.words = L.tc + align4((n * delta + 31) / 32);
+    return L;
 }
 
 // Words of one working-set slot: the list W, the tabu list (packed pairs),

@@ -45,7 +45,7 @@ template <int G>
 __global__ void __launch_bounds__(512, 2) search_kernel(const LaunchItem *__restrict__ items, int count,
                                                       int *__restrict__ queue, int move_cap, int csize) {
     extern __shared__ __align__(16) int sm[];
-    __shared__ int s_item, s_nmoves, s_C, s_Cbest, s_widx, s_it, s_improved, s_err;
+    __shared__ int s_item, s_nmoves, s_C, s_Cbest, s_widx, s_it, s_improved, s_err, s_it0, s_it_end;
     __shared__ unsigned long long s_bestp[2], s_t0;      // best key of the iteration, by parity
     __shared__ long long s_eval, s_work;
     const unsigned crank = csize > 1 ? cg::this_cluster().block_rank() : 0u;
@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(512, 2) search_kernel(const LaunchItem *__rest
             item = s_item;
         }
         if (item >= count) break;
-        const LaunchItem it = items[item];
+        const LaunchItem &it = items[item];
         const InstHeader &h = it.h;
         const int n = h.n, mode = it.mode, delta = it.delta, tl = it.tabu_len;
         const int pw = profile_words(mode, h.wps, h.ub, h.sum_cap);
@@ -85,39 +85,75 @@ __global__ void __launch_bounds__(512, 2) search_kernel(const LaunchItem *__rest
         unsigned *tc = reinterpret_cast<unsigned *>(sm + S.tc);
         int *moves = sm + S.moves;
         int *area = sm + S.groups + warp * NG * S.group_words + wl / G;
-        const int32_t *W0 = it.record + h.inst_words;
-        for (int p = tid; p < n; p += nthr) {
-            const int a = W0[p];
-            W[p] = a;
-            Wbest[p] = a;
-            pos[a] = p;
-        }
-        for (int x = tid; x < tl; x += nthr) stl[x] = 0;                 // (0,0) = empty move
-        for (int x = tid; x < (n * delta + 31) / 32; x += nthr) tc[x] = 0u;
-        if (tid == 0) {
-            s_t0 = global_timer_ns();
-            s_widx = 0;
-            s_it = 0;
-            s_eval = 0;
-            s_work = 0;
-            s_err = 0;
-        }
-        __syncthreads();
+        const int tcw = (n * delta + 31) / 32;
         int err = 0;
-        if (warp == 0) {
-            long long w0 = 0;
-            const int c0 = decode<G>(I, mode, W, 0, 0, gw == 0, area, NG, g, w0, err);
-            if (gw == 0 && g.lane == 0) {
-                s_C = c0;
-                s_Cbest = c0;
+        if (it.state && (it.ckpt & kCkptResume)) {
+            // continue a saved search: lists, tabu state, iteration and
+            // makespans as they were; the counters so far ride on rank 0
+            const CkptLayout CL = ckpt_layout(n, tl, delta);
+            const int32_t *sv = it.state;
+            for (int p = tid; p < n; p += nthr) {
+                const int a = sv[CL.W + p];
+                W[p] = a;
+                pos[a] = p;
+                Wbest[p] = sv[CL.Wbest + p];
             }
+            for (int x = tid; x < tl; x += nthr) stl[x] = sv[CL.stl + x];
+            for (int x = tid; x < tcw; x += nthr) tc[x] = static_cast<unsigned>(sv[CL.tc + x]);
+            if (tid == 0) {
+                s_t0 = global_timer_ns();
+                s_widx = sv[kCkWidx];
+                s_it = sv[kCkIters];
+                s_it0 = s_it;                     // iterations before this call
+                s_it_end = s_it + it.iterations;
+                s_C = sv[kCkC];
+                s_Cbest = sv[kCkCbest];
+                const long long ev = static_cast<long long>(static_cast<uint32_t>(sv[kCkEvalLo])) |
+                                     (static_cast<long long>(sv[kCkEvalHi]) << 32);
+                const long long wk = static_cast<long long>(static_cast<uint32_t>(sv[kCkWorkLo])) |
+                                     (static_cast<long long>(sv[kCkWorkHi]) << 32);
+                s_eval = crank == 0 ? ev : 0;
+                s_work = crank == 0 ? wk : 0;
+                s_err = 0;
+            }
+            __syncthreads();
+        } else {
+            const int32_t *W0 = it.record + h.inst_words;
+            for (int p = tid; p < n; p += nthr) {
+                const int a = W0[p];
+                W[p] = a;
+                Wbest[p] = a;
+                pos[a] = p;
+            }
+            for (int x = tid; x < tl; x += nthr) stl[x] = 0;             // (0,0) = empty move
+            for (int x = tid; x < tcw; x += nthr) tc[x] = 0u;
+            if (tid == 0) {
+                s_t0 = global_timer_ns();
+                s_widx = 0;
+                s_it = 0;
+                s_it0 = 0;
+                s_it_end = it.iterations;
+                s_eval = 0;
+                s_work = 0;
+                s_err = 0;
+            }
+            __syncthreads();
+            if (warp == 0) {
+                long long w0 = 0;
+                const int c0 = decode<G>(I, mode, W, 0, 0, gw == 0, area, NG, g, w0, err);
+                if (gw == 0 && g.lane == 0) {
+                    s_C = c0;
+                    s_Cbest = c0;
+                }
+            }
+            __syncthreads();
         }
-        __syncthreads();
+
         const int nslots = n > 3 ? (n - 3) * delta : 0;
         const unsigned dmagic = slot_magic(delta);
         long long my_work = 0;
         for (;;) {
-            if (s_it >= it.iterations || (it.stop_at_cp && s_Cbest == h.cp)) break;
+            if (s_it >= s_it_end || (it.stop_at_cp && s_Cbest == h.cp)) break;
             const int par = s_it & 1;
             if (tid == 0) s_bestp[par] = ~0ull;
             const unsigned long long my_key =
@@ -159,9 +195,9 @@ __global__ void __launch_bounds__(512, 2) search_kernel(const LaunchItem *__rest
                 if (bu | bv) tc_put(tc, bu, bv, delta, true);
                 s_widx = s_widx + 1 == tl ? 0 : s_widx + 1;
                 if (it.trace && crank == 0) {
-                    it.trace[3 * s_it + 0] = bu;
-                    it.trace[3 * s_it + 1] = bv;
-                    it.trace[3 * s_it + 2] = s_C;
+                    it.trace[3 * (s_it - s_it0) + 0] = bu;
+                    it.trace[3 * (s_it - s_it0) + 1] = bv;
+                    it.trace[3 * (s_it - s_it0) + 2] = s_C;
                 }
                 s_it = s_it + 1;
             }
@@ -209,6 +245,7 @@ __global__ void __launch_bounds__(512, 2) search_kernel(const LaunchItem *__rest
             st[kOutWorkLo] = static_cast<int32_t>(s_work & 0xffffffffll);
             st[kOutWorkHi] = static_cast<int32_t>(s_work >> 32);
             st[kOutIters] = s_it;
+            st[kOutIters0] = s_it0;
             st[kOutMode] = mode;
             st[kOutStatus] = s_err ? RCPSP_E_DEVICE : 0;
             const unsigned long long t1 = global_timer_ns();
@@ -216,6 +253,32 @@ __global__ void __launch_bounds__(512, 2) search_kernel(const LaunchItem *__rest
             st[kOutT0Hi] = static_cast<int32_t>(s_t0 >> 32);
             st[kOutT1Lo] = static_cast<int32_t>(t1 & 0xffffffffull);
             st[kOutT1Hi] = static_cast<int32_t>(t1 >> 32);
+        }
+        if (it.state && (it.ckpt & kCkptSave)) {
+            // keep the search where it stopped, for a later call to resume
+            const CkptLayout CL = ckpt_layout(n, tl, delta);
+            int32_t *sv = it.state;
+            for (int p = tid; p < n; p += nthr) {
+                sv[CL.W + p] = W[p];
+                sv[CL.Wbest + p] = Wbest[p];
+            }
+            for (int x = tid; x < tl; x += nthr) sv[CL.stl + x] = stl[x];
+            for (int x = tid; x < tcw; x += nthr) sv[CL.tc + x] = static_cast<int32_t>(tc[x]);
+            if (tid == 0) {
+                sv[kCkMagic] = kCkptMagic;
+                sv[kCkN] = n;
+                sv[kCkDelta] = delta;
+                sv[kCkTabu] = tl;
+                sv[kCkMode] = mode;
+                sv[kCkIters] = s_it;
+                sv[kCkC] = s_C;
+                sv[kCkCbest] = s_Cbest;
+                sv[kCkWidx] = s_widx;
+                sv[kCkEvalLo] = static_cast<int32_t>(s_eval & 0xffffffffll);
+                sv[kCkEvalHi] = static_cast<int32_t>(s_eval >> 32);
+                sv[kCkWorkLo] = static_cast<int32_t>(s_work & 0xffffffffll);
+                sv[kCkWorkHi] = static_cast<int32_t>(s_work >> 32);
+            }
         }
         }
         __syncthreads();

@@ -348,7 +348,8 @@ int rcpsp_server_destroy(rcpsp_server *s) {
 
 int rcpsp_server_submit(rcpsp_server *s, const rcpsp_instance *inst, const rcpsp_params *params, int64_t tag) {
     if (!s || !inst || !params) return RCPSP_E_INVALID_ARG;
-    if (params->record_trace || params->use_graph || params->iterations < 0) return RCPSP_E_INVALID_ARG;
+    if (params->record_trace || params->use_graph || params->checkpoint || params->resume || params->iterations < 0)
+        return RCPSP_E_INVALID_ARG;
     rcpsp::PackedInstance pk;
     std::string msg;
     const int rc = rcpsp::prepare_instance(*inst, pk, msg);

@@ -21,7 +21,8 @@ ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "CYCLE", -3: "DUMMY", -4: "DEMAND_EXCE
           -5: "TOO_LARGE", -6: "CUDA", -7: "TIMEOUT", -8: "NOT_FOUND", -9: "DEVICE"}
 EXPORTS = ("rcpsp_create", "rcpsp_destroy", "rcpsp_load_instances", "rcpsp_free_instances",
            "rcpsp_tabu_search", "rcpsp_tabu_search_noalloc", "rcpsp_coop_search", "rcpsp_autotune", "rcpsp_get_schedules", "rcpsp_get_trace", "rcpsp_evaluate_lists",
-           "rcpsp_prepare_instance", "rcpsp_transfer_bytes", "rcpsp_kernel_launches", "rcpsp_server_create", "rcpsp_server_destroy",
+           "rcpsp_prepare_instance", "rcpsp_transfer_bytes", "rcpsp_kernel_launches", "rcpsp_get_state",
+           "rcpsp_set_state", "rcpsp_server_create", "rcpsp_server_destroy",
            "rcpsp_server_submit", "rcpsp_server_poll", "rcpsp_server_get_stats", "rcpsp_last_error")
 
 
@@ -42,7 +43,7 @@ class Params(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("max_swap_dist", C.c_int32), ("tabu_len", C.c_int32),
                 ("eval_mode", C.c_int32), ("stop_at_cp", C.c_int32), ("group_size", C.c_int32),
                 ("warps_per_cta", C.c_int32), ("record_trace", C.c_int32), ("use_graph", C.c_int32),
-                ("cluster_size", C.c_int32)]
+                ("cluster_size", C.c_int32), ("checkpoint", C.c_int32), ("resume", C.c_int32)]
 
 
 class CoopParams(C.Structure):
@@ -123,6 +124,8 @@ def library(path: Optional[str] = None):
                                              P(C.c_int32), C.c_char_p, C.c_int32]),
         "rcpsp_transfer_bytes": (C.c_int, [C.c_void_p, P(C.c_int64), P(C.c_int64)]),
         "rcpsp_kernel_launches": (C.c_int, [C.c_void_p, P(C.c_int64)]),
+        "rcpsp_get_state": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_size_t, P(C.c_size_t)]),
+        "rcpsp_set_state": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_size_t]),
         "rcpsp_server_create": (C.c_int, [P(C.c_void_p), C.c_int, P(ServerConfig)]),
         "rcpsp_server_destroy": (C.c_int, [C.c_void_p]),
         "rcpsp_server_submit": (C.c_int, [C.c_void_p, P(Instance), P(Params), C.c_int64]),
@@ -277,11 +280,13 @@ class Solver:
 
     def search(self, ids, iterations: int = 100, delta: int = 0, tabu_len: int = 0, mode: int = EVAL_AUTO,
                stop_at_cp: bool = True, group_size: int = 0, warps_per_cta: int = 0, trace: bool = False,
-               use_graph: bool = False, stream=None, cluster_size: int = 0):
-        """Asynchronous search on ``stream`` (a torch.cuda.Stream, a raw handle or None)."""
+               use_graph: bool = False, stream=None, cluster_size: int = 0, checkpoint: bool = False,
+               resume: bool = False):
+        """Asynchronous search on ``stream`` (a torch.cuda.Stream, a raw handle or None).
+        checkpoint keeps each search's state on the device; resume continues it."""
         ids = _i32(ids)
         p = Params(iterations, delta, tabu_len, mode, int(stop_at_cp), group_size, warps_per_cta,
-                   int(trace), int(use_graph), cluster_size)
+                   int(trace), int(use_graph), cluster_size, int(checkpoint), int(resume))
         handle = getattr(stream, "cuda_stream", stream) or None
         self._check(self.lib.rcpsp_tabu_search(self.ctx, _ptr(ids), len(ids), C.byref(p), handle))
 
@@ -360,6 +365,19 @@ class Solver:
         h2d, d2h = C.c_int64(0), C.c_int64(0)
         self._check(self.lib.rcpsp_transfer_bytes(self.ctx, C.byref(h2d), C.byref(d2h)))
         return h2d.value, d2h.value
+
+    def get_state(self, id_: int) -> bytes:
+        """rcpsp_get_state: the kept search state of instance `id_`."""
+        size = C.c_size_t(0)
+        self._check(self.lib.rcpsp_get_state(self.ctx, int(id_), None, 0, C.byref(size)))
+        buf = (C.c_char * size.value)()
+        self._check(self.lib.rcpsp_get_state(self.ctx, int(id_), buf, size.value, C.byref(size)))
+        return bytes(buf)
+
+    def set_state(self, id_: int, state: bytes) -> None:
+        """rcpsp_set_state: give instance `id_` a kept state (from get_state)."""
+        buf = C.create_string_buffer(state, len(state))
+        self._check(self.lib.rcpsp_set_state(self.ctx, int(id_), buf, len(state)))
 
     def kernel_launches(self) -> int:
         n = C.c_int64(0)
