@@ -337,6 +337,14 @@ typedef struct {
                                    A request larger than the budget is admitted
                                    alone when nothing else is in flight          */
     int32_t poll_us;            /* idle wait of the worker loop; 0 = 100 us        */
+    int32_t slice_iterations;   /* > 0: time-slice requests of more iterations:
+                                   each batch runs at most this many iterations
+                                   of a request, whose state is then kept
+                                   (rcpsp_params.checkpoint) and which goes back
+                                   to the end of its queue until done, so long
+                                   searches take turns with newer requests;
+                                   results are those of an uninterrupted search.
+                                   0 = no slicing                                 */
 } rcpsp_server_config;
 
 typedef struct {
@@ -355,6 +363,7 @@ typedef struct {
     int64_t submitted, rejected, admitted, completed, batches;
     int64_t inflight_requests, pending, inflight_bytes, max_inflight_bytes;
     int64_t evaluated;          /* neighbours decoded by completed requests        */
+    int64_t requeued;           /* slices that ended with the request requeued     */
 } rcpsp_server_stats;
 
 /* Starts a server on `device` (cfg may be NULL for the defaults).  It owns

@@ -16,6 +16,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "host_prep.h"
 #include "kernels.h"
 #include "rcpsp_internal.h"
@@ -51,6 +53,14 @@ struct Inst {
 };
 
 int out_words(int n) { return rcpsp::align4(2 * n + rcpsp::kOutStats); }
+
+// A host phase as an NVTX range (shown by Nsight Systems; a no-op without a tool attached).
+struct HostRange {
+    explicit HostRange(const char *name) { nvtxRangePushA(name); }
+    ~HostRange() { nvtxRangePop(); }
+    HostRange(const HostRange &) = delete;
+    HostRange &operator=(const HostRange &) = delete;
+};
 
 constexpr int kClasses = 9;                  // launch classes of one call (see footprint_class)
 constexpr int kAuxStreams = kClasses - 1;
@@ -398,6 +408,7 @@ int rcpsp_prepare_instance(const rcpsp_instance *inst, int32_t *critical_path, i
 }
 
 int rcpsp_load_instances(rcpsp_ctx *c, const rcpsp_instance *inst, int32_t count, int32_t *out_ids) {
+    HostRange range("rcpsp_load_instances");
     if (!c) return RCPSP_E_INVALID_ARG;
     if (count < 0 || (count > 0 && (!inst || !out_ids))) return set_err(c, RCPSP_E_INVALID_ARG, "bad arguments");
     if (count == 0) return RCPSP_OK;
@@ -508,6 +519,7 @@ int rcpsp_free_instances(rcpsp_ctx *c, const int32_t *ids, int32_t count) {
 }
 
 int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcpsp_params *p, void *stream) {
+    HostRange range("rcpsp_tabu_search");
     if (!c) return RCPSP_E_INVALID_ARG;
     if (!p || count < 0 || (count > 0 && !ids)) return set_err(c, RCPSP_E_INVALID_ARG, "bad arguments");
     if (p->iterations < 0 || p->max_swap_dist < 0 || p->tabu_len < 0 || p->tabu_len > RCPSP_MAX_TABU ||
@@ -775,6 +787,7 @@ int rcpsp_set_state(rcpsp_ctx *c, int32_t id, const void *buf, size_t bytes) {
 int rcpsp_coop_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcpsp_params *p,
                       const rcpsp_coop_params *cp, const int32_t *slot_keys, const uint32_t *random_words,
                       void *stream) {
+    HostRange range("rcpsp_coop_search");
     if (!c) return RCPSP_E_INVALID_ARG;
     if (!p || !cp || count < 0 || (count > 0 && !ids)) return set_err(c, RCPSP_E_INVALID_ARG, "bad arguments");
     if (p->iterations < 0 || p->max_swap_dist < 0 || p->tabu_len < 0 || p->tabu_len > RCPSP_MAX_TABU ||
@@ -917,6 +930,7 @@ int rcpsp_coop_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
 
 int rcpsp_tabu_search_noalloc(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcpsp_params *p,
                               void *stream) {
+    HostRange range("rcpsp_tabu_search_noalloc");
     if (!c) return RCPSP_E_INVALID_ARG;
     if (!p || count < 0 || (count > 0 && !ids)) return set_err(c, RCPSP_E_INVALID_ARG, "bad arguments");
     if (p->iterations < 0 || p->max_swap_dist < 0 || p->tabu_len < 0 || p->tabu_len > RCPSP_MAX_TABU ||
@@ -1006,6 +1020,7 @@ int rcpsp_tabu_search_noalloc(rcpsp_ctx *c, const int32_t *ids, int32_t count, c
 
 int rcpsp_autotune(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcpsp_params *p, int32_t trial_iterations,
                    void *stream, int32_t *best_group_size, int32_t *best_warps, int32_t *best_cluster_size) {
+    HostRange range("rcpsp_autotune");
     if (!c) return RCPSP_E_INVALID_ARG;
     if (!p || count <= 0 || !ids || trial_iterations < 1) return set_err(c, RCPSP_E_INVALID_ARG, "bad arguments");
     cudaSetDevice(c->device);
@@ -1126,6 +1141,7 @@ int rcpsp_autotune(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcpsp_
 
 int rcpsp_get_schedules(rcpsp_ctx *c, const int32_t *ids, int32_t count, int32_t *order, int32_t *start,
                         int32_t *makespan, rcpsp_stats *stats) {
+    HostRange range("rcpsp_get_schedules");
     if (!c) return RCPSP_E_INVALID_ARG;
     if (count < 0 || (count > 0 && !ids)) return set_err(c, RCPSP_E_INVALID_ARG, "bad arguments");
     cudaSetDevice(c->device);
@@ -1204,6 +1220,7 @@ int rcpsp_get_trace(rcpsp_ctx *c, int32_t id, int32_t *trace, int32_t capacity, 
 
 int rcpsp_evaluate_lists(rcpsp_ctx *c, int32_t id, const int32_t *lists, int32_t count, int32_t eval_mode,
                          int32_t *start, int32_t *makespan, int64_t *work, void *stream) {
+    HostRange range("rcpsp_evaluate_lists");
     if (!c) return RCPSP_E_INVALID_ARG;
     if (count < 0 || (count > 0 && !lists) || eval_mode < 0 || eval_mode > 2)
         return set_err(c, RCPSP_E_INVALID_ARG, "bad arguments");

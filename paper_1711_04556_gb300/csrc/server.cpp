@@ -17,6 +17,12 @@
 //      instance size (256 / 64 / 16) and max_batch;
 //   3. sleeps on a condition variable until a submission or the next poll
 //      tick (no GPU spin: completion is an event query).
+// With slice_iterations > 0 a request of more iterations runs in slices:
+// each slice keeps the search state (rcpsp_params.checkpoint); at harvest an
+// unfinished request takes its state to the host (rcpsp_get_state) and goes
+// back to the end of its class queue, and its next batch restores the state
+// (rcpsp_set_state) and resumes.  The slices add up to exactly the
+// uninterrupted search.
 // Searches are deterministic and independent per instance, so a request's
 // result does not depend on what else is in flight.
 #include <cuda_runtime.h>
@@ -56,6 +62,8 @@ struct Request {
     bool has_key = false;
     int64_t bytes = 0;
     int64_t t_submit = 0;
+    int32_t total_iters = 0;     // iterations asked for
+    std::vector<char> state;     // kept search state between slices (empty: fresh)
     rcpsp_instance view() const {
         rcpsp_instance in;
         in.n = n;
@@ -127,6 +135,15 @@ int64_t footprint(const rcpsp::PackedInstance &pk) {
            static_cast<int64_t>(sizeof(rcpsp::LaunchItem));
 }
 
+// Parameters of a request's next slice: `done` iterations are behind it.
+void slice_params(const rcpsp_server *s, Request &r, int32_t done) {
+    const int32_t left = r.total_iters - done;
+    const int32_t sl = s->cfg.slice_iterations;
+    r.params.iterations = sl > 0 ? std::min(left, sl) : left;
+    r.params.checkpoint = sl > 0 && left > sl ? 1 : 0;
+    r.params.resume = done > 0 ? 1 : 0;
+}
+
 void harvest(rcpsp_server *s, Slot &sl) {
     const int cnt = static_cast<int>(sl.ids.size());
     int total_n = 0;
@@ -135,11 +152,28 @@ void harvest(rcpsp_server *s, Slot &sl) {
     std::vector<rcpsp_stats> stats(cnt);
     const int rc = rcpsp_get_schedules(sl.ctx, sl.ids.data(), cnt, W.data(), S.data(), cm.data(), stats.data());
     const int64_t t = now_ns();
-    std::vector<Completion> out(cnt);
+    std::vector<Completion> out;
+    std::vector<Request> again;                  // unfinished slices, back to their queues
+    out.reserve(cnt);
     int at = 0;
     for (int k = 0; k < cnt; ++k) {
-        const Request &r = sl.reqs[k];
-        Completion &c = out[k];
+        Request &r = sl.reqs[k];
+        const bool stopped = r.params.stop_at_cp && cm[k] == stats[k].critical_path;
+        if (rc == RCPSP_OK && stats[k].status == RCPSP_OK && r.params.checkpoint && !stopped &&
+            stats[k].iterations < r.total_iters) {
+            size_t bytes = 0;
+            if (rcpsp_get_state(sl.ctx, sl.ids[k], nullptr, 0, &bytes) == RCPSP_OK) {
+                r.state.resize(bytes);
+                if (rcpsp_get_state(sl.ctx, sl.ids[k], r.state.data(), bytes, &bytes) == RCPSP_OK) {
+                    slice_params(s, r, stats[k].iterations);
+                    at += r.n;
+                    again.push_back(std::move(r));
+                    continue;
+                }
+            }
+        }
+        out.emplace_back();
+        Completion &c = out.back();
         c.W.assign(W.begin() + at, W.begin() + at + r.n);
         c.S.assign(S.begin() + at, S.begin() + at + r.n);
         at += r.n;
@@ -166,6 +200,10 @@ void harvest(rcpsp_server *s, Slot &sl) {
         }
         s->inflight_bytes -= sl.bytes;
         s->st.inflight_requests -= cnt;
+        for (Request &r : again) {
+            s->st.requeued++;
+            s->pending[r.cls].push_back(std::move(r));
+        }
     }
     s->cv_done.notify_all();
     sl.busy = false;
@@ -233,6 +271,9 @@ bool admit(rcpsp_server *s, Slot &sl) {
     for (const Request &r : sl.reqs) views.push_back(r.view());
     sl.ids.assign(views.size(), 0);
     int rc = rcpsp_load_instances(sl.ctx, views.data(), static_cast<int32_t>(views.size()), sl.ids.data());
+    for (size_t k = 0; rc == RCPSP_OK && k < sl.reqs.size(); ++k)
+        if (!sl.reqs[k].state.empty())
+            rc = rcpsp_set_state(sl.ctx, sl.ids[k], sl.reqs[k].state.data(), sl.reqs[k].state.size());
     if (rc == RCPSP_OK) {
         sl.t_launch = now_ns();
         rc = rcpsp_tabu_search(sl.ctx, sl.ids.data(), static_cast<int32_t>(sl.ids.size()), &sl.reqs[0].params,
@@ -308,6 +349,7 @@ int rcpsp_server_create(rcpsp_server **out, int device, const rcpsp_server_confi
         if (cfg->max_batch > 0) s->cfg.max_batch = cfg->max_batch;
         if (cfg->memory_budget > 0) s->cfg.memory_budget = cfg->memory_budget;
         if (cfg->poll_us > 0) s->cfg.poll_us = cfg->poll_us;
+        if (cfg->slice_iterations > 0) s->cfg.slice_iterations = cfg->slice_iterations;
     }
     if (cudaSetDevice(device) != cudaSuccess) {
         delete s;
@@ -375,6 +417,8 @@ int rcpsp_server_submit(rcpsp_server *s, const rcpsp_instance *inst, const rcpsp
     }
     r.bytes = footprint(pk);
     r.cls = request_class(pk, *params);
+    r.total_iters = params->iterations;
+    slice_params(s, r, 0);
     r.t_submit = now_ns();
     {
         std::lock_guard<std::mutex> lk(s->mu);

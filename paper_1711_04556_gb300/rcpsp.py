@@ -66,7 +66,7 @@ assert _STATS_DTYPE.itemsize == C.sizeof(Stats)
 
 class ServerConfig(C.Structure):
     _fields_ = [("slots", C.c_int32), ("max_batch", C.c_int32), ("memory_budget", C.c_int64),
-                ("poll_us", C.c_int32)]
+                ("poll_us", C.c_int32), ("slice_iterations", C.c_int32)]
 
 
 class Completion(C.Structure):
@@ -80,7 +80,7 @@ class Completion(C.Structure):
 class ServerStats(C.Structure):
     _fields_ = [(k, C.c_int64) for k in ("submitted", "rejected", "admitted", "completed", "batches",
                                          "inflight_requests", "pending", "inflight_bytes",
-                                         "max_inflight_bytes", "evaluated")]
+                                         "max_inflight_bytes", "evaluated", "requeued")]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -407,10 +407,10 @@ class Server:
     """Continuous-batching solve server (rcpsp_server_* in include/rcpsp.h)."""
 
     def __init__(self, device: int = 0, slots: int = 8, max_batch: int = 256, memory_budget: int = 1 << 30,
-                 poll_us: int = 100, lib_path: Optional[str] = None):
+                 poll_us: int = 100, lib_path: Optional[str] = None, slice_iterations: int = 0):
         self.lib = library(lib_path)
         self.srv = C.c_void_p()
-        cfg = ServerConfig(slots, max_batch, memory_budget, poll_us)
+        cfg = ServerConfig(slots, max_batch, memory_budget, poll_us, slice_iterations)
         rc = self.lib.rcpsp_server_create(C.byref(self.srv), device, C.byref(cfg))
         if rc != 0:
             raise RcpspError(rc, "server create")

@@ -85,3 +85,29 @@ def test_invalid_request_is_rejected():
             srv.submit(bad, tag=1)
         assert e.value.code == -4
         assert srv.stats()["rejected"] == 1
+
+
+def test_time_slicing_gives_uninterrupted_results(oracle):
+    """With slice_iterations the server runs long requests in slices (state
+    kept between batches, requests requeued); every result is still the
+    uninterrupted search's, and short requests submitted later finish first."""
+    longs = I.config_batch("j30_batch", 40, first=150) + I.config_batch("j120_batch", 3, first=40)
+    shorts = I.config_batch("j30_batch", 8, first=400)
+    with R.Server(0, slots=4, max_batch=16, slice_iterations=30) as srv:
+        for k, x in enumerate(longs):
+            srv.submit(x, tag=k, iterations=150, delta=0, tabu_len=0, stop_at_cp=False)
+        for k, x in enumerate(shorts):
+            srv.submit(x, tag=1000 + k, iterations=20, delta=0, tabu_len=0, stop_at_cp=False)
+        got = drain(srv, len(longs) + len(shorts))
+        st = srv.stats()
+    assert st["requeued"] > 0
+    params = [(150,) + I.search_params(x.n - 2) + (0, 0) for x in longs]
+    refs = oracle.tabu_search_batch(longs, params, NPROC)
+    for k, r in enumerate(refs):
+        g = got[k]
+        assert g["status"] == 0 and g["iterations"] == 150
+        assert g["best_cmax"] == r["best_cmax"] and g["evaluated"] == r["evaluated"] and g["work"] == r["work"]
+        assert g["best_W"].tolist() == r["best_W"].tolist()
+    last_short = max(got[1000 + k]["t_done_ns"] for k in range(len(shorts)))
+    last_long = max(got[k]["t_done_ns"] for k in range(len(longs)))
+    assert last_short < last_long
