@@ -145,7 +145,7 @@ __device__ int decode_time(const SInst &I, const int *W, int u, int v, bool acti
     const uint32_t hi = I.hi;
     uint32_t capw[WPS];
 #pragma unroll
-    for (int w = 0; w < WPS; ++w) capw[w] = I.capw[w];
+    for (int w = 0; w < WPS; ++w) capw[w] = I.capw[w] | hi;   // profile words carry the guard bits
     clear_es<G>(esa, n, NG, active, g);
     // Every step starts with R_k free units (Sec. 5.2.1).  Steps at or after
     // the frontier F have not been touched by this decode, so they are not
@@ -181,7 +181,7 @@ __device__ int decode_time(const SInst &I, const int *W, int u, int v, bool acti
 #pragma unroll
                     for (int w = 0; w < WPS; ++w) {
                         const uint32_t x = a0[(w * ubs + G * j) * NG];
-                        fit[j] = fit[j] && (((x | hi) - rq[w]) & hi) == hi;
+                        fit[j] = fit[j] && ((x - rq[w]) & hi) == hi;
                     }
                 }
             }
