@@ -175,15 +175,30 @@ int launch_move_cap(const std::vector<LaunchItem> &items) {
     return std::min(rcpsp::kDefaultMoveCap, (m + 31) & ~31);
 }
 
-size_t smem_bytes(const std::vector<LaunchItem> &items, int ngroups, int move_cap) {
+// Positions between the kept prefix states of an N-activity search: at most
+// 16 states (16 / kmul), at least 8 * kmul positions apart.
+int prefix_k_for(int n, int kmul) { return kmul * std::max(8, (n + 15) / 16); }
+
+// Shared memory of a class at this shape; kmul > 0 adds the kept prefix states.
+size_t smem_bytes(const std::vector<LaunchItem> &items, int ngroups, int move_cap, int kmul = 0) {
     int words = 0;
     for (const LaunchItem &it : items) {
         const int pw = rcpsp::profile_words(it.mode, it.h.wps, it.h.ub, it.h.sum_cap);
+        const int snap = kmul > 0 ? rcpsp::prefix_words(it.h.n, pw, prefix_k_for(it.h.n, kmul)) : 0;
         const rcpsp::StateLayout S =
-            rcpsp::state_layout(it.h.inst_words, it.h.n, it.tabu_len, it.delta, move_cap, pw, ngroups);
+            rcpsp::state_layout(it.h.inst_words, it.h.n, it.tabu_len, it.delta, move_cap, pw, ngroups, snap);
         words = std::max(words, S.total);
     }
     return static_cast<size_t>(words) * 4;
+}
+
+// Prefix reuse pays when an iteration takes several decode rounds: the
+// kept states cost one decode of the current list per iteration.
+bool prefix_pays(const std::vector<LaunchItem> &items, int ngroups, int csize) {
+    double feas = 0;
+    for (const LaunchItem &it : items) feas += it.h.n > 3 ? 0.12 * (it.h.n - 3) * it.delta : 0.0;
+    feas /= std::max<size_t>(1, items.size());
+    return feas >= 3.0 * ngroups * std::max(1, csize);
 }
 
 // Launch class of a search: its footprint -- per-group scratch words (profile
@@ -202,6 +217,7 @@ int footprint_class(const LaunchItem &it) {
 
 struct ClassLaunch {
     int offset = 0, count = 0, G = 0, threads = 0, blocks = 0, move_cap = 0, csize = 1;
+    bool prefix = false;         // prefix reuse (kernel variant, kept states in shared memory)
     size_t smem = 0;
 };
 
@@ -622,6 +638,15 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
         }
         if (smem > smem_limit)
             return set_err(c, RCPSP_E_TOO_LARGE, "instance state does not fit in shared memory at this launch shape");
+        if (prefix_pays(part, warps * (32 / G), L.csize))
+            for (int kmul = 1; kmul <= 4 && !L.prefix; kmul *= 2) {   // fewer states when short of room
+                const size_t with = smem_bytes(part, warps * (32 / G), L.move_cap, kmul);
+                if (with > smem_limit) continue;
+                L.prefix = true;
+                smem = with;
+                for (int k = L.offset; k < L.offset + L.count; ++k)
+                    sorted[k].prefix_k = prefix_k_for(sorted[k].h.n, kmul);
+            }
         L.G = G;
         L.threads = warps * 32;
         L.smem = smem;
@@ -629,7 +654,7 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
         cudaError_t e = rcpsp::prepare_search(G, smem_limit);
         if (e != cudaSuccess) return cuda_err(c, e, "kernel attributes");
         int units = 0;
-        e = rcpsp::search_occupancy(G, L.threads, smem, L.csize, &units);
+        e = rcpsp::search_occupancy(G, L.threads, smem, L.csize, &units, L.prefix);
         if (e != cudaSuccess) return cuda_err(c, e, "occupancy");
         if (units < 1) return set_err(c, RCPSP_E_TOO_LARGE, "launch shape does not fit on the GPU");
         L.blocks = L.csize == 1 ? std::max(1, std::min(L.count, units * c->prop.multiProcessorCount))
@@ -638,7 +663,8 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
     }
     std::vector<int> sig;
     for (const ClassLaunch &L : launches)
-        sig.insert(sig.end(), {L.offset, L.count, L.G, L.threads, L.blocks, L.move_cap, static_cast<int>(L.smem), L.csize});
+        sig.insert(sig.end(), {L.offset, L.count, L.G, L.threads, L.blocks, L.move_cap, static_cast<int>(L.smem),
+                               L.csize, L.prefix ? 1 : 0});
     // device copy of the plan
     cudaError_t e = cudaSuccess;
     const size_t ibytes = sizeof(LaunchItem) * count;
@@ -679,7 +705,7 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
             cudaStream_t sq = q == 0 ? s0 : c->aux[q - 1];
             if (q > 0 && (r = cudaStreamWaitEvent(sq, c->fork, 0)) != cudaSuccess) return r;
             r = rcpsp::launch_search(L.G, c->items_dev + L.offset, L.count, c->queue_dev + q, L.move_cap, L.blocks,
-                                     L.threads, L.smem, sq, L.csize);
+                                     L.threads, L.smem, sq, L.csize, L.prefix);
             if (r != cudaSuccess) return r;
             if (q > 0 && (r = cudaEventRecord(c->join[q - 1], sq)) != cudaSuccess) return r;
         }

@@ -132,10 +132,27 @@ __device__ __forceinline__ void clear_es(int *es, int n, int NG, bool active, co
     __syncwarp();
 }
 
+// Kept decoder states of the current list (prefix reuse, see prefix_count):
+// snapshot j (1..count) is the state before position j*K, at base +
+// (j-1)*stride: [0] frontier F, [1] makespan so far, [2] work so far, then
+// the profile (time-indexed: WPS planes of UB words; capacity-indexed: the
+// c_k) and the N earliest starts.  base == nullptr: no prefix reuse.
+struct Prefix {
+    int *base;
+    int K, count, stride;
+};
+
+// First position a neighbour decode of swap(u, v) must place itself.
+__device__ __forceinline__ int prefix_start(const Prefix &px, int u, bool produce) {
+    if (!px.base || produce || u <= 0) return 0;
+    return ::min(u / px.K, px.count) * px.K;
+}
+
 // Time-indexed decode, WPS = 32-bit words per time step of the packed profile.
-template <int G, int WPS>
+template <int G, int WPS, bool PFX>
 __device__ int decode_time(const SInst &I, const int *W, int u, int v, bool active, int *area, int NG,
-                           const Group<G> &g, int &work, int &err, int *S_out) {
+                           const Group<G> &g, int &work, int &err, int *S_out, const Prefix &px,
+                           bool produce) {
     constexpr int U = G >= 32 ? 1 : (G >= 16 ? 2 : 4);   // steps a lane tests per round
     constexpr int R = G * U;                               // steps a group tests per round (<= 32)
     const int n = I.n, ub = I.ub;
@@ -146,14 +163,48 @@ __device__ int decode_time(const SInst &I, const int *W, int u, int v, bool acti
     uint32_t capw[WPS];
 #pragma unroll
     for (int w = 0; w < WPS; ++w) capw[w] = I.capw[w] | hi;   // profile words carry the guard bits
-    clear_es<G>(esa, n, NG, active, g);
     // Every step starts with R_k free units (Sec. 5.2.1).  Steps at or after
     // the frontier F have not been touched by this decode, so they are not
     // stored: they are written the first time an activity covers them.
     int F = 0;
     int cmax = 0;
-    int i = activity_at<G>(W, 0, u, v);
-    for (int p = 0; p < n; ++p) {
+    const int p0 = PFX ? prefix_start(px, u, produce) : 0;
+    if (PFX && p0 > 0) {
+        // start from the kept state of the current list before position p0
+        const int *sn = px.base + (p0 / px.K - 1) * px.stride;
+        if (active) {
+            F = sn[0];
+            cmax = sn[1];
+            work += sn[2];
+#pragma unroll
+            for (int w = 0; w < WPS; ++w)
+                for (int t = g.lane; t < F; t += G) prof[(w * ubs + t) * NG] = sn[4 + w * ubs + t];
+            for (int x = g.lane; x < n; x += G) esa[x * NG] = sn[4 + WPS * ubs + x];
+        }
+        __syncwarp();
+    } else {
+        clear_es<G>(esa, n, NG, active, g);
+    }
+    const int pstart = PFX ? __reduce_min_sync(kFull, active ? p0 : n) : 0;
+    int i = activity_at<G>(W, pstart < n ? pstart : 0, u, v);
+    for (int p = pstart; p < n; ++p) {
+        const bool act = PFX ? active && p >= p0 : active;
+        if (PFX && produce && p > 0 && p % px.K == 0 && p / px.K <= px.count) {
+            // keep the state before position p (warp-uniform condition)
+            int *sn = px.base + (p / px.K - 1) * px.stride;
+            if (active) {
+#pragma unroll
+                for (int w = 0; w < WPS; ++w)
+                    for (int t = g.lane; t < F; t += G) sn[4 + w * ubs + t] = prof[(w * ubs + t) * NG];
+                for (int x = g.lane; x < n; x += G) sn[4 + WPS * ubs + x] = esa[x * NG];
+                if (g.lane == 0) {
+                    sn[0] = F;
+                    sn[1] = cmax;
+                    sn[2] = work;
+                }
+            }
+            __syncwarp();
+        }
         const int inext = activity_at<G>(W, p + 1 < n ? p + 1 : p, u, v);
         const int es = esa[i * NG];
         const int d = I.dur[i];
@@ -167,7 +218,7 @@ __device__ int decode_time(const SInst &I, const int *W, int u, int v, bool acti
         // steps, or keeps the trailing run of fitting steps as the new
         // verified prefix -- the same window as Alg. 5's loadTime count.
         int s = es, k = 0;
-        bool done = !active || d == 0;
+        bool done = !act || d == 0;
         while (__any_sync(kFull, !done)) {
             if (!done && s + k >= F) done = true;
             const int tlim = done ? INT_MIN : F;
@@ -226,7 +277,7 @@ __device__ int decode_time(const SInst &I, const int *W, int u, int v, bool acti
             }
         }
         const int f = s + d;
-        if (active) {
+        if (act) {
             // Alg. 6: take r_{i,k} units over [s, s+d) (fields never borrow);
             // untouched steps in [F, s) get R_k, those in [F, s+d) R_k - r.
             if (d > 0) {
@@ -247,31 +298,62 @@ __device__ int decode_time(const SInst &I, const int *W, int u, int v, bool acti
             work += f - es;
             cmax = ::max(cmax, f);
         }
-        push_finish<G>(I, i, f, esa, NG, g, active);
+        push_finish<G>(I, i, f, esa, NG, g, act);
         __syncwarp();
         i = inext;
     }
     return cmax;
 }
 
-template <int G>
+template <int G, bool PFX>
 __device__ int decode_capacity(const SInst &I, const int *W, int u, int v, bool active, int *area, int NG,
-                               const Group<G> &g, int &work, int &err, int *S_out) {
-    const int n = I.n, m = I.m;
+                               const Group<G> &g, int &work, int &err, int *S_out, const Prefix &px,
+                               bool produce) {
+    const int n = I.n, m = I.m, sc = I.sum_cap;
     int *cst = area;                                   // c_k, concatenated
-    int *esa = area + I.sum_cap * NG;
-    if (active)
-        for (int j = g.lane; j < I.sum_cap; j += G) cst[j * NG] = 0;   // Sec. 5.1.1
-    clear_es<G>(esa, n, NG, active, g);
+    int *esa = area + sc * NG;
     int cmax = 0;
     int wk = 0;                                        // this lane's Alg. 4 steps
-    int i = activity_at<G>(W, 0, u, v);
-    for (int p = 0; p < n; ++p) {
+    const int p0 = PFX ? prefix_start(px, u, produce) : 0;
+    if (PFX && p0 > 0) {
+        // start from the kept state of the current list before position p0
+        const int *sn = px.base + (p0 / px.K - 1) * px.stride;
+        if (active) {
+            cmax = sn[1];
+            if (g.lane == 0) wk = sn[2];
+            for (int j = g.lane; j < sc; j += G) cst[j * NG] = sn[4 + j];
+            for (int x = g.lane; x < n; x += G) esa[x * NG] = sn[4 + sc + x];
+        }
+        __syncwarp();
+    } else {
+        if (active)
+            for (int j = g.lane; j < sc; j += G) cst[j * NG] = 0;   // Sec. 5.1.1
+        clear_es<G>(esa, n, NG, active, g);
+    }
+    const int pstart = PFX ? __reduce_min_sync(kFull, active ? p0 : n) : 0;
+    int i = activity_at<G>(W, pstart < n ? pstart : 0, u, v);
+    for (int p = pstart; p < n; ++p) {
+        const bool act = PFX ? active && p >= p0 : active;
+        if (PFX && produce && p > 0 && p % px.K == 0 && p / px.K <= px.count) {
+            // keep the state before position p (warp-uniform condition)
+            int *sn = px.base + (p / px.K - 1) * px.stride;
+            const int wsum = g.sum(wk);
+            if (active) {
+                for (int j = g.lane; j < sc; j += G) sn[4 + j] = cst[j * NG];
+                for (int x = g.lane; x < n; x += G) sn[4 + sc + x] = esa[x * NG];
+                if (g.lane == 0) {
+                    sn[0] = 0;
+                    sn[1] = cmax;
+                    sn[2] = wsum;
+                }
+            }
+            __syncwarp();
+        }
         const int inext = activity_at<G>(W, p + 1 < n ? p + 1 : p, u, v);
         const int es = esa[i * NG];
         // Eq. 7: es_res = max over used resources of c_k[R_k - r_{i,k}]
         int er = 0;
-        if (active)
+        if (act)
             for (int k = g.lane; k < m; k += G) {
                 const int r = I.reqk[i * m + k];
                 if (r > 0) er = ::max(er, cst[(I.cbase[k] + I.cap[k] - r) * NG]);
@@ -287,7 +369,7 @@ __device__ int decode_capacity(const SInst &I, const int *W, int u, int v, bool 
         // search and nothing at j >= r + a changes (there c[j-r] <= s).  The
         // lane updates [0, r+a) from the top down, so that c[j-r] is still old
         // when it is read; the first change it meets is Alg. 4's last one.
-        if (active && d > 0)
+        if (act && d > 0)
             for (int k = g.lane; k < m; k += G) {
                 const int r = I.reqk[i * m + k];
                 if (r == 0) continue;
@@ -316,11 +398,11 @@ __device__ int decode_capacity(const SInst &I, const int *W, int u, int v, bool 
                 }
                 wk += last + 1;                         // Alg. 4 stops after its last change
             }
-        if (active) {
+        if (act) {
             if (S_out && g.lane == 0) S_out[i] = s;
             cmax = ::max(cmax, s + d);
         }
-        push_finish<G>(I, i, s + d, esa, NG, g, active);
+        push_finish<G>(I, i, s + d, esa, NG, g, act);
         __syncwarp();
         i = inext;
     }
@@ -329,15 +411,21 @@ __device__ int decode_capacity(const SInst &I, const int *W, int u, int v, bool 
     return cmax;
 }
 
-template <int G>
+// One decode by the groups of a warp; PFX compiles the prefix-reuse paths in.
+template <int G, bool PFX = false>
 __device__ __forceinline__ int decode(const SInst &I, int mode, const int *W, int u, int v, bool active,
                                       int *area, int NG, const Group<G> &g, long long &work, int &err,
-                                      int *S_out = nullptr) {
+                                      int *S_out = nullptr, const Prefix &px = Prefix{nullptr, 1, 0, 0},
+                                      bool produce = false) {
     int wk = 0, c;
-    if (mode == RCPSP_EVAL_CAPACITY) c = decode_capacity<G>(I, W, u, v, active, area, NG, g, wk, err, S_out);
-    else if (I.wps == 1) c = decode_time<G, 1>(I, W, u, v, active, area, NG, g, wk, err, S_out);
-    else if (I.wps == 2) c = decode_time<G, 2>(I, W, u, v, active, area, NG, g, wk, err, S_out);
-    else c = decode_time<G, 4>(I, W, u, v, active, area, NG, g, wk, err, S_out);
+    if (mode == RCPSP_EVAL_CAPACITY)
+        c = decode_capacity<G, PFX>(I, W, u, v, active, area, NG, g, wk, err, S_out, px, produce);
+    else if (I.wps == 1)
+        c = decode_time<G, 1, PFX>(I, W, u, v, active, area, NG, g, wk, err, S_out, px, produce);
+    else if (I.wps == 2)
+        c = decode_time<G, 2, PFX>(I, W, u, v, active, area, NG, g, wk, err, S_out, px, produce);
+    else
+        c = decode_time<G, 4, PFX>(I, W, u, v, active, area, NG, g, wk, err, S_out, px, produce);
     work += wk;
     return c;
 }
@@ -376,7 +464,8 @@ __device__ __forceinline__ void tc_put(unsigned *tc, int u, int v, int delta, bo
 
 // ---------------------------------------------------------------------------
 // Steps 1-3 of an iteration (Sec. 6) on the CTA's current list W: the first
-// successor / last predecessor position of every position, then, stripe by
+// successor / last predecessor position of every position (and, with prefix
+// reuse, the kept decoder states of W, see Prefix), then, stripe by
 // stripe of move_cap potential moves, the feasible moves (with csize > 1
 // only this cluster rank's chunks of 32 slots) ballot-compacted into
 // `moves` and decoded by the groups.  Returns the thread's smallest key
@@ -386,11 +475,12 @@ __device__ __forceinline__ void tc_put(unsigned *tc, int u, int v, int delta, bo
 // my_work.  Starts and ends with a __syncthreads, so the caller may reset
 // its reduction word before the call.
 // ---------------------------------------------------------------------------
-template <int G>
+template <int G, bool PFX = false>
 __device__ __forceinline__ unsigned long long best_admissible_key(
         const SInst &I, int mode, const int *W, const int *pos, int *fsp, int *lpp, const unsigned *tc,
         int *moves, int *area, int n, int delta, int nslots, unsigned dmagic, int move_cap, int aspiration,
-        int csize, unsigned crank, int *s_nmoves, long long *s_eval, long long &my_work, int &err) {
+        int csize, unsigned crank, int *s_nmoves, long long *s_eval, long long &my_work, int &err,
+        const Prefix &px = Prefix{nullptr, 1, 0, 0}) {
     constexpr int NG = 32 / G;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int warp = tid >> 5, wl = tid & 31;
@@ -405,6 +495,12 @@ __device__ __forceinline__ unsigned long long best_admissible_key(
         for (int e = I.poff[a]; e < I.poff[a + 1]; ++e) l = ::max(l, pos[I.plist[e]]);
         fsp[p] = f;
         lpp[p] = l;
+    }
+    if (PFX && warp == 0) {
+        // prefix reuse: one group decodes the current list and keeps its
+        // state before positions K, 2K, ... (its work is not a neighbour's)
+        long long w0 = 0;
+        decode<G, PFX>(I, mode, W, 0, 0, gw == 0, area, NG, g, w0, err, nullptr, px, true);
     }
     __syncthreads();
     unsigned long long my_key = ~0ull;
@@ -443,7 +539,7 @@ __device__ __forceinline__ unsigned long long best_admissible_key(
             const bool act = q < nm;
             const int code = act ? moves[q] : 0;
             const int u = code & 0xffff, v = code >> 16;
-            const int c = decode<G>(I, mode, W, u, v, act, area, NG, g, my_work, err);
+            const int c = decode<G, PFX>(I, mode, W, u, v, act, area, NG, g, my_work, err, nullptr, px);
             if (act && (!tc_get(tc, u, v, delta) || c < aspiration)) {
                 const unsigned long long key =
                     (static_cast<unsigned long long>(c) << 32) | static_cast<unsigned>(code & 0xffff) << 16 |

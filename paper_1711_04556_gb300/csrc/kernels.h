@@ -11,10 +11,12 @@ namespace rcpsp {
 cudaError_t prepare_search(int group_size, size_t smem);
 // Resident units of the search kernel at this shape: CTAs per SM when
 // csize == 1, clusters on the whole GPU when csize > 1.
-cudaError_t search_occupancy(int group_size, int threads, size_t smem, int csize, int *units);
+// `prefix`: the kernel variant with prefix reuse (items with prefix_k > 0).
+cudaError_t search_occupancy(int group_size, int threads, size_t smem, int csize, int *units,
+                             bool prefix = false);
 // blocks = CTAs (a multiple of csize); csize > 1 launches clusters of csize CTAs.
 cudaError_t launch_search(int group_size, const LaunchItem *items, int count, int *queue, int move_cap,
-                          int blocks, int threads, size_t smem, cudaStream_t st, int csize);
+                          int blocks, int threads, size_t smem, cudaStream_t st, int csize, bool prefix = false);
 cudaError_t launch_evaluate(int group_size, const LaunchItem &item, const int32_t *lists, int count,
                             int32_t *start, int32_t *cmax, long long *work, int *err, int blocks, int threads,
                             size_t smem, cudaStream_t st);

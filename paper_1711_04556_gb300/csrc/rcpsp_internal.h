@@ -47,7 +47,8 @@ struct LaunchItem {
     int32_t tabu_len;           // tabu list length
     int32_t stop_at_cp;
     int32_t ckpt;               // kCkpt* bits: resume from / save to `state`
-    int32_t pad[2];
+    int32_t prefix_k;           // > 0: positions between kept prefix states (prefix_*)
+    int32_t pad;
 };
 static_assert(sizeof(LaunchItem) == 128, "LaunchItem is 128 bytes");
 
@@ -118,6 +119,7 @@ struct StateLayout {
     int groups;          // first word of the per-warp group areas
     int prof_words;      // profile words of one group (time- or capacity-indexed)
     int group_words;     // profile + finish times of one group
+    int snaps;           // first word of the kept prefix states (prefix reuse)
     int total;           // words of dynamic shared memory
 };
 
@@ -125,8 +127,17 @@ RC_HD int profile_words(int mode, int wps, int ub, int sum_cap) {
     return mode == RCPSP_EVAL_CAPACITY ? sum_cap : wps * (ub > 0 ? ub : 1);
 }
 
+// Prefix reuse: a swap (u, v) leaves list positions below u as they are, so
+// a neighbour's decode may start from the decoder state of the current list
+// before position floor(u/K)*K.  These states -- frontier, makespan so far,
+// work so far, the profile (or capacity state) and the earliest starts --
+// are kept before positions K, 2K, ..., count*K < N.
+RC_HD int prefix_count(int n, int K) { return K > 0 ? (n - 1) / K : 0; }
+RC_HD int prefix_stride(int n, int prof_words) { return align4(4 + prof_words + n); }
+RC_HD int prefix_words(int n, int prof_words, int K) { return prefix_count(n, K) * prefix_stride(n, prof_words); }
+
 RC_HD StateLayout state_layout(int inst_words, int n, int tabu_len, int delta, int move_cap,
-                               int prof_words, int ngroups) {
+                               int prof_words, int ngroups, int snap_words = 0) {
     StateLayout S;
     int o = inst_words;
     S.W = o;     o += align4(n);
@@ -141,6 +152,8 @@ RC_HD StateLayout state_layout(int inst_words, int n, int tabu_len, int delta, i
     S.prof_words = prof_words;
     S.group_words = prof_words + n;
     o += ngroups * S.group_words;
+    S.snaps = o;
+    o += snap_words;
     S.total = o;
     return S;
 }

@@ -41,7 +41,7 @@ namespace {
 // memory; all CTAs then apply the same move.  Rank 0 pops the work queue,
 // sums the counters and writes the results.
 // ---------------------------------------------------------------------------
-template <int G>
+template <int G, bool PFX>
 __global__ void __launch_bounds__(512, 2) search_kernel(const LaunchItem *__restrict__ items, int count,
                                                       int *__restrict__ queue, int move_cap, int csize) {
     extern __shared__ __align__(16) int sm[];
@@ -73,7 +73,11 @@ __global__ void __launch_bounds__(512, 2) search_kernel(const LaunchItem *__rest
         const InstHeader &h = it.h;
         const int n = h.n, mode = it.mode, delta = it.delta, tl = it.tabu_len;
         const int pw = profile_words(mode, h.wps, h.ub, h.sum_cap);
-        const StateLayout S = state_layout(h.inst_words, n, tl, delta, move_cap, pw, ngroups);
+        const int pk = PFX ? it.prefix_k : 0;
+        const StateLayout S = state_layout(h.inst_words, n, tl, delta, move_cap, pw, ngroups,
+                                           prefix_words(n, pw, pk));
+        const Prefix px{pk > 0 ? sm + S.snaps : nullptr, pk > 0 ? pk : 1, prefix_count(n, pk),
+                        prefix_stride(n, pw)};
         stage_instance(sm, it.record, h.inst_words);
         const SInst I = bind_instance(sm, h);
         int *W = sm + S.W;
@@ -157,8 +161,8 @@ __global__ void __launch_bounds__(512, 2) search_kernel(const LaunchItem *__rest
             const int par = s_it & 1;
             if (tid == 0) s_bestp[par] = ~0ull;
             const unsigned long long my_key =
-                best_admissible_key<G>(I, mode, W, pos, fsp, lpp, tc, moves, area, n, delta, nslots, dmagic,
-                                       move_cap, s_Cbest, csize, crank, &s_nmoves, &s_eval, my_work, err);
+                best_admissible_key<G, PFX>(I, mode, W, pos, fsp, lpp, tc, moves, area, n, delta, nslots, dmagic,
+                                       move_cap, s_Cbest, csize, crank, &s_nmoves, &s_eval, my_work, err, px);
             // 4. best admissible move of the block, then of the cluster
             const unsigned long long wk = warp_min_u64(my_key);
             if (wl == 0 && wk != ~0ull) atomicMin(&s_bestp[par], wk);
@@ -334,13 +338,18 @@ __global__ void __launch_bounds__(512, 2) evaluate_kernel(LaunchItem item, const
 
 template <int G>
 cudaError_t prepare_search_g(size_t smem) {
-    return cudaFuncSetAttribute(search_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(smem));
+    cudaError_t e = cudaFuncSetAttribute(search_kernel<G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(search_kernel<G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(smem));
+    return e;
 }
 
-template <int G>
+template <int G, bool PFX>
 cudaError_t occupancy_g(int threads, size_t smem, int csize, int *units) {
-    if (csize <= 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(units, search_kernel<G>, threads, smem);
+    if (csize <= 1)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(units, search_kernel<G, PFX>, threads, smem);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(csize);
     cfg.blockDim = dim3(threads);
@@ -352,14 +361,14 @@ cudaError_t occupancy_g(int threads, size_t smem, int csize, int *units) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaOccupancyMaxActiveClusters(units, search_kernel<G>, &cfg);
+    return cudaOccupancyMaxActiveClusters(units, search_kernel<G, PFX>, &cfg);
 }
 
-template <int G>
+template <int G, bool PFX>
 cudaError_t launch_search_g(const LaunchItem *items, int count, int *queue, int move_cap, int blocks,
                             int threads, size_t smem, cudaStream_t st, int csize) {
     if (csize <= 1) {
-        search_kernel<G><<<blocks, threads, smem, st>>>(items, count, queue, move_cap, 1);
+        search_kernel<G, PFX><<<blocks, threads, smem, st>>>(items, count, queue, move_cap, 1);
         return cudaGetLastError();
     }
     cudaLaunchConfig_t cfg = {};
@@ -374,7 +383,7 @@ cudaError_t launch_search_g(const LaunchItem *items, int count, int *queue, int 
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, search_kernel<G>, items, count, queue, move_cap, csize);
+    return cudaLaunchKernelEx(&cfg, search_kernel<G, PFX>, items, count, queue, move_cap, csize);
 }
 
 template <int G>
@@ -405,14 +414,18 @@ cudaError_t prepare_search(int group_size, size_t smem) {
     RCPSP_DISPATCH_G(group_size, return prepare_search_g<GG>(smem))
 }
 
-cudaError_t search_occupancy(int group_size, int threads, size_t smem, int csize, int *units) {
-    RCPSP_DISPATCH_G(group_size, return occupancy_g<GG>(threads, smem, csize, units))
+cudaError_t search_occupancy(int group_size, int threads, size_t smem, int csize, int *units, bool prefix) {
+    if (prefix) RCPSP_DISPATCH_G(group_size, return (occupancy_g<GG, true>(threads, smem, csize, units)))
+    RCPSP_DISPATCH_G(group_size, return (occupancy_g<GG, false>(threads, smem, csize, units)))
 }
 
 cudaError_t launch_search(int group_size, const LaunchItem *items, int count, int *queue, int move_cap,
-                          int blocks, int threads, size_t smem, cudaStream_t st, int csize) {
-    RCPSP_DISPATCH_G(group_size,
-                     return launch_search_g<GG>(items, count, queue, move_cap, blocks, threads, smem, st, csize))
+                          int blocks, int threads, size_t smem, cudaStream_t st, int csize, bool prefix) {
+    if (prefix)
+        RCPSP_DISPATCH_G(group_size, return (launch_search_g<GG, true>(items, count, queue, move_cap, blocks,
+                                                                       threads, smem, st, csize)))
+    RCPSP_DISPATCH_G(group_size, return (launch_search_g<GG, false>(items, count, queue, move_cap, blocks,
+                                                                    threads, smem, st, csize)))
 }
 
 cudaError_t launch_evaluate(int group_size, const LaunchItem &item, const int32_t *lists, int count,
