@@ -219,7 +219,8 @@ def run_reference(args):
     return 0
 
 
-def serving_run(R, I, device, family, rate, seconds, iterations, pool_size=512, seed=5, drain_s=30.0):
+def serving_run(R, I, device, family, rate, seconds, iterations, pool_size=512, seed=5, drain_s=30.0,
+                slice_iterations=0):
     """Poisson arrivals at `rate` req/s for `seconds` into the continuous-batching server.
 
     Requests cycle through a pool of distinct instances of `family`; each is
@@ -233,7 +234,7 @@ def serving_run(R, I, device, family, rate, seconds, iterations, pool_size=512, 
     arrivals = np.cumsum(gaps)
     arrivals = arrivals[arrivals < seconds]
     done = []
-    with R.Server(device, slots=8, max_batch=256, memory_budget=2 << 30) as srv:
+    with R.Server(device, slots=8, max_batch=256, memory_budget=2 << 30, slice_iterations=slice_iterations) as srv:
         # warm-up: batches on the slots (kernels loaded, staging allocated)
         # before the measured stream
         for k in range(64):
@@ -263,11 +264,15 @@ def serving_run(R, I, device, family, rate, seconds, iterations, pool_size=512, 
     ev = sum(c["evaluated"] for c in done)
     st = {k: st[k] - st0[k] if k in ("batches",) else st[k] for k in st}
     p50, p99 = percentiles(lat) if lat else (None, None)
+    p90 = float(np.percentile(lat, 90)) if lat else None
+    lmax = float(max(lat)) if lat else None
     return {"workload": f"{family} requests, {iterations} iterations each, Poisson {rate:g} req/s for {seconds:g} s "
-                        f"(after a warm-up of 64 requests)",
+                        f"(after a warm-up of 64 requests)"
+                        + (f", time-sliced every {slice_iterations} iterations" if slice_iterations else ""),
+            "requeued": st.get("requeued", 0),
             "offered_req_s": len(arrivals) / seconds, "completed": len(lat), "submitted": int(len(arrivals)),
             "completed_req_s": len(lat) / wall, "schedules_per_s": ev / wall, "wall_s": wall,
-            "latency_ms": {"p50": p50, "p99": p99}, "batches": st["batches"],
+            "latency_ms": {"p50": p50, "p90": p90, "p99": p99, "max": lmax}, "batches": st["batches"],
             "max_inflight_bytes": st["max_inflight_bytes"]}
 
 
@@ -450,7 +455,8 @@ def run_ours(args):
             extra["cooperation"] = coop_run(solver, R, I, insts, ids, ref_res, kw, st, args)
         if args.serving_seconds > 0:
             extra["serving"] = serving_run(R, I, local, args.serving_family, args.serving_rate, args.serving_seconds,
-                                           args.serving_iterations, drain_s=args.serving_drain)
+                                           args.serving_iterations, drain_s=args.serving_drain,
+                                           slice_iterations=args.serving_slice)
         extra["latency_ms"] = {
             "single_instance_e2e": {"p50": p50, "p99": p99, "reps": args.latency_reps,
                                     "what": "1 instance, 100 iterations, load+search+results through the C API"},
@@ -529,6 +535,8 @@ def main():
     ap.add_argument("--serving-family", default=WORKLOAD["family"])
     ap.add_argument("--serving-iterations", type=int, default=WORKLOAD["iterations"])
     ap.add_argument("--serving-drain", type=float, default=30.0)
+    ap.add_argument("--serving-slice", type=int, default=0,
+                    help="server time slice in iterations (0: no slicing)")
     ap.add_argument("--serving-only", action="store_true",
                     help="run only the serving measurement and print its JSON object")
     ap.add_argument("--plain-sample", type=int, default=48)
@@ -552,7 +560,8 @@ def main():
         torch.cuda.init()
         print(json.dumps({"serving": serving_run(R, I, 0, args.serving_family, args.serving_rate,
                                                  args.serving_seconds, args.serving_iterations,
-                                                 drain_s=args.serving_drain)}), flush=True)
+                                                 drain_s=args.serving_drain,
+                                                 slice_iterations=args.serving_slice)}), flush=True)
         return 0
     return run_reference(args) if args.impl == "reference" else run_ours(args)
 

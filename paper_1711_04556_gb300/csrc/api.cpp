@@ -458,15 +458,17 @@ int rcpsp_load_instances(rcpsp_ctx *c, const rcpsp_instance *inst, int32_t count
     if (!b.ptr) return set_err(c, RCPSP_E_CUDA, "device allocation failed");
     cudaError_t e = cudaSuccess;
     if (c->load_host_cap < rec_words * 4) {
+        // grows geometrically: pinning memory is slow, and batch sizes vary
+        const size_t cap = std::max(rec_words * 4, 2 * c->load_host_cap);
         if (c->load_host) cudaFreeHost(c->load_host);
         c->load_host = nullptr;
         c->load_host_cap = 0;
-        e = cudaMallocHost(reinterpret_cast<void **>(&c->load_host), rec_words * 4);
+        e = cudaMallocHost(reinterpret_cast<void **>(&c->load_host), cap);
         if (e != cudaSuccess) {
             dev_free(c, b.ptr, b.bytes, nullptr);
             return cuda_err(c, e, "pinned staging");
         }
-        c->load_host_cap = rec_words * 4;
+        c->load_host_cap = cap;
     }
     int32_t *host = reinterpret_cast<int32_t *>(c->load_host);
     size_t ro = 0;
@@ -672,14 +674,15 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
                            std::memcmp(c->g_items.data(), sorted.data(), ibytes) == 0 && c->g_launch_sig == sig;
     if (!(p->use_graph && same_plan)) {
         if (c->items_cap < ibytes) {
+            const size_t cap = std::max(ibytes, 2 * c->items_cap);   // geometric growth
             cudaStreamSynchronize(st);
             dev_free(c, c->items_dev, c->items_cap, nullptr);
             if (c->items_host) cudaFreeHost(c->items_host);
             c->items_host = nullptr;
-            c->items_dev = static_cast<LaunchItem *>(dev_alloc(c, ibytes, nullptr));
-            c->items_cap = c->items_dev ? ibytes : 0;
+            c->items_dev = static_cast<LaunchItem *>(dev_alloc(c, cap, nullptr));
+            c->items_cap = c->items_dev ? cap : 0;
             if (!c->items_dev) return set_err(c, RCPSP_E_CUDA, "plan allocation failed");
-            e = cudaMallocHost(reinterpret_cast<void **>(&c->items_host), ibytes);
+            e = cudaMallocHost(reinterpret_cast<void **>(&c->items_host), cap);
             if (e != cudaSuccess) return cuda_err(c, e, "pinned staging");
         } else {
             cudaStreamSynchronize(st);   // the staging buffer may still feed a copy
