@@ -270,3 +270,22 @@ def test_kernel_launch_count(solver):
     assert solver.kernel_launches() - k0 == 5          # two classes, twice
     solver.results(ids)
     solver.free(ids)
+
+
+@pytest.mark.parametrize("mode", [R.EVAL_TIME, R.EVAL_CAPACITY])
+def test_prefix_reuse_and_full_decodes_agree(solver, oracle, mode):
+    """Prefix reuse is used when an iteration needs several decode rounds:
+    few groups (G = 8 x 2 warps: 8 groups for ~850 feasible moves) run the
+    kernel variant that starts neighbour decodes from kept states, many
+    groups (G = 1 x 16 warps: 512 groups) the one that decodes from the
+    start.  Both must be the oracle's search."""
+    insts = I.config_batch("j120_batch", 6, first=90)
+    ids = solver.load(insts)
+    ref = oracle.tabu_search_batch(insts, [(12, 60, 800, mode, 1)] * len(insts), NPROC, trace=True)
+    for g, w in ((8, 2), (1, 16)):
+        solver.search(ids, iterations=12, delta=60, tabu_len=800, mode=mode, group_size=g, warps_per_cta=w,
+                      cluster_size=1, trace=True)
+        got = solver.results(ids)
+        for k, (a, b) in enumerate(zip(got, ref)):
+            compare_search(oracle, a, b, solver.trace(ids[k], 12))
+    solver.free(ids)
