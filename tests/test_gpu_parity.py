@@ -277,14 +277,14 @@ def test_prefix_reuse_and_full_decodes_agree(solver, oracle, mode):
     """Prefix reuse is used when an iteration needs several decode rounds:
     few groups (G = 8 x 2 warps: 8 groups for ~850 feasible moves) run the
     kernel variant that starts neighbour decodes from kept states, many
-    groups (G = 1 x 16 warps: 512 groups) the one that decodes from the
-    start.  Both must be the oracle's search."""
+    groups (48 per CTA on clusters of 8 CTAs: 384) the one that decodes
+    from the start.  Both must be the oracle's search."""
     insts = I.config_batch("j120_batch", 6, first=90)
     ids = solver.load(insts)
     ref = oracle.tabu_search_batch(insts, [(12, 60, 800, mode, 1)] * len(insts), NPROC, trace=True)
-    for g, w in ((8, 2), (1, 16)):
+    for g, w, c in ((8, 2, 1), (8, 12, 8)):
         solver.search(ids, iterations=12, delta=60, tabu_len=800, mode=mode, group_size=g, warps_per_cta=w,
-                      cluster_size=1, trace=True)
+                      cluster_size=c, trace=True)
         got = solver.results(ids)
         for k, (a, b) in enumerate(zip(got, ref)):
             compare_search(oracle, a, b, solver.trace(ids[k], 12))
