@@ -162,8 +162,11 @@ int rcpsp_free_instances(rcpsp_ctx *ctx, const int32_t *ids, int32_t count);
  * with its own shape -- lanes per decode, warps per CTA, CTAs per search --
  * the first on `cuda_stream` (a cudaStream_t; NULL = legacy default stream),
  * the others on streams of the context forked from it and joined back into
- * it.  The call is asynchronous.  Results stay on the device until
- * rcpsp_get_schedules. */
+ * it.  A class whose iterations take several decode rounds per CTA keeps
+ * the decoder state of the current list every K positions and starts each
+ * neighbour's decode from the last state before its first swapped position
+ * (prefix reuse; results and counts are those of full decodes).  The call
+ * is asynchronous.  Results stay on the device until rcpsp_get_schedules. */
 int rcpsp_tabu_search(rcpsp_ctx *ctx, const int32_t *ids, int32_t count,
                       const rcpsp_params *params, void *cuda_stream);
 
