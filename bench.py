@@ -313,6 +313,7 @@ def coop_run(solver, R, I, insts, ids, ref_res, kw, st, args):
                     f"Phi_max 3, Phi_steps 20; the same instances as the main step",
             "schedules_per_s": ev / t, "ms_per_step": 1000 * t, "schedules_per_step": ev,
             "mean_best_cmax": cm, "mean_best_cmax_independent": ind,
+            "mean_cp_dev_pct": float(np.mean([100.0 * (r["best_cmax"] - r["cp"]) / r["cp"] for r in res if r["cp"] > 0])),
             "better_instances": int(sum(a["best_cmax"] < b["best_cmax"] for a, b in zip(res, ref_res))),
             "worse_instances": int(sum(a["best_cmax"] > b["best_cmax"] for a, b in zip(res, ref_res)))}
 
@@ -457,6 +458,12 @@ def run_ours(args):
             extra["serving"] = serving_run(R, I, local, args.serving_family, args.serving_rate, args.serving_seconds,
                                            args.serving_iterations, drain_s=args.serving_drain,
                                            slice_iterations=args.serving_slice)
+        # solution quality: deviation of the best makespan from the critical-path
+        # lower bound (the paper's "CP dev." measure), and how many reach it
+        devs = [100.0 * (r["best_cmax"] - r["cp"]) / r["cp"] for r in ref_res if r["cp"] > 0]
+        extra["quality"] = {"mean_cp_dev_pct": float(np.mean(devs)) if devs else None,
+                            "at_critical_path": int(sum(r["best_cmax"] == r["cp"] for r in ref_res)),
+                            "instances": len(ref_res)}
         extra["latency_ms"] = {
             "single_instance_e2e": {"p50": p50, "p99": p99, "reps": args.latency_reps,
                                     "what": "1 instance, 100 iterations, load+search+results through the C API"},
