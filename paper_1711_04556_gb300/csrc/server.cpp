@@ -83,9 +83,17 @@ struct Completion {
     std::vector<int32_t> W, S;
 };
 
+// Device memory of one slot: stream-ordered allocations on the slot's own
+// stream from the server's pool.
+struct SlotMem {
+    cudaStream_t stream = nullptr;
+    cudaMemPool_t pool = nullptr;
+};
+
 struct Slot {
     rcpsp_ctx *ctx = nullptr;
     cudaStream_t stream = nullptr;
+    SlotMem mem;
     bool busy = false;
     std::vector<Request> reqs;
     std::vector<int32_t> ids;
@@ -96,17 +104,21 @@ struct Slot {
 
 bool same_params(const rcpsp_params &a, const rcpsp_params &b) { return std::memcmp(&a, &b, sizeof(a)) == 0; }
 
-// Device memory of a slot: stream-ordered on the slot's own stream, made
-// ready before the synchronous upload that follows it.
+// Device memory of a slot: stream-ordered on the slot's own stream, from a
+// pool that keeps up to the memory budget mapped between batches (no
+// remapping on the request path), made ready before the upload that
+// follows it.
 void *slot_alloc(size_t bytes, void *, void *user) {
-    cudaStream_t st = static_cast<cudaStream_t>(user);
+    const SlotMem *m = static_cast<const SlotMem *>(user);
     void *p = nullptr;
-    if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) return nullptr;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return nullptr;
+    if (cudaMallocFromPoolAsync(&p, bytes, m->pool, m->stream) != cudaSuccess) return nullptr;
+    if (cudaStreamSynchronize(m->stream) != cudaSuccess) return nullptr;
     return p;
 }
 
-void slot_release(void *ptr, size_t, void *, void *user) { cudaFreeAsync(ptr, static_cast<cudaStream_t>(user)); }
+void slot_release(void *ptr, size_t, void *, void *user) {
+    cudaFreeAsync(ptr, static_cast<const SlotMem *>(user)->stream);
+}
 
 }  // namespace
 
@@ -121,6 +133,7 @@ struct rcpsp_server {
     std::deque<Completion> done;
     std::vector<Completion> handed;      // returned by the last poll, owned until the next one
     std::thread worker;
+    cudaMemPool_t pool = nullptr;        // device memory of every slot
     std::atomic<bool> stop{false};
     int64_t inflight_bytes = 0;
     rcpsp_server_stats st{};
@@ -355,6 +368,18 @@ int rcpsp_server_create(rcpsp_server **out, int device, const rcpsp_server_confi
         delete s;
         return RCPSP_E_CUDA;
     }
+    {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        uint64_t keep = static_cast<uint64_t>(s->cfg.memory_budget);
+        if (cudaMemPoolCreate(&s->pool, &props) != cudaSuccess ||
+            cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+            rcpsp_server_destroy(s);
+            return RCPSP_E_CUDA;
+        }
+    }
     s->slots.resize(s->cfg.slots);
     s->allocs.resize(s->cfg.slots);
     for (int k = 0; k < s->cfg.slots; ++k) {
@@ -363,7 +388,9 @@ int rcpsp_server_create(rcpsp_server **out, int device, const rcpsp_server_confi
             rcpsp_server_destroy(s);
             return RCPSP_E_CUDA;
         }
-        s->allocs[k] = rcpsp_allocator{slot_alloc, slot_release, sl.stream};
+        sl.mem.stream = sl.stream;
+        sl.mem.pool = s->pool;
+        s->allocs[k] = rcpsp_allocator{slot_alloc, slot_release, &sl.mem};
         const int rc = rcpsp_create(&sl.ctx, device, &s->allocs[k]);
         if (rc != RCPSP_OK) {
             rcpsp_server_destroy(s);
@@ -384,6 +411,7 @@ int rcpsp_server_destroy(rcpsp_server *s) {
         if (sl.ctx) rcpsp_destroy(sl.ctx);
         if (sl.stream) cudaStreamDestroy(sl.stream);
     }
+    if (s->pool) cudaMemPoolDestroy(s->pool);
     delete s;
     return RCPSP_OK;
 }
