@@ -220,8 +220,10 @@ def run_reference(args):
 
 
 def serving_run(R, I, device, family, rate, seconds, iterations, pool_size=512, seed=5, drain_s=30.0,
-                slice_iterations=0):
-    """Poisson arrivals at `rate` req/s for `seconds` into the continuous-batching server.
+                slice_iterations=0, warm_s=1.0):
+    """Poisson arrivals at `rate` req/s for `warm_s` + `seconds` into the
+    continuous-batching server; the first `warm_s` seconds bring the server
+    and the GPU to their steady state and are not measured.
 
     Requests cycle through a pool of distinct instances of `family`; each is
     one search of `iterations` iterations.  Latency = host time from submit
@@ -230,9 +232,10 @@ def serving_run(R, I, device, family, rate, seconds, iterations, pool_size=512, 
     """
     pool = I.config_batch(family, pool_size)
     rng = np.random.default_rng(seed)
-    gaps = rng.exponential(1.0 / rate, int(rate * seconds * 1.5) + 16)
+    total = warm_s + seconds
+    gaps = rng.exponential(1.0 / rate, int(rate * total * 1.5) + 16)
     arrivals = np.cumsum(gaps)
-    arrivals = arrivals[arrivals < seconds]
+    arrivals = arrivals[arrivals < total]
     done = []
     with R.Server(device, slots=8, max_batch=256, memory_budget=2 << 30, slice_iterations=slice_iterations) as srv:
         # warm-up: batches on the slots (kernels loaded, staging allocated)
@@ -254,23 +257,25 @@ def serving_run(R, I, device, family, rate, seconds, iterations, pool_size=512, 
                 srv.submit(pool[k % pool_size], tag=k, iterations=iterations)
                 k += 1
             done += srv.poll(wait_ms=0)
-            if k == len(arrivals) and (len(done) == k or now > seconds + drain_s):
+            if k == len(arrivals) and (len(done) == k or now > total + drain_s):
                 break
             nxt = arrivals[k] - now if k < len(arrivals) else 0.002
             time.sleep(min(max(nxt, 0.0), 0.002))
-        wall = time.perf_counter() - t0
+        wall = time.perf_counter() - t0 - warm_s
         st = srv.stats()
-    lat = [(c["t_done_ns"] - c["t_submit_ns"]) / 1e6 for c in done if c["status"] == 0]
-    ev = sum(c["evaluated"] for c in done)
+    measured = [c for c in done if c["tag"] >= 0 and arrivals[c["tag"]] >= warm_s]
+    n_meas = int(np.count_nonzero(arrivals >= warm_s))
+    lat = [(c["t_done_ns"] - c["t_submit_ns"]) / 1e6 for c in measured if c["status"] == 0]
+    ev = sum(c["evaluated"] for c in measured)
     st = {k: st[k] - st0[k] if k in ("batches",) else st[k] for k in st}
     p50, p99 = percentiles(lat) if lat else (None, None)
     p90 = float(np.percentile(lat, 90)) if lat else None
     lmax = float(max(lat)) if lat else None
     return {"workload": f"{family} requests, {iterations} iterations each, Poisson {rate:g} req/s for {seconds:g} s "
-                        f"(after a warm-up of 64 requests)"
+                        f"measured after {warm_s:g} s of the same stream (and 64 warm-up requests)"
                         + (f", time-sliced every {slice_iterations} iterations" if slice_iterations else ""),
             "requeued": st.get("requeued", 0),
-            "offered_req_s": len(arrivals) / seconds, "completed": len(lat), "submitted": int(len(arrivals)),
+            "offered_req_s": n_meas / seconds, "completed": len(lat), "submitted": n_meas,
             "completed_req_s": len(lat) / wall, "schedules_per_s": ev / wall, "wall_s": wall,
             "latency_ms": {"p50": p50, "p90": p90, "p99": p99, "max": lmax}, "batches": st["batches"],
             "max_inflight_bytes": st["max_inflight_bytes"]}
