@@ -92,7 +92,9 @@ struct rcpsp_ctx {
     // from and joined back to the caller's stream
     cudaStream_t aux[kAuxStreams] = {};
     cudaEvent_t fork = nullptr, join[kAuxStreams] = {};
-    std::vector<int> g_launch_sig;
+    std::vector<long long> g_launch_sig;
+    int32_t *snap_dev = nullptr;        // kept prefix states of the CTAs (prefix reuse)
+    size_t snap_cap = 0;
     // co-operative searches: plan, initial lists, random words and working sets
     // instance upload: pinned staging and a stream of its own, so that a
     // load overlaps a search that is still running on the caller's stream
@@ -175,18 +177,27 @@ int launch_move_cap(const std::vector<LaunchItem> &items) {
     return std::min(rcpsp::kDefaultMoveCap, (m + 31) & ~31);
 }
 
-// Positions between the kept prefix states of an N-activity search: at most
-// 16 states (16 / kmul), at least 8 * kmul positions apart.
-int prefix_k_for(int n, int kmul) { return kmul * std::max(8, (n + 15) / 16); }
+// Positions between the kept prefix states of an N-activity search: every 8
+// positions, at most 32 states.
+int prefix_k_for(int n) { return std::max(8, (n + 31) / 32); }
 
-// Shared memory of a class at this shape; kmul > 0 adds the kept prefix states.
-size_t smem_bytes(const std::vector<LaunchItem> &items, int ngroups, int move_cap, int kmul = 0) {
+// Words of kept prefix states one CTA needs for a class (global scratch).
+int prefix_words_max(const std::vector<LaunchItem> &items) {
     int words = 0;
     for (const LaunchItem &it : items) {
         const int pw = rcpsp::profile_words(it.mode, it.h.wps, it.h.ub, it.h.sum_cap);
-        const int snap = kmul > 0 ? rcpsp::prefix_words(it.h.n, pw, prefix_k_for(it.h.n, kmul)) : 0;
+        words = std::max(words, rcpsp::prefix_words(it.h.n, pw, prefix_k_for(it.h.n)));
+    }
+    return rcpsp::align4(words);
+}
+
+// Shared memory of a class at this shape.
+size_t smem_bytes(const std::vector<LaunchItem> &items, int ngroups, int move_cap) {
+    int words = 0;
+    for (const LaunchItem &it : items) {
+        const int pw = rcpsp::profile_words(it.mode, it.h.wps, it.h.ub, it.h.sum_cap);
         const rcpsp::StateLayout S =
-            rcpsp::state_layout(it.h.inst_words, it.h.n, it.tabu_len, it.delta, move_cap, pw, ngroups, snap);
+            rcpsp::state_layout(it.h.inst_words, it.h.n, it.tabu_len, it.delta, move_cap, pw, ngroups);
         words = std::max(words, S.total);
     }
     return static_cast<size_t>(words) * 4;
@@ -217,7 +228,9 @@ int footprint_class(const LaunchItem &it) {
 
 struct ClassLaunch {
     int offset = 0, count = 0, G = 0, threads = 0, blocks = 0, move_cap = 0, csize = 1;
-    bool prefix = false;         // prefix reuse (kernel variant, kept states in shared memory)
+    bool prefix = false;         // prefix reuse (kernel variant, kept states in global scratch)
+    int snap_words = 0;          // kept-state words per CTA
+    size_t snap_off = 0;         // its first word in the context's scratch
     size_t smem = 0;
 };
 
@@ -376,6 +389,7 @@ int rcpsp_destroy(rcpsp_ctx *c) {
     dev_free(c, c->items_dev, c->items_cap, nullptr);
     dev_free(c, c->queue_dev, 64, nullptr);
     dev_free(c, c->coop_dev, c->coop_cap, nullptr);
+    dev_free(c, c->snap_dev, c->snap_cap, nullptr);
     if (c->items_host) cudaFreeHost(c->items_host);
     if (c->coop_host) cudaFreeHost(c->coop_host);
     if (c->load_host) cudaFreeHost(c->load_host);
@@ -640,15 +654,11 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
         }
         if (smem > smem_limit)
             return set_err(c, RCPSP_E_TOO_LARGE, "instance state does not fit in shared memory at this launch shape");
-        if (prefix_pays(part, warps * (32 / G), L.csize))
-            for (int kmul = 1; kmul <= 4 && !L.prefix; kmul *= 2) {   // fewer states when short of room
-                const size_t with = smem_bytes(part, warps * (32 / G), L.move_cap, kmul);
-                if (with > smem_limit) continue;
-                L.prefix = true;
-                smem = with;
-                for (int k = L.offset; k < L.offset + L.count; ++k)
-                    sorted[k].prefix_k = prefix_k_for(sorted[k].h.n, kmul);
-            }
+        if (prefix_pays(part, warps * (32 / G), L.csize)) {
+            L.prefix = true;
+            L.snap_words = prefix_words_max(part);
+            for (int k = L.offset; k < L.offset + L.count; ++k) sorted[k].prefix_k = prefix_k_for(sorted[k].h.n);
+        }
         L.G = G;
         L.threads = warps * 32;
         L.smem = smem;
@@ -663,10 +673,26 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
                                 : L.csize * std::max(1, std::min(L.count, units));
         launches.push_back(L);
     }
-    std::vector<int> sig;
+    // kept prefix states: one region per CTA of every class that uses them
+    {
+        size_t need = 0;
+        for (ClassLaunch &L : launches)
+            if (L.prefix) {
+                L.snap_off = need;
+                need += static_cast<size_t>(L.blocks) * L.snap_words;
+            }
+        if (need * 4 > c->snap_cap) {
+            dev_free(c, c->snap_dev, c->snap_cap, nullptr);
+            c->snap_dev = static_cast<int32_t *>(dev_alloc(c, need * 4, nullptr));
+            c->snap_cap = c->snap_dev ? need * 4 : 0;
+            if (!c->snap_dev) return set_err(c, RCPSP_E_CUDA, "prefix scratch allocation failed");
+        }
+    }
+    std::vector<long long> sig;
     for (const ClassLaunch &L : launches)
-        sig.insert(sig.end(), {L.offset, L.count, L.G, L.threads, L.blocks, L.move_cap, static_cast<int>(L.smem),
-                               L.csize, L.prefix ? 1 : 0});
+        sig.insert(sig.end(), {L.offset, L.count, L.G, L.threads, L.blocks, L.move_cap, static_cast<long long>(L.smem),
+                               L.csize, L.prefix ? 1 : 0, L.snap_words, static_cast<long long>(L.snap_off)});
+    sig.push_back(reinterpret_cast<long long>(c->snap_dev));
     // device copy of the plan
     cudaError_t e = cudaSuccess;
     const size_t ibytes = sizeof(LaunchItem) * count;
@@ -708,7 +734,8 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
             cudaStream_t sq = q == 0 ? s0 : c->aux[q - 1];
             if (q > 0 && (r = cudaStreamWaitEvent(sq, c->fork, 0)) != cudaSuccess) return r;
             r = rcpsp::launch_search(L.G, c->items_dev + L.offset, L.count, c->queue_dev + q, L.move_cap, L.blocks,
-                                     L.threads, L.smem, sq, L.csize, L.prefix);
+                                     L.threads, L.smem, sq, L.csize, L.prefix,
+                                     L.prefix ? c->snap_dev + L.snap_off : nullptr, L.snap_words);
             if (r != cudaSuccess) return r;
             if (q > 0 && (r = cudaEventRecord(c->join[q - 1], sq)) != cudaSuccess) return r;
         }

@@ -132,7 +132,8 @@ __device__ __forceinline__ void clear_es(int *es, int n, int NG, bool active, co
     __syncwarp();
 }
 
-// Kept decoder states of the current list (prefix reuse, see prefix_count):
+// Kept decoder states of the current list (prefix reuse, see prefix_count),
+// in the CTA's own global scratch (L2-resident, read and written past L1):
 // snapshot j (1..count) is the state before position j*K, at base +
 // (j-1)*stride: [0] frontier F, [1] makespan so far, [2] work so far, then
 // the profile (time-indexed: WPS planes of UB words; capacity-indexed: the
@@ -173,13 +174,13 @@ __device__ int decode_time(const SInst &I, const int *W, int u, int v, bool acti
         // start from the kept state of the current list before position p0
         const int *sn = px.base + (p0 / px.K - 1) * px.stride;
         if (active) {
-            F = sn[0];
-            cmax = sn[1];
-            work += sn[2];
+            F = __ldcg(sn);
+            cmax = __ldcg(sn + 1);
+            work += __ldcg(sn + 2);
 #pragma unroll
             for (int w = 0; w < WPS; ++w)
-                for (int t = g.lane; t < F; t += G) prof[(w * ubs + t) * NG] = sn[4 + w * ubs + t];
-            for (int x = g.lane; x < n; x += G) esa[x * NG] = sn[4 + WPS * ubs + x];
+                for (int t = g.lane; t < F; t += G) prof[(w * ubs + t) * NG] = __ldcg(sn + 4 + w * ubs + t);
+            for (int x = g.lane; x < n; x += G) esa[x * NG] = __ldcg(sn + 4 + WPS * ubs + x);
         }
         __syncwarp();
     } else {
@@ -195,12 +196,13 @@ __device__ int decode_time(const SInst &I, const int *W, int u, int v, bool acti
             if (active) {
 #pragma unroll
                 for (int w = 0; w < WPS; ++w)
-                    for (int t = g.lane; t < F; t += G) sn[4 + w * ubs + t] = prof[(w * ubs + t) * NG];
-                for (int x = g.lane; x < n; x += G) sn[4 + WPS * ubs + x] = esa[x * NG];
+                    for (int t = g.lane; t < F; t += G)
+                        __stcg(sn + 4 + w * ubs + t, static_cast<int>(prof[(w * ubs + t) * NG]));
+                for (int x = g.lane; x < n; x += G) __stcg(sn + 4 + WPS * ubs + x, esa[x * NG]);
                 if (g.lane == 0) {
-                    sn[0] = F;
-                    sn[1] = cmax;
-                    sn[2] = work;
+                    __stcg(sn, F);
+                    __stcg(sn + 1, cmax);
+                    __stcg(sn + 2, work);
                 }
             }
             __syncwarp();
@@ -319,10 +321,10 @@ __device__ int decode_capacity(const SInst &I, const int *W, int u, int v, bool 
         // start from the kept state of the current list before position p0
         const int *sn = px.base + (p0 / px.K - 1) * px.stride;
         if (active) {
-            cmax = sn[1];
-            if (g.lane == 0) wk = sn[2];
-            for (int j = g.lane; j < sc; j += G) cst[j * NG] = sn[4 + j];
-            for (int x = g.lane; x < n; x += G) esa[x * NG] = sn[4 + sc + x];
+            cmax = __ldcg(sn + 1);
+            if (g.lane == 0) wk = __ldcg(sn + 2);
+            for (int j = g.lane; j < sc; j += G) cst[j * NG] = __ldcg(sn + 4 + j);
+            for (int x = g.lane; x < n; x += G) esa[x * NG] = __ldcg(sn + 4 + sc + x);
         }
         __syncwarp();
     } else {
@@ -339,12 +341,12 @@ __device__ int decode_capacity(const SInst &I, const int *W, int u, int v, bool 
             int *sn = px.base + (p / px.K - 1) * px.stride;
             const int wsum = g.sum(wk);
             if (active) {
-                for (int j = g.lane; j < sc; j += G) sn[4 + j] = cst[j * NG];
-                for (int x = g.lane; x < n; x += G) sn[4 + sc + x] = esa[x * NG];
+                for (int j = g.lane; j < sc; j += G) __stcg(sn + 4 + j, cst[j * NG]);
+                for (int x = g.lane; x < n; x += G) __stcg(sn + 4 + sc + x, esa[x * NG]);
                 if (g.lane == 0) {
-                    sn[0] = 0;
-                    sn[1] = cmax;
-                    sn[2] = wsum;
+                    __stcg(sn, 0);
+                    __stcg(sn + 1, cmax);
+                    __stcg(sn + 2, wsum);
                 }
             }
             __syncwarp();

@@ -119,7 +119,6 @@ struct StateLayout {
     int groups;          // first word of the per-warp group areas
     int prof_words;      // profile words of one group (time- or capacity-indexed)
     int group_words;     // profile + finish times of one group
-    int snaps;           // first word of the kept prefix states (prefix reuse)
     int total;           // words of dynamic shared memory
 };
 
@@ -131,13 +130,14 @@ RC_HD int profile_words(int mode, int wps, int ub, int sum_cap) {
 // a neighbour's decode may start from the decoder state of the current list
 // before position floor(u/K)*K.  These states -- frontier, makespan so far,
 // work so far, the profile (or capacity state) and the earliest starts --
-// are kept before positions K, 2K, ..., count*K < N.
+// are kept before positions K, 2K, ..., count*K < N, in a global scratch
+// region of each CTA.
 RC_HD int prefix_count(int n, int K) { return K > 0 ? (n - 1) / K : 0; }
 RC_HD int prefix_stride(int n, int prof_words) { return align4(4 + prof_words + n); }
 RC_HD int prefix_words(int n, int prof_words, int K) { return prefix_count(n, K) * prefix_stride(n, prof_words); }
 
 RC_HD StateLayout state_layout(int inst_words, int n, int tabu_len, int delta, int move_cap,
-                               int prof_words, int ngroups, int snap_words = 0) {
+                               int prof_words, int ngroups) {
     StateLayout S;
     int o = inst_words;
     S.W = o;     o += align4(n);
@@ -152,8 +152,6 @@ RC_HD StateLayout state_layout(int inst_words, int n, int tabu_len, int delta, i
     S.prof_words = prof_words;
     S.group_words = prof_words + n;
     o += ngroups * S.group_words;
-    S.snaps = o;
-    o += snap_words;
     S.total = o;
     return S;
 }

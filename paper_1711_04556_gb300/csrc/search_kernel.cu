@@ -43,7 +43,8 @@ namespace {
 // ---------------------------------------------------------------------------
 template <int G, bool PFX>
 __global__ void __launch_bounds__(512, 2) search_kernel(const LaunchItem *__restrict__ items, int count,
-                                                      int *__restrict__ queue, int move_cap, int csize) {
+                                                      int *__restrict__ queue, int move_cap, int csize,
+                                                      int *__restrict__ gsnap, int gsnap_words) {
     extern __shared__ __align__(16) int sm[];
     __shared__ int s_item, s_nmoves, s_C, s_Cbest, s_widx, s_it, s_improved, s_err, s_it0, s_it_end;
     __shared__ unsigned long long s_bestp[2], s_t0;      // best key of the iteration, by parity
@@ -74,10 +75,9 @@ __global__ void __launch_bounds__(512, 2) search_kernel(const LaunchItem *__rest
         const int n = h.n, mode = it.mode, delta = it.delta, tl = it.tabu_len;
         const int pw = profile_words(mode, h.wps, h.ub, h.sum_cap);
         const int pk = PFX ? it.prefix_k : 0;
-        const StateLayout S = state_layout(h.inst_words, n, tl, delta, move_cap, pw, ngroups,
-                                           prefix_words(n, pw, pk));
-        const Prefix px{pk > 0 ? sm + S.snaps : nullptr, pk > 0 ? pk : 1, prefix_count(n, pk),
-                        prefix_stride(n, pw)};
+        const StateLayout S = state_layout(h.inst_words, n, tl, delta, move_cap, pw, ngroups);
+        const Prefix px{pk > 0 ? gsnap + static_cast<long long>(blockIdx.x) * gsnap_words : nullptr,
+                        pk > 0 ? pk : 1, prefix_count(n, pk), prefix_stride(n, pw)};
         stage_instance(sm, it.record, h.inst_words);
         const SInst I = bind_instance(sm, h);
         int *W = sm + S.W;
@@ -366,9 +366,9 @@ cudaError_t occupancy_g(int threads, size_t smem, int csize, int *units) {
 
 template <int G, bool PFX>
 cudaError_t launch_search_g(const LaunchItem *items, int count, int *queue, int move_cap, int blocks,
-                            int threads, size_t smem, cudaStream_t st, int csize) {
+                            int threads, size_t smem, cudaStream_t st, int csize, int *gsnap, int gsnap_words) {
     if (csize <= 1) {
-        search_kernel<G, PFX><<<blocks, threads, smem, st>>>(items, count, queue, move_cap, 1);
+        search_kernel<G, PFX><<<blocks, threads, smem, st>>>(items, count, queue, move_cap, 1, gsnap, gsnap_words);
         return cudaGetLastError();
     }
     cudaLaunchConfig_t cfg = {};
@@ -383,7 +383,8 @@ cudaError_t launch_search_g(const LaunchItem *items, int count, int *queue, int 
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, search_kernel<G, PFX>, items, count, queue, move_cap, csize);
+    return cudaLaunchKernelEx(&cfg, search_kernel<G, PFX>, items, count, queue, move_cap, csize, gsnap,
+                              gsnap_words);
 }
 
 template <int G>
@@ -420,12 +421,14 @@ cudaError_t search_occupancy(int group_size, int threads, size_t smem, int csize
 }
 
 cudaError_t launch_search(int group_size, const LaunchItem *items, int count, int *queue, int move_cap,
-                          int blocks, int threads, size_t smem, cudaStream_t st, int csize, bool prefix) {
+                          int blocks, int threads, size_t smem, cudaStream_t st, int csize, bool prefix,
+                          int *gsnap, int gsnap_words) {
     if (prefix)
         RCPSP_DISPATCH_G(group_size, return (launch_search_g<GG, true>(items, count, queue, move_cap, blocks,
-                                                                       threads, smem, st, csize)))
+                                                                       threads, smem, st, csize, gsnap,
+                                                                       gsnap_words)))
     RCPSP_DISPATCH_G(group_size, return (launch_search_g<GG, false>(items, count, queue, move_cap, blocks,
-                                                                    threads, smem, st, csize)))
+                                                                    threads, smem, st, csize, nullptr, 0)))
 }
 
 cudaError_t launch_evaluate(int group_size, const LaunchItem &item, const int32_t *lists, int count,
