@@ -24,11 +24,11 @@
  *   R1  Algs. 5 and 6 print the resource loop bound as k < M-1; read k < M,
  *       as in Alg. 4 (only k < M reproduces C_max = 22 of Table 1).
  *   R2  Inside a level the order is ascending (key, label); key = 0 unless
- *       the caller passes shuffle keys (Sec. 4.1 "shuffling").
+ *       the caller passes shuffle keys (the shuffling of Sec. 4.1).
  *   R3  The best move is the admissible move with the lexicographically
  *       smallest (C_max, u, v); the enumeration is u-major, v ascending.
- *   R4  Aspiration ("leads to the global best solution", Sec. 6): strictly
- *       C_uv < C*_max.
+ *   R4  Aspiration (Sec. 6: a tabu move is admitted when it gives a new best
+ *       makespan): strictly C_uv < C*_max.
  *   R5  No admissible move: W is kept and the empty move (0,0) is added to
  *       the tabu list, so that tabu entries still age.
  *   R6  The stop test (C*_max equal to the critical path) runs before each
@@ -453,8 +453,9 @@ int orc_tabu_search_batch(const orc_instance *in, int count, const orc_params *p
 /* ------------- forward-backward improvement (FBI, Sec. 6) ---------------- */
 /*
  * The paper improves every second initial solution by the forward-backward
- * improvement of Li and Willis, "shaking" the schedule right and left while
- * it gets shorter.  Restated here as the usual justification passes of the
+ * improvement of Li and Willis, which moves the activities of a schedule to
+ * the right and back to the left while the makespan falls.  Restated here as
+ * the usual justification passes of the
  * serial SGS, with the readings:
  *   F1  Backward pass: the activities ordered by non-increasing finish time
  *       of the forward schedule (ties: later list position first) are
@@ -572,7 +573,7 @@ out:
  *       floor(w * n_f / 2^32)-th of the n_f feasible swaps (u-major order,
  *       v - u <= delta); the new makespan is decoded and not counted.
  *   C6  Eq. 8's quantity factor, printed as (1/5) I_block / I_total, is read
- *       as I_block / 5 ("at least five reads per block"):
+ *       as I_block / 5 (every block reads at least five solutions):
  *       I_assigned = floor(I_block/5 * (0.8 e^{-100 (C^k/C* - 1)} +
  *       0.2 e^{-4 IC^k / I_block})).  e^{-x} is computed as
  *       (sum_{i=0..24} (-x/1024)^i / i!)^(2^10), Horner form, IEEE double
