@@ -289,3 +289,24 @@ def test_prefix_reuse_and_full_decodes_agree(solver, oracle, mode):
         for k, (a, b) in enumerate(zip(got, ref)):
             compare_search(oracle, a, b, solver.trace(ids[k], 12))
     solver.free(ids)
+
+
+def test_largest_sizes_and_zero_durations(solver, oracle):
+    """N = 302 with 8 resources and durations up to 50 (the longest horizon),
+    the largest tabu list, non-dummy activities of zero duration, and an
+    empty call."""
+    big = I.generate(17, 300, 8, 180, 50, dmin=1, dmax=50, stream=41)
+    zero_dur = I.config_batch("j30_batch", 1, first=77)[0]
+    d = zero_dur.dur.copy()
+    d[1:-1:4] = 0
+    zero = I.Instance(zero_dur.n, zero_dur.m, d, zero_dur.cap, zero_dur.req, zero_dur.succ_off, zero_dur.succ)
+    for inst, it, dl, tl in ((big, 2, 60, 8192),             # 8192 = RCPSP_MAX_TABU
+                             (zero, 40, 20, 60)):
+        for mode in (R.EVAL_TIME, R.EVAL_CAPACITY):
+            ids = solver.load([inst])
+            solver.search(ids, iterations=it, delta=dl, tabu_len=tl, mode=mode, trace=True)
+            ref = oracle.tabu_search(inst, it, dl, tl, mode, 1, trace=True)
+            compare_search(oracle, solver.results(ids)[0], ref, solver.trace(ids[0], it))
+            solver.free(ids)
+    solver.search([], iterations=5)
+    assert solver.results([]) == []
