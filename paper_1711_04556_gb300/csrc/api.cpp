@@ -166,7 +166,7 @@ void default_shape(const std::vector<LaunchItem> &items, int *G, int *warps) {
     *G = g;
     const int groups_wanted = static_cast<int>(feas) + 1;
     int w = (groups_wanted * g + 31) / 32;
-    *warps = std::max(1, std::min(16, w));
+    *warps = std::max(1, std::min(rcpsp::kSearchMaxWarps, w));
 }
 
 // Potential moves one stripe examines: the largest (N-3)*delta of the batch,
@@ -555,8 +555,9 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
     if (!c) return RCPSP_E_INVALID_ARG;
     if (!p || count < 0 || (count > 0 && !ids)) return set_err(c, RCPSP_E_INVALID_ARG, "bad arguments");
     if (p->iterations < 0 || p->max_swap_dist < 0 || p->tabu_len < 0 || p->tabu_len > RCPSP_MAX_TABU ||
-        p->eval_mode < 0 || p->eval_mode > 2 || p->warps_per_cta < 0 || p->warps_per_cta > 16 ||
-        p->checkpoint < 0 || p->checkpoint > 1 || p->resume < 0 || p->resume > 1)
+        p->eval_mode < 0 || p->eval_mode > 2 || p->warps_per_cta < 0 ||
+        p->warps_per_cta > rcpsp::kSearchMaxWarps || p->checkpoint < 0 || p->checkpoint > 1 || p->resume < 0 ||
+        p->resume > 1)
         return set_err(c, RCPSP_E_INVALID_ARG, "bad search parameters");
     const int gs = p->group_size;
     if (gs != 0 && gs != 1 && gs != 2 && gs != 4 && gs != 8 && gs != 16 && gs != 32)
@@ -990,7 +991,7 @@ int rcpsp_tabu_search_noalloc(rcpsp_ctx *c, const int32_t *ids, int32_t count, c
     if (!c) return RCPSP_E_INVALID_ARG;
     if (!p || count < 0 || (count > 0 && !ids)) return set_err(c, RCPSP_E_INVALID_ARG, "bad arguments");
     if (p->iterations < 0 || p->max_swap_dist < 0 || p->tabu_len < 0 || p->tabu_len > RCPSP_MAX_TABU ||
-        p->eval_mode < 0 || p->eval_mode > 2 || p->warps_per_cta < 0 || p->warps_per_cta > 16)
+        p->eval_mode < 0 || p->eval_mode > 2 || p->warps_per_cta < 0 || p->warps_per_cta > rcpsp::kSearchMaxWarps)
         return set_err(c, RCPSP_E_INVALID_ARG, "bad search parameters");
     const int gs = p->group_size;
     if (gs != 0 && gs != 1 && gs != 2 && gs != 4 && gs != 8 && gs != 16 && gs != 32)
@@ -1126,7 +1127,7 @@ int rcpsp_autotune(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcpsp_
         double best_rate = -1.0;
         int bG = 0, bW = 0, bC = 1;
         const int gsz[] = {1, 2, 4, 8, 16, 32};
-        const int wcnt[] = {1, 2, 3, 4, 6, 8, 12, 16};
+        const int wcnt[] = {1, 2, 3, 4, 6, 8, 10, 12, 16};
         // clusters pay when the class has fewer searches than the GPU has SMs,
         // or when its searches are large (N > 160: long decode chains and big
         // neighbourhoods, which would otherwise leave the GPU to a few

@@ -19,6 +19,8 @@
 namespace rcpsp {
 
 constexpr int kDefaultMoveCap = 2048;   // potential moves examined per stripe
+constexpr int kSearchMaxWarps = 16;     // largest search CTA (512 threads)
+constexpr int kSearchNarrowThreads = 384;   // CTAs up to this size run the 384-thread build of the kernel
 
 // Per-instance header (64 bytes).
 struct InstHeader {

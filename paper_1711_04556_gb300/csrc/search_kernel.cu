@@ -1,293 +1,13 @@
-// sm_103a kernels of the tabu search for the RCPSP (Bukata, Sucha, Hanzalek).
-//
-// One persistent CTA runs one search at a time and pops the next instance
-// from a device work queue when it is done (Sec. 6: one block = one tabu
-// search; the homogeneous model: instance and state stay on the device for
-// the whole run).  Inside a CTA the neighbourhood is split over "groups" of
-// G lanes (G = 1, 2, ..., 32, chosen at launch); a group decodes one
-// neighbour at a time with the serial SGS of Alg. 7, its lanes cooperating
-// on the resource scan and update.  Each group owns a private resource
-// profile in shared memory, interleaved with the other groups of its warp so
-// that the G lanes of every group always hit G distinct banks and the groups
-// of a warp hit disjoint bank sets.
-//
-// Per iteration (Sec. 6):
-//   1. first-successor / last-predecessor positions of the current list;
-//      swap(u,v) satisfies Eqs. 5-6 iff v < firstSucc(u) and
-//      u > lastPred(v) -- the same predicate, evaluated in O(1);
-//   2. feasible moves of the reduced neighbourhood (v - u <= delta) are
-//      ballot-compacted into shared memory (Alg. 1's filter, one pass);
-//   3. the groups decode the neighbours (time-indexed: Algs. 5-6 on a
-//      SWAR-packed profile; capacity-indexed: Eq. 7 and Alg. 4 in a
-//      per-index closed form) and form the key (C_max, u, v) of every
-//      admissible move (not tabu, or strictly better than C*_max);
-//   4. warp-shuffle min, then a shared-memory atomicMin, give the move;
-//   5. one thread applies it and updates the simple tabu list (Alg. 3).
-//
-// The kernel never spins: the work queue is a single atomicAdd.  Internal
-// inconsistencies set an error word that the host reads as a status.
-#include "device_search.cuh"
+// sm_103a kernels of the tabu search for the RCPSP (Bukata, Sucha, Hanzalek):
+// the search kernel for CTAs of up to 384 threads (two CTAs of 384 threads
+// per SM leave each thread 85 registers, so the decode loop runs without
+// spills at 80), the dispatch by CTA size, and the decoding of caller-given
+// lists.  The kernel itself is in search_kernel.cuh.
 #include "kernels.h"
+#include "search_kernel.cuh"
 
 namespace rcpsp {
 namespace {
-
-// ---------------------------------------------------------------------------
-// Persistent search kernel.  With csize > 1 it runs as clusters of csize
-// CTAs, one search per cluster: every CTA holds the same search state,
-// examines its share of the potential moves (chunks of 32 slots, round
-// robin over the cluster ranks), finds its best admissible key, and after a
-// cluster barrier reads the other CTAs' keys through distributed shared
-// memory; all CTAs then apply the same move.  Rank 0 pops the work queue,
-// sums the counters and writes the results.
-// ---------------------------------------------------------------------------
-template <int G, bool PFX>
-__global__ void __launch_bounds__(512, 2) search_kernel(const LaunchItem *__restrict__ items, int count,
-                                                      int *__restrict__ queue, int move_cap, int csize,
-                                                      int *__restrict__ gsnap, int gsnap_words) {
-    extern __shared__ __align__(16) int sm[];
-    __shared__ int s_item, s_nmoves, s_C, s_Cbest, s_widx, s_it, s_improved, s_err, s_it0, s_it_end;
-    __shared__ unsigned long long s_bestp[2], s_t0;      // best key of the iteration, by parity
-    __shared__ long long s_eval, s_work;
-    const unsigned crank = csize > 1 ? cg::this_cluster().block_rank() : 0u;
-
-    constexpr int NG = 32 / G;
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    const int warp = tid >> 5, wl = tid & 31;
-    const int ngroups = (nthr >> 5) * NG;
-    const int gw = wl / G;                     // group inside the warp
-    const Group<G> g;
-
-    for (;;) {
-        if (tid == 0 && crank == 0) s_item = atomicAdd(queue, 1);
-        int item;
-        if (csize > 1) {
-            cg::this_cluster().sync();
-            item = *cg::this_cluster().map_shared_rank(&s_item, 0);
-            cg::this_cluster().sync();                      // read before rank 0 pops again
-        } else {
-            __syncthreads();
-            item = s_item;
-        }
-        if (item >= count) break;
-        const LaunchItem &it = items[item];
-        const InstHeader &h = it.h;
-        const int n = h.n, mode = it.mode, delta = it.delta, tl = it.tabu_len;
-        const int pw = profile_words(mode, h.wps, h.ub, h.sum_cap);
-        const int pk = PFX ? it.prefix_k : 0;
-        const StateLayout S = state_layout(h.inst_words, n, tl, delta, move_cap, pw, ngroups);
-        const Prefix px{pk > 0 ? gsnap + static_cast<long long>(blockIdx.x) * gsnap_words : nullptr,
-                        pk > 0 ? pk : 1, prefix_count(n, pk), prefix_stride(n, pw)};
-        stage_instance(sm, it.record, h.inst_words);
-        const SInst I = bind_instance(sm, h);
-        int *W = sm + S.W;
-        int *pos = sm + S.pos;
-        int *Wbest = sm + S.Wbest;
-        int *fsp = sm + S.fsp;
-        int *lpp = sm + S.lpp;
-        int *stl = sm + S.stl;
-        unsigned *tc = reinterpret_cast<unsigned *>(sm + S.tc);
-        int *moves = sm + S.moves;
-        int *area = sm + S.groups + warp * NG * S.group_words + wl / G;
-        const int tcw = (n * delta + 31) / 32;
-        int err = 0;
-        if (it.state && (it.ckpt & kCkptResume)) {
-            // continue a saved search: lists, tabu state, iteration and
-            // makespans as they were; the counters so far ride on rank 0
-            const CkptLayout CL = ckpt_layout(n, tl, delta);
-            const int32_t *sv = it.state;
-            for (int p = tid; p < n; p += nthr) {
-                const int a = sv[CL.W + p];
-                W[p] = a;
-                pos[a] = p;
-                Wbest[p] = sv[CL.Wbest + p];
-            }
-            for (int x = tid; x < tl; x += nthr) stl[x] = sv[CL.stl + x];
-            for (int x = tid; x < tcw; x += nthr) tc[x] = static_cast<unsigned>(sv[CL.tc + x]);
-            if (tid == 0) {
-                s_t0 = global_timer_ns();
-                s_widx = sv[kCkWidx];
-                s_it = sv[kCkIters];
-                s_it0 = s_it;                     // iterations before this call
-                s_it_end = s_it + it.iterations;
-                s_C = sv[kCkC];
-                s_Cbest = sv[kCkCbest];
-                const long long ev = static_cast<long long>(static_cast<uint32_t>(sv[kCkEvalLo])) |
-                                     (static_cast<long long>(sv[kCkEvalHi]) << 32);
-                const long long wk = static_cast<long long>(static_cast<uint32_t>(sv[kCkWorkLo])) |
-                                     (static_cast<long long>(sv[kCkWorkHi]) << 32);
-                s_eval = crank == 0 ? ev : 0;
-                s_work = crank == 0 ? wk : 0;
-                s_err = 0;
-            }
-            __syncthreads();
-        } else {
-            const int32_t *W0 = it.record + h.inst_words;
-            for (int p = tid; p < n; p += nthr) {
-                const int a = W0[p];
-                W[p] = a;
-                Wbest[p] = a;
-                pos[a] = p;
-            }
-            for (int x = tid; x < tl; x += nthr) stl[x] = 0;             // (0,0) = empty move
-            for (int x = tid; x < tcw; x += nthr) tc[x] = 0u;
-            if (tid == 0) {
-                s_t0 = global_timer_ns();
-                s_widx = 0;
-                s_it = 0;
-                s_it0 = 0;
-                s_it_end = it.iterations;
-                s_eval = 0;
-                s_work = 0;
-                s_err = 0;
-            }
-            __syncthreads();
-            if (warp == 0) {
-                long long w0 = 0;
-                const int c0 = decode<G>(I, mode, W, 0, 0, gw == 0, area, NG, g, w0, err);
-                if (gw == 0 && g.lane == 0) {
-                    s_C = c0;
-                    s_Cbest = c0;
-                }
-            }
-            __syncthreads();
-        }
-
-        const int nslots = n > 3 ? (n - 3) * delta : 0;
-        const unsigned dmagic = slot_magic(delta);
-        long long my_work = 0;
-        for (;;) {
-            if (s_it >= s_it_end || (it.stop_at_cp && s_Cbest == h.cp)) break;
-            const int par = s_it & 1;
-            if (tid == 0) s_bestp[par] = ~0ull;
-            const unsigned long long my_key =
-                best_admissible_key<G, PFX>(I, mode, W, pos, fsp, lpp, tc, moves, area, n, delta, nslots, dmagic,
-                                       move_cap, s_Cbest, csize, crank, &s_nmoves, &s_eval, my_work, err, px);
-            // 4. best admissible move of the block, then of the cluster
-            const unsigned long long wk = warp_min_u64(my_key);
-            if (wl == 0 && wk != ~0ull) atomicMin(&s_bestp[par], wk);
-            if (csize > 1) cg::this_cluster().sync();
-            else __syncthreads();
-            // 5. apply, Alg. 3 (every CTA of a cluster applies the same move)
-            if (tid == 0) {
-                unsigned long long kb = s_bestp[par];
-                for (int r = 1; r < csize; ++r) {
-                    const unsigned long long o = *cg::this_cluster().map_shared_rank(&s_bestp[par],
-                                                                                  (crank + r) % csize);
-                    kb = o < kb ? o : kb;
-                }
-                int bu = 0, bv = 0;
-                s_improved = 0;
-                if (kb != ~0ull) {
-                    const int c = static_cast<int>(kb >> 32);
-                    bu = static_cast<int>((kb >> 16) & 0xffff);
-                    bv = static_cast<int>(kb & 0xffff);
-                    const int a = W[bu], b = W[bv];
-                    W[bu] = b;
-                    W[bv] = a;
-                    pos[b] = bu;
-                    pos[a] = bv;
-                    s_C = c;
-                    if (c < s_Cbest) {
-                        s_Cbest = c;
-                        s_improved = 1;
-                    }
-                }
-                const int old = stl[s_widx];
-                if (old) tc_put(tc, old & 0xffff, old >> 16, delta, false);
-                stl[s_widx] = bu | (bv << 16);
-                if (bu | bv) tc_put(tc, bu, bv, delta, true);
-                s_widx = s_widx + 1 == tl ? 0 : s_widx + 1;
-                if (it.trace && crank == 0) {
-                    it.trace[3 * (s_it - s_it0) + 0] = bu;
-                    it.trace[3 * (s_it - s_it0) + 1] = bv;
-                    it.trace[3 * (s_it - s_it0) + 2] = s_C;
-                }
-                s_it = s_it + 1;
-            }
-            __syncthreads();
-            if (s_improved)
-                for (int p = tid; p < n; p += nthr) Wbest[p] = W[p];
-        }
-        // work of all groups (the lanes of a group hold the same count)
-        const long long ws = warp_sum_i64(g.lane == 0 ? my_work : 0);
-        if (wl == 0) atomicAdd(reinterpret_cast<unsigned long long *>(&s_work), static_cast<unsigned long long>(ws));
-        if (err) atomicOr(&s_err, err);
-        __syncthreads();
-        if (csize > 1) {
-            // rank 0 adds up the cluster's counters; the other CTAs go on to
-            // the next queue pop, which waits for rank 0
-            cg::this_cluster().sync();
-            if (crank == 0 && tid == 0)
-                for (int r = 1; r < csize; ++r) {
-                    s_eval += *cg::this_cluster().map_shared_rank(&s_eval, r);
-                    s_work += *cg::this_cluster().map_shared_rank(&s_work, r);
-                    s_err |= *cg::this_cluster().map_shared_rank(&s_err, r);
-                }
-            __syncthreads();
-        }
-        // outputs: W*, its schedule S*, statistics (rank 0)
-        int32_t *out = it.out;
-        if (crank == 0) {
-        if (warp == 0) {
-            long long w1 = 0;
-            int e1 = 0;
-            const int cb = decode<G>(I, mode, Wbest, 0, 0, gw == 0, area, NG, g, w1, e1, out + n);
-            if (gw == 0) {
-                if (g.lane == 0) {
-                    out[2 * n + kOutCmax] = cb;
-                    if (e1 || cb != s_Cbest) atomicOr(&s_err, 2);
-                }
-            }
-        }
-        for (int p = tid; p < n; p += nthr) out[p] = Wbest[p];
-        __syncthreads();
-        if (tid == 0) {
-            int32_t *st = out + 2 * n;
-            st[kOutEvalLo] = static_cast<int32_t>(s_eval & 0xffffffffll);
-            st[kOutEvalHi] = static_cast<int32_t>(s_eval >> 32);
-            st[kOutWorkLo] = static_cast<int32_t>(s_work & 0xffffffffll);
-            st[kOutWorkHi] = static_cast<int32_t>(s_work >> 32);
-            st[kOutIters] = s_it;
-            st[kOutIters0] = s_it0;
-            st[kOutMode] = mode;
-            st[kOutStatus] = s_err ? RCPSP_E_DEVICE : 0;
-            const unsigned long long t1 = global_timer_ns();
-            st[kOutT0Lo] = static_cast<int32_t>(s_t0 & 0xffffffffull);
-            st[kOutT0Hi] = static_cast<int32_t>(s_t0 >> 32);
-            st[kOutT1Lo] = static_cast<int32_t>(t1 & 0xffffffffull);
-            st[kOutT1Hi] = static_cast<int32_t>(t1 >> 32);
-        }
-        if (it.state && (it.ckpt & kCkptSave)) {
-            // keep the search where it stopped, for a later call to resume
-            const CkptLayout CL = ckpt_layout(n, tl, delta);
-            int32_t *sv = it.state;
-            for (int p = tid; p < n; p += nthr) {
-                sv[CL.W + p] = W[p];
-                sv[CL.Wbest + p] = Wbest[p];
-            }
-            for (int x = tid; x < tl; x += nthr) sv[CL.stl + x] = stl[x];
-            for (int x = tid; x < tcw; x += nthr) sv[CL.tc + x] = static_cast<int32_t>(tc[x]);
-            if (tid == 0) {
-                sv[kCkMagic] = kCkptMagic;
-                sv[kCkN] = n;
-                sv[kCkDelta] = delta;
-                sv[kCkTabu] = tl;
-                sv[kCkMode] = mode;
-                sv[kCkIters] = s_it;
-                sv[kCkC] = s_C;
-                sv[kCkCbest] = s_Cbest;
-                sv[kCkWidx] = s_widx;
-                sv[kCkEvalLo] = static_cast<int32_t>(s_eval & 0xffffffffll);
-                sv[kCkEvalHi] = static_cast<int32_t>(s_eval >> 32);
-                sv[kCkWorkLo] = static_cast<int32_t>(s_work & 0xffffffffll);
-                sv[kCkWorkHi] = static_cast<int32_t>(s_work >> 32);
-            }
-        }
-        }
-        __syncthreads();
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Decoding of caller-given lists (rcpsp_evaluate_lists).
@@ -337,57 +57,6 @@ __global__ void __launch_bounds__(512, 2) evaluate_kernel(LaunchItem item, const
 }
 
 template <int G>
-cudaError_t prepare_search_g(size_t smem) {
-    cudaError_t e = cudaFuncSetAttribute(search_kernel<G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(search_kernel<G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(smem));
-    return e;
-}
-
-template <int G, bool PFX>
-cudaError_t occupancy_g(int threads, size_t smem, int csize, int *units) {
-    if (csize <= 1)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(units, search_kernel<G, PFX>, threads, smem);
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(csize);
-    cfg.blockDim = dim3(threads);
-    cfg.dynamicSmemBytes = smem;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = csize;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaOccupancyMaxActiveClusters(units, search_kernel<G, PFX>, &cfg);
-}
-
-template <int G, bool PFX>
-cudaError_t launch_search_g(const LaunchItem *items, int count, int *queue, int move_cap, int blocks,
-                            int threads, size_t smem, cudaStream_t st, int csize, int *gsnap, int gsnap_words) {
-    if (csize <= 1) {
-        search_kernel<G, PFX><<<blocks, threads, smem, st>>>(items, count, queue, move_cap, 1, gsnap, gsnap_words);
-        return cudaGetLastError();
-    }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(blocks);
-    cfg.blockDim = dim3(threads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = csize;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, search_kernel<G, PFX>, items, count, queue, move_cap, csize, gsnap,
-                              gsnap_words);
-}
-
-template <int G>
 cudaError_t launch_eval_g(const LaunchItem &item, const int32_t *lists, int count, int32_t *start,
                           int32_t *cmax, long long *work, int *err, int blocks, int threads, size_t smem,
                           cudaStream_t st) {
@@ -400,35 +69,25 @@ cudaError_t launch_eval_g(const LaunchItem &item, const int32_t *lists, int coun
 
 }  // namespace
 
-#define RCPSP_DISPATCH_G(G_, CALL)                 \
-    switch (G_) {                                  \
-        case 1: { constexpr int GG = 1; CALL; }    \
-        case 2: { constexpr int GG = 2; CALL; }    \
-        case 4: { constexpr int GG = 4; CALL; }    \
-        case 8: { constexpr int GG = 8; CALL; }    \
-        case 16: { constexpr int GG = 16; CALL; }  \
-        case 32: { constexpr int GG = 32; CALL; }  \
-        default: return cudaErrorInvalidValue;     \
-    }
-
 cudaError_t prepare_search(int group_size, size_t smem) {
-    RCPSP_DISPATCH_G(group_size, return prepare_search_g<GG>(smem))
+    cudaError_t e = prepare_search_nt<kSearchNarrowThreads>(group_size, smem);
+    return e == cudaSuccess ? prepare_search_wide(group_size, smem) : e;
 }
 
 cudaError_t search_occupancy(int group_size, int threads, size_t smem, int csize, int *units, bool prefix) {
-    if (prefix) RCPSP_DISPATCH_G(group_size, return (occupancy_g<GG, true>(threads, smem, csize, units)))
-    RCPSP_DISPATCH_G(group_size, return (occupancy_g<GG, false>(threads, smem, csize, units)))
+    if (threads > kSearchNarrowThreads)
+        return search_occupancy_wide(group_size, threads, smem, csize, units, prefix);
+    return search_occupancy_nt<kSearchNarrowThreads>(group_size, threads, smem, csize, units, prefix);
 }
 
 cudaError_t launch_search(int group_size, const LaunchItem *items, int count, int *queue, int move_cap,
                           int blocks, int threads, size_t smem, cudaStream_t st, int csize, bool prefix,
                           int *gsnap, int gsnap_words) {
-    if (prefix)
-        RCPSP_DISPATCH_G(group_size, return (launch_search_g<GG, true>(items, count, queue, move_cap, blocks,
-                                                                       threads, smem, st, csize, gsnap,
-                                                                       gsnap_words)))
-    RCPSP_DISPATCH_G(group_size, return (launch_search_g<GG, false>(items, count, queue, move_cap, blocks,
-                                                                    threads, smem, st, csize, nullptr, 0)))
+    if (threads > kSearchNarrowThreads)
+        return launch_search_wide(group_size, items, count, queue, move_cap, blocks, threads, smem, st, csize,
+                                  prefix, gsnap, gsnap_words);
+    return launch_search_nt<kSearchNarrowThreads>(group_size, items, count, queue, move_cap, blocks, threads, smem,
+                                                  st, csize, prefix, gsnap, gsnap_words);
 }
 
 cudaError_t launch_evaluate(int group_size, const LaunchItem &item, const int32_t *lists, int count,

@@ -310,3 +310,25 @@ def test_largest_sizes_and_zero_durations(solver, oracle):
             solver.free(ids)
     solver.search([], iterations=5)
     assert solver.results([]) == []
+
+
+def test_launch_shape_limits(solver, oracle):
+    """CTAs of up to 12 warps run the 384-thread build of the search kernel,
+    13 to 16 warps the 512-thread build: both give the oracle's searches.
+    17 warps is refused as an invalid parameter."""
+    insts = I.config_batch("j30_batch", 6, first=31)
+    ids = solver.load(insts)
+    ref = oracle.tabu_search_batch(insts, [(30, 20, 60, 0, 1)] * len(insts), NPROC)
+    for w in (12, 13, 16):
+        solver.search(ids, iterations=30, delta=20, tabu_len=60, group_size=2, warps_per_cta=w)
+        for g, r in zip(solver.results(ids), ref):
+            assert g["best_cmax"] == r["best_cmax"] and g["evaluated"] == r["evaluated"]
+            assert g["best_W"].tolist() == r["best_W"].tolist()
+    for bad in (17, -1):
+        with pytest.raises(R.RcpspError) as e:
+            solver.search(ids, iterations=5, delta=20, tabu_len=60, warps_per_cta=bad)
+        assert e.value.code == -1
+    with pytest.raises(R.RcpspError) as e:
+        solver.coop_search(ids, iterations=5, blocks=2, working_set=2, phi_steps=0, warps_per_cta=17)
+    assert e.value.code == -1
+    solver.free(ids)

@@ -41,6 +41,15 @@ MUTANTS = {
                            "if (fb < fa || (fb == fa && pos[b] > pos[a])) break;"),
     # a block's improvement not written back to the working set
     "no_write_back": ("if (improved && x->Cbb < f->C) {", "if (improved && x->Cbb < f->C && 0) {"),
+    # aspiration admitting a tabu move that only equals the best makespan
+    "aspiration_not_strict": ("if (tabu && !(c < Cbest)) continue;", "if (tabu && !(c <= Cbest)) continue;"),
+    # ties of equal makespan resolved to the last move instead of the smallest (u, v)
+    "tie_break_last": ("if (!found || c < bc) { found = 1;", "if (!found || c <= bc) { found = 1;"),
+    # Alg. 3 without clearing the evicted entry's cache bit
+    "eviction_keeps_cache": ("tabuCache[uo * N + vo] = 0;", "tabuCache[uo * N + vo] = tabuCache[uo * N + vo];"),
+    # an empty iteration (no admissible move) does not advance the tabu list
+    "empty_move_stalls": ("writeIndex = (writeIndex + 1) % p->tabu_len;\n        if (found && C < Cbest)",
+                          "writeIndex = (writeIndex + found) % p->tabu_len;\n        if (found && C < Cbest)"),
 }
 
 
@@ -127,3 +136,10 @@ def test_mutant_fbi_breaks_backward_schedule(oracle, tmp_path, name):
     with mutant(oracle, tmp_path, name):
         with pytest.raises(AssertionError):
             coop.test_fbi_backward_schedule_is_a_schedule(oracle)
+
+
+@pytest.mark.parametrize("name", ["aspiration_not_strict", "tie_break_last", "eviction_keeps_cache",
+                                  "empty_move_stalls"])
+def test_mutant_tabu_rules_break_restatement(oracle, tmp_path, name):
+    with mutant(oracle, tmp_path, name):
+        assert sum(pins.restatement_mismatches(oracle, mode)[0] for mode in (1, 2)) > 0

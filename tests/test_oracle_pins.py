@@ -365,3 +365,126 @@ def test_batch_equals_single(oracle):
         s = oracle.tabu_search(inst, 20, 8, 9, 0, 1)
         assert b["best_cmax"] == s["best_cmax"] and b["evaluated"] == s["evaluated"]
         assert b["best_W"].tolist() == s["best_W"].tolist()
+
+
+# ------------------------------------- tabu search: restated from the paper
+def sgs_earliest_fit(inst, W):
+    """Serial SGS (Alg. 7) from its definition: in list order, each
+    activity starts at the first t >= its predecessors' latest finish at
+    which its demand fits beside everything placed before it."""
+    H = int(inst.dur.sum()) + 1
+    use = np.zeros((inst.m, H + 1), np.int64)
+    preds = {j: [] for j in range(inst.n)}
+    for i, j in inst.arcs():
+        preds[j].append(i)
+    S = np.zeros(inst.n, np.int64)
+    for i in W:
+        d = int(inst.dur[i])
+        r = inst.req[i * inst.m:(i + 1) * inst.m]
+        es = max([S[p] + inst.dur[p] for p in preds[i]], default=0)
+        S[i] = next(t for t in range(es, H + 1)
+                    if all(use[k, t:t + d].max(initial=0) + r[k] <= inst.cap[k] for k in range(inst.m)))
+        for k in range(inst.m):
+            use[k, S[i]:S[i] + d] += r[k]
+    return int(max(S + inst.dur))
+
+
+def level_order(inst):
+    """W0 of Sec. 4.1: ascending (level, label), level = most arcs on a
+    path from the source, by path enumeration."""
+    lev = [max(len(p) - 1 for p in all_paths(inst, 0, j)) for j in range(inst.n)]
+    return np.array(sorted(range(inst.n), key=lambda j: (lev[j], j)), np.int32)
+
+
+def is_tabu(history, x, L):
+    """The simple tabu list of Alg. 3 stated over the history of applied
+    moves m_0, m_1, ...: each iteration writes its move into the cache and
+    evicts the move of L iterations before, clearing its cache entry even
+    when a later copy of the same move is still listed.  So x is tabu iff
+    its last occurrence i is one of the last L moves and no earlier copy of
+    x was evicted after i, i.e. none lies in (i - L, j - L], j the last
+    iteration."""
+    j = len(history) - 1
+    last = max((i for i, m in enumerate(history) if m == x), default=None)
+    if last is None or last <= j - L:
+        return False
+    return not any(history[k] == x for k in range(max(0, last - L + 1), j - L + 1))
+
+
+def tabu_search_restated(inst, iterations, delta, L, mode, stop_at_cp):
+    """Sec. 6 iteration by definitions: every swap (u, v), 1 <= u < v <=
+    N-2, v - u <= delta, whose swapped list is precedence-feasible is
+    decoded; a tabu move is admissible only if strictly better than the best
+    so far; the admissible move with the smallest (C, u, v) is applied; with
+    none, the list stays and the empty move enters the tabu list."""
+    decode = sgs_earliest_fit if mode == 1 else (lambda x, w: decode_by_envelope(x, w)[0])
+    cp = max(sum(int(inst.dur[x]) for x in p[:-1]) for p in all_paths(inst, 0, inst.n - 1))
+    W = level_order(inst)
+    best, best_W = decode(inst, W), W.copy()
+    history, trace, evaluated = [], [], 0
+    for _ in range(iterations):
+        if stop_at_cp and best == cp:
+            break
+        cands = []
+        for u in range(1, inst.n - 2):
+            for v in range(u + 1, min(u + delta, inst.n - 2) + 1):
+                Wc = W.copy()
+                Wc[u], Wc[v] = W[v], W[u]
+                if not list_is_feasible(inst, Wc):
+                    continue
+                c = decode(inst, Wc)
+                evaluated += 1
+                if not is_tabu(history, (u, v), L) or c < best:
+                    cands.append((c, u, v))
+        if cands:
+            c, u, v = min(cands)
+            W[u], W[v] = W[v], W[u]
+            if c < best:
+                best, best_W = c, W.copy()
+        else:
+            u = v = 0
+            c = trace[-1][2] if trace else decode(inst, W)
+        history.append((u, v))
+        trace.append((u, v, c))
+    return dict(trace=trace, evaluated=evaluated, best_cmax=best, best_W=best_W)
+
+
+def restatement_cases():
+    """Tiny instances, plus three found by search on which a tabu move is
+    taken again by aspiration while its older copy is still listed (the
+    case reading R7 decides)."""
+    out = [(x, d, L, stop) for x in small_instances(12, n=6, first=40)
+           for d, L, stop in ((1, 1, 0), (2, 2, 0), (3, 3, 1), (x.n, 5, 0), (2, 9, 0))]
+    for s, d, L in ((264, 3, 5), (308, 4, 12), (170, 4, 12)):
+        out.append((generate(s, 6 + s % 9, 1 + s % 3, 150 + 30 * (s % 3), 20 + 30 * (s % 3), dmax=3 + s % 6,
+                             rmax=2 + s % 7, relabel=bool(s % 2), stream=97), d, L, 0))
+    return out
+
+
+def restatement_mismatches(oracle, mode, iterations=40):
+    """Runs whose oracle trajectory differs from the restatement, and how
+    many empty moves and aspirated repeats of a listed move the
+    restatement made."""
+    bad = empty = dup = 0
+    for inst, delta, L, stop in restatement_cases():
+        ref = tabu_search_restated(inst, iterations, delta, L, mode, stop)
+        got = oracle.tabu_search(inst, iterations, delta, L, mode, stop, trace=True)
+        same = ([tuple(int(x) for x in t) for t in got["trace"][:got["iterations"]]] == ref["trace"]
+                and got["evaluated"] == ref["evaluated"] and got["best_cmax"] == ref["best_cmax"]
+                and got["best_W"].tolist() == ref["best_W"].tolist())
+        bad += not same
+        moves = [t[:2] for t in ref["trace"]]
+        empty += moves.count((0, 0))
+        dup += sum(1 for i, m in enumerate(moves) if m != (0, 0) and m in moves[max(0, i - L):i])
+    return bad, empty, dup
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_tabu_search_equals_restatement(oracle, mode):
+    """The oracle's whole trajectory -- every selected move, its makespan,
+    the neighbour count and the best list -- equals the search restated
+    from the definitions, with tabu lists short enough that entries are
+    evicted, leave no admissible move, and are taken again by aspiration."""
+    bad, empty, dup = restatement_mismatches(oracle, mode)
+    assert bad == 0
+    assert empty > 0 and dup > 0
