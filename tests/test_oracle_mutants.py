@@ -47,6 +47,13 @@ MUTANTS = {
     "tie_break_last": ("if (!found || c < bc) { found = 1;", "if (!found || c <= bc) { found = 1;"),
     # Alg. 3 without clearing the evicted entry's cache bit
     "eviction_keeps_cache": ("tabuCache[uo * N + vo] = 0;", "tabuCache[uo * N + vo] = tabuCache[uo * N + vo];"),
+    # a block exchanging once its budget is reached instead of exceeded (reading C3)
+    "exchange_timeout_inclusive": ("exch[b] = (char)(improved || x->since > x->assigned);",
+                                   "exch[b] = (char)(improved || x->since >= x->assigned);"),
+    # a written slot's iterations counter without the IC that was read (reading C4)
+    "write_ic_without_read_ic": ("f->IC = x->ICread + x->since;", "f->IC = x->since;"),
+    # a block's aspiration threshold its own best instead of C*_max (reading C2)
+    "aspiration_block_best": ("if (tabu && !(c < Casp)) continue;", "if (tabu && !(c < x->Cbb)) continue;"),
     # an empty iteration (no admissible move) does not advance the tabu list
     "empty_move_stalls": ("writeIndex = (writeIndex + 1) % p->tabu_len;\n        if (found && C < Cbest)",
                           "writeIndex = (writeIndex + found) % p->tabu_len;\n        if (found && C < Cbest)"),
@@ -143,3 +150,11 @@ def test_mutant_fbi_breaks_backward_schedule(oracle, tmp_path, name):
 def test_mutant_tabu_rules_break_restatement(oracle, tmp_path, name):
     with mutant(oracle, tmp_path, name):
         assert sum(pins.restatement_mismatches(oracle, mode)[0] for mode in (1, 2)) > 0
+
+
+@pytest.mark.parametrize("name", ["exchange_timeout_inclusive", "write_ic_without_read_ic", "aspiration_block_best",
+                                  "reads_skip_slots", "fbi_backward_order"])
+def test_mutant_cooperation_breaks_restatement(oracle, tmp_path, name):
+    import test_oracle_coop_restated as coop
+    with mutant(oracle, tmp_path, name):
+        assert sum(coop.coop_mismatches(oracle, mode)[0] for mode in (1, 2)) > 0

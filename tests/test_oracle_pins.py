@@ -386,14 +386,16 @@ def sgs_earliest_fit(inst, W):
                     if all(use[k, t:t + d].max(initial=0) + r[k] <= inst.cap[k] for k in range(inst.m)))
         for k in range(inst.m):
             use[k, S[i]:S[i] + d] += r[k]
-    return int(max(S + inst.dur))
+    return int(max(S + inst.dur)), S
 
 
-def level_order(inst):
-    """W0 of Sec. 4.1: ascending (level, label), level = most arcs on a
-    path from the source, by path enumeration."""
+def level_order(inst, key=None):
+    """W0 of Sec. 4.1: ascending (level, key, label), level = most arcs on
+    a path from the source, by path enumeration; key = 0 unless shuffle
+    keys are given."""
     lev = [max(len(p) - 1 for p in all_paths(inst, 0, j)) for j in range(inst.n)]
-    return np.array(sorted(range(inst.n), key=lambda j: (lev[j], j)), np.int32)
+    kk = [0] * inst.n if key is None else [int(x) for x in key]
+    return np.array(sorted(range(inst.n), key=lambda j: (lev[j], kk[j], j)), np.int32)
 
 
 def is_tabu(history, x, L):
@@ -417,7 +419,7 @@ def tabu_search_restated(inst, iterations, delta, L, mode, stop_at_cp):
     decoded; a tabu move is admissible only if strictly better than the best
     so far; the admissible move with the smallest (C, u, v) is applied; with
     none, the list stays and the empty move enters the tabu list."""
-    decode = sgs_earliest_fit if mode == 1 else (lambda x, w: decode_by_envelope(x, w)[0])
+    decode = (lambda x, w: sgs_earliest_fit(x, w)[0]) if mode == 1 else (lambda x, w: decode_by_envelope(x, w)[0])
     cp = max(sum(int(inst.dur[x]) for x in p[:-1]) for p in all_paths(inst, 0, inst.n - 1))
     W = level_order(inst)
     best, best_W = decode(inst, W), W.copy()
