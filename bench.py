@@ -152,14 +152,31 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def load_traffic():
+def load_counters():
+    """The committed ncu figures of the search kernel, if they were taken on
+    the kernel source as it is now (else None)."""
     try:
         d = json.load(open(TRAFFIC_FILE))
         if d.get("kernel_hash") == kernel_hash():
-            return d.get("dram_bytes_per_launch")
+            return d
     except Exception:
         pass
     return None
+
+
+def smem_roofline(counters, per_launch_s, sms, max_mhz):
+    """Shared-memory side of the roofline: the captured launch's wavefronts
+    over the live launch duration, against one 128-byte wavefront per SM per
+    clock."""
+    if not counters or not counters.get("smem_wavefronts_per_launch"):
+        return None
+    wf = counters["smem_wavefronts_per_launch"]
+    peak = sms * max_mhz * 1e6
+    return {"wavefronts_per_launch": wf, "achieved_per_s": wf / per_launch_s, "peak_per_s": peak,
+            "frac": wf / per_launch_s / peak, "issue_active_pct": counters.get("issue_active_pct"),
+            "alu_pipe_active_pct": counters.get("alu_pipe_active_pct"),
+            "basis": "wavefronts from the committed ncu capture of this kernel source; peak = SMs x 1 wavefront "
+                     "per clock (derived)"}
 
 
 def oracle_params(O, I, insts, iterations):
@@ -487,6 +504,11 @@ def run_ours(args):
     peak = sms * 128 * max_mhz * 1e6 / 1e9            # INT32 lane-ops/s, in Gop/s
     per_launch_s = dev_s / args.steps if world == 1 else sum(step_ms) / 1000.0 / args.steps
     achieved = ops_step / per_launch_s / 1e9
+    # the committed counters were taken on the j30 batch; its DRAM traffic does
+    # not depend on the launch shape, the shared-memory wavefronts do
+    counters = load_counters() if WORKLOAD["family"] == "j30_batch" else None
+    shape = tuple(tuned or (args.group_size, args.warps, args.cluster_size or 1))
+    smem = smem_roofline(counters, per_launch_s, sms, max_mhz) if shape == (4, 12, 1) else None
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_sample, args.cpu_iterations or WORKLOAD["iterations"])
@@ -504,9 +526,10 @@ def run_ours(args):
                 "d2h_bytes_per_step": (d1 - d0) // e2e_steps},
         "gpu_launches": launches_timed,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
-                     "frac": achieved / peak, "traffic": load_traffic() if WORKLOAD["family"] == "j30_batch" else None,
+                     "frac": achieved / peak, "traffic": counters["dram_bytes_per_launch"] if counters else None,
                      "ops_per_launch": ops_step,
                      "peak_basis": f"{sms} SMs x 128 INT32 lanes x {max_mhz:.0f} MHz (derived, not measured)",
+                     "smem": smem,
                      **({} if WORKLOAD["family"] == "j30_batch" else
                         {"note": "ops count full decodes; where prefix reuse is on (several decode rounds per "
                                  "iteration) the kernel skips part of them, so this fraction overstates"})},

@@ -21,3 +21,20 @@ def test_reference_arm_prints_one_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
     assert d["config"]["iterations"] == 50 and "j30_batch" in d["config"]["workload"]
+
+
+def test_committed_counters_match_the_kernel_source():
+    """The ncu figures the bench line quotes (DRAM traffic, shared-memory
+    wavefronts) are used only while the kernel source is the one captured;
+    after a change of the kernel they read as null until it is captured
+    again."""
+    import pytest
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.load_counters()
+    if c is None:
+        pytest.skip("the kernel changed since its ncu capture: the bench line reports no counters")
+    assert c["dram_bytes_per_launch"] > 0 and c["smem_wavefronts_per_launch"] > 0
+    s = bench.smem_roofline(c, 0.0407, 152, 2070.0)
+    assert abs(s["frac"] - c["smem_wavefronts_per_launch"] / 0.0407 / (152 * 2070e6)) < 1e-12
+    assert 0 < s["frac"] < 1
