@@ -13,7 +13,9 @@ host preparation, search, result download).
 
 Run: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
      [--workload j30_batch|j120_batch|mixed_batch] [--iterations I]
-Under torchrun each rank solves its own 480 instances (weak scaling).
+Under torchrun each rank solves its own 480 instances (weak scaling); with
+--shard lpt the ranks split one batch by estimated cost instead and rank 0
+gathers the results (strong scaling).
 """
 from __future__ import annotations
 
@@ -362,7 +364,17 @@ def run_ours(args):
     from paper_1711_04556_gb300 import rcpsp as R
     B.build()
     from paper_1711_04556_gb300 import replicas
-    insts = replicas.shard(WORKLOAD["family"], WORKLOAD["count"], rank)
+    if args.shard == "lpt":
+        # one batch split over the ranks by estimated cost (strong scaling)
+        batch = I.config_batch(WORKLOAD["family"], WORKLOAD["count"])
+        if len(batch) < world:
+            raise RuntimeError("fewer instances than ranks")
+        parts = replicas.lpt_partition([replicas.estimated_cost(x, WORKLOAD["iterations"], WORKLOAD["delta"])
+                                        for x in batch], world)
+        insts = [batch[i] for i in parts[rank]]
+    else:
+        parts = None
+        insts = replicas.shard(WORKLOAD["family"], WORKLOAD["count"], rank)
     solver = R.Solver(local)
     st = torch.cuda.Stream(device=dev)
     kw = dict(iterations=WORKLOAD["iterations"], delta=WORKLOAD["delta"], tabu_len=WORKLOAD["tabu_len"],
@@ -442,6 +454,9 @@ def run_ours(args):
     h1, d1 = solver.transfer_bytes()
     t_e2e_max, ev_e2e_all = replicas.reduce_timing(dist, dev, t_e2e, float(ev_e2e), world)
     e2e_val = ev_e2e_all / t_e2e_max
+    # the whole batch's results on rank 0 (after the timed regions)
+    all_res = (replicas.gather_results(dist, ref_res, parts[rank], WORKLOAD["count"], world, rank)
+               if parts is not None else None)
 
     extra = {}
     if rank == 0:
@@ -483,10 +498,11 @@ def run_ours(args):
                                            slice_iterations=args.serving_slice)
         # solution quality: deviation of the best makespan from the critical-path
         # lower bound (the paper's "CP dev." measure), and how many reach it
-        devs = [100.0 * (r["best_cmax"] - r["cp"]) / r["cp"] for r in ref_res if r["cp"] > 0]
+        qres = all_res if all_res is not None else ref_res
+        devs = [100.0 * (r["best_cmax"] - r["cp"]) / r["cp"] for r in qres if r["cp"] > 0]
         extra["quality"] = {"mean_cp_dev_pct": float(np.mean(devs)) if devs else None,
-                            "at_critical_path": int(sum(r["best_cmax"] == r["cp"] for r in ref_res)),
-                            "instances": len(ref_res)}
+                            "at_critical_path": int(sum(r["best_cmax"] == r["cp"] for r in qres)),
+                            "instances": len(qres)}
         extra["latency_ms"] = {
             "single_instance_e2e": {"p50": p50, "p99": p99, "reps": args.latency_reps,
                                     "what": "1 instance, 100 iterations, load+search+results through the C API"},
@@ -515,8 +531,10 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": sum(step_ms) / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": workload_config({"parallelism": f"replicas{world}" if world > 1 else "single GPU",
+        "scaling": "strong" if parts is not None else "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": workload_config({"parallelism": (f"lpt{world}" if parts is not None else f"replicas{world}")
+                                   if world > 1 else "single GPU",
                                    "schedules_per_step": ev_step, "wall_s_timed": t_wall,
                                    "launch_shape": dict(zip(("group_size", "warps_per_cta", "cluster_size"),
                                                             tuned or (args.group_size, args.warps,
@@ -581,6 +599,9 @@ def main():
     ap.add_argument("--cpu-iterations", type=int, default=0, help="iterations of the oracle sample (0: the step's)")
     ap.add_argument("--reference-sample", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--shard", choices=("seeds", "lpt"), default="seeds",
+                    help="seeds: each rank its own batch (weak scaling); lpt: one batch split over the ranks "
+                         "by estimated cost, results gathered on rank 0 (strong scaling)")
     ap.add_argument("--coop-blocks", type=int, default=4,
                     help="co-operating searches per instance in the cooperation measurement (0 skips it)")
     args = ap.parse_args()

@@ -43,3 +43,74 @@ def test_two_gloo_ranks_shard_and_reduce():
         assert not set(gathered[0]) & set(gathered[1])          # disjoint shards
     from paper_1711_04556_gb300 import replicas
     assert [x.digest() for x in replicas.shard("j30_batch", 6, 1)] == out[0][2][1]
+
+
+# ------------------------------------------- one batch split by LPT over ranks
+def _lpt_rank(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from paper_1711_04556_gb300 import instances, replicas
+    batch = instances.config_batch("mixed_batch", 40)
+    costs = [replicas.estimated_cost(x, 1000) for x in batch]
+    parts = replicas.lpt_partition(costs, world)
+    mine = parts[rank]
+    # a stand-in for the search: what a rank reports about each instance
+    results = [{"digest": batch[i].digest(), "rank": rank} for i in mine]
+    got = replicas.gather_results(dist, results, mine, len(batch), world, rank)
+    out[rank] = (parts, got)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_lpt_split_and_gather_over_two_gloo_ranks():
+    world, port = 2, _free_port()
+    mgr = mp.Manager()
+    out = mgr.dict()
+    mp.spawn(_lpt_rank, args=(world, port, out), nprocs=world, join=True)
+    from paper_1711_04556_gb300 import instances
+    batch = instances.config_batch("mixed_batch", 40)
+    parts0, got = out[0]
+    assert out[1][0] == parts0 and out[1][1] is None             # same split everywhere; rank 0 gathers
+    assert sorted(parts0[0] + parts0[1]) == list(range(40))
+    assert [g["digest"] for g in got] == [x.digest() for x in batch]
+    assert all(g["rank"] == (0 if i in parts0[0] else 1) for i, g in enumerate(got))
+
+
+def test_lpt_partition_bounds():
+    """Greedy list scheduling keeps every rank within total/m + the largest
+    cost, and LPT within Graham's (4/3 - 1/(3m)) of the optimum (brute force
+    on small cases)."""
+    import itertools
+    import random
+    from paper_1711_04556_gb300 import replicas
+    rnd = random.Random(5)
+    for trial in range(300):
+        m = rnd.randint(1, 4)
+        costs = [rnd.randint(1, 50) for _ in range(rnd.randint(0, 9))]
+        parts = replicas.lpt_partition(costs, m)
+        assert len(parts) == m and sorted(i for p in parts for i in p) == list(range(len(costs)))
+        loads = [sum(costs[i] for i in p) for p in parts]
+        if costs:
+            assert max(loads) <= sum(costs) / m + max(costs)
+            opt = min(max(sum(c for c, r in zip(costs, a) if r == q) for q in range(m))
+                      for a in itertools.product(range(m), repeat=len(costs)))
+            assert max(loads) <= (4 / 3 - 1 / (3 * m)) * opt + 1e-9
+        assert replicas.lpt_partition(costs, m) == parts
+
+
+def test_potential_moves_is_the_neighbourhood_size(oracle):
+    """With no precedence between the non-dummy activities every swap is
+    feasible, so one iteration decodes exactly the potential moves."""
+    import numpy as np
+    from paper_1711_04556_gb300 import replicas
+    from paper_1711_04556_gb300.instances import Instance
+    for n_act, delta in ((5, 2), (12, 4), (12, 20), (30, 20)):
+        n = n_act + 2
+        succ = [list(range(1, n - 1))] + [[n - 1] for _ in range(n_act)] + [[]]
+        off = np.r_[0, np.cumsum([len(s) for s in succ])].astype(np.int32)
+        inst = Instance(n, 1, np.r_[0, np.ones(n_act), 0].astype(np.int32), np.array([2], np.int32),
+                        np.r_[0, np.ones(n_act), 0].astype(np.int32), off,
+                        np.array([x for s in succ for x in s], np.int32))
+        r = oracle.tabu_search(inst, 1, delta, 5, 1, 0)
+        brute = sum(1 for u in range(1, n - 2) for v in range(u + 1, n - 1) if v - u <= delta)
+        assert r["evaluated"] == brute == replicas.potential_moves(n, delta)
