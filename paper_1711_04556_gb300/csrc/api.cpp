@@ -893,32 +893,57 @@ int rcpsp_coop_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
         key_off[k] = keys_total;
         keys_total += static_cast<size_t>(F) * in.h.n;
     }
-    // launch shape: one for the call, every CTA of a cluster alike
-    int G = gs, warps = p->warps_per_cta, dG, dW;
-    default_shape(items, &dG, &dW);
-    if (!gs && !warps) tuned_shape(c, shape_key(items), &dG, &dW);   // the search's tuned shape, if any
-    if (!G) G = dG;
-    if (!warps) warps = std::max(dW, (G + 31) / 32);
-    const int move_cap = launch_move_cap(items);
+    // footprint classes as in rcpsp_tabu_search, each with its own shape
+    // (every CTA of a cluster alike) and its own queue, longest first
+    struct CoopLaunch {
+        int offset = 0, count = 0, G = 0, warps = 0, move_cap = 0, nclusters = 0;
+        size_t smem = 0;
+    };
+    std::vector<int> order;
+    order.reserve(count);
+    std::vector<CoopLaunch> launches;
     const size_t static_smem = 3072;                       // the kernel's own bookkeeping
     const size_t smem_limit =
         c->prop.sharedMemPerBlockOptin > static_smem ? c->prop.sharedMemPerBlockOptin - static_smem : 0;
-    size_t smem = smem_bytes(items, warps * (32 / G), move_cap);
-    while (smem > smem_limit && p->warps_per_cta == 0 && warps > 1) {
-        --warps;
-        smem = smem_bytes(items, warps * (32 / G), move_cap);
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; q < kClasses; ++q) {
+        std::vector<int> idx;
+        for (int k = 0; k < count; ++k)
+            if (footprint_class(items[k]) == q) idx.push_back(k);
+        if (idx.empty()) continue;
+        std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+        std::vector<LaunchItem> part;
+        for (int k : idx) part.push_back(items[k]);
+        CoopLaunch L;
+        L.offset = static_cast<int>(order.size());
+        L.count = static_cast<int>(idx.size());
+        order.insert(order.end(), idx.begin(), idx.end());
+        int G = gs, warps = p->warps_per_cta, dG, dW;
+        default_shape(part, &dG, &dW);
+        if (!gs && !warps) tuned_shape(c, shape_key(part), &dG, &dW);   // the search's tuned shape, if any
+        if (!G) G = dG;
+        if (!warps) warps = std::max(dW, (G + 31) / 32);
+        L.move_cap = launch_move_cap(part);
+        size_t smem = smem_bytes(part, warps * (32 / G), L.move_cap);
+        while (smem > smem_limit && p->warps_per_cta == 0 && warps > 1) {
+            --warps;
+            smem = smem_bytes(part, warps * (32 / G), L.move_cap);
+        }
+        if (smem > smem_limit)
+            return set_err(c, RCPSP_E_TOO_LARGE, "instance state does not fit in shared memory at this launch shape");
+        int clusters = 0;
+        e = rcpsp::coop_occupancy(G, warps * 32, smem, B, &clusters);
+        if (e != cudaSuccess) return cuda_err(c, e, "co-operative occupancy");
+        if (clusters < 1)
+            return set_err(c, RCPSP_E_TOO_LARGE, "a cluster of this many CTAs does not fit at this shape");
+        L.G = G;
+        L.warps = warps;
+        L.smem = smem;
+        L.nclusters = std::max(1, std::min(L.count, clusters));
+        launches.push_back(L);
     }
-    if (smem > smem_limit)
-        return set_err(c, RCPSP_E_TOO_LARGE, "instance state does not fit in shared memory at this launch shape");
-    int clusters = 0;
-    cudaError_t e = rcpsp::coop_occupancy(G, warps * 32, smem, B, &clusters);
-    if (e != cudaSuccess) return cuda_err(c, e, "co-operative occupancy");
-    if (clusters < 1) return set_err(c, RCPSP_E_TOO_LARGE, "a cluster of this many CTAs does not fit at this shape");
     // device block: [plan][initial lists][random words][working sets]; the
     // first three are uploaded, the working sets are written by the kernel
-    std::vector<int> order(count);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
     auto up16 = [](size_t x) { return (x + 15) & ~static_cast<size_t>(15); };
     const size_t plan_bytes = up16(sizeof(rcpsp::CoopItem) * count);
     const size_t lists_bytes = up16(keys_total * 4);
@@ -970,15 +995,26 @@ int rcpsp_coop_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
     if (random_words)
         std::memcpy(hb + plan_bytes + lists_bytes, random_words, static_cast<size_t>(count) * B * P * 4);
     e = cudaMemcpyAsync(db, hb, up_bytes, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->queue_dev, 0, sizeof(int), st);
-    rcpsp::CoopConfig cfg{B, F, cp->phi_max, cp->phi_steps, cp->assign_fixed, P, cp->fbi_every};
-    const int nclusters = std::max(1, std::min(count, clusters));
-    if (e == cudaSuccess)
-        e = rcpsp::launch_coop(G, reinterpret_cast<const rcpsp::CoopItem *>(db), count, c->queue_dev, move_cap, cfg,
-                               nclusters * B, warps * 32, smem, st);
-    if (e != cudaSuccess) return cuda_err(c, e, "co-operative search launch");
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->queue_dev, 0, sizeof(int) * kClasses, st);
+    if (e != cudaSuccess) return cuda_err(c, e, "co-operative search upload");
     c->h2d += static_cast<long long>(up_bytes);
-    c->kernels += 1;
+    // one launch per class; classes after the first run on forked streams
+    // and join back before the done event
+    rcpsp::CoopConfig cfg{B, F, cp->phi_max, cp->phi_steps, cp->assign_fixed, P, cp->fbi_every};
+    if (launches.size() > 1 && (e = cudaEventRecord(c->fork, st)) != cudaSuccess)
+        return cuda_err(c, e, "event record");
+    for (size_t q = 0; q < launches.size(); ++q) {
+        const CoopLaunch &L = launches[q];
+        cudaStream_t sq = q == 0 ? st : c->aux[q - 1];
+        if (q > 0 && (e = cudaStreamWaitEvent(sq, c->fork, 0)) != cudaSuccess) return cuda_err(c, e, "stream fork");
+        e = rcpsp::launch_coop(L.G, reinterpret_cast<const rcpsp::CoopItem *>(db) + L.offset, L.count,
+                               c->queue_dev + q, L.move_cap, cfg, L.nclusters * B, L.warps * 32, L.smem, sq);
+        if (e != cudaSuccess) return cuda_err(c, e, "co-operative search launch");
+        c->kernels += 1;
+        if (q > 0 && (e = cudaEventRecord(c->join[q - 1], sq)) != cudaSuccess) return cuda_err(c, e, "event record");
+    }
+    for (size_t q = 1; q < launches.size(); ++q)
+        if ((e = cudaStreamWaitEvent(st, c->join[q - 1], 0)) != cudaSuccess) return cuda_err(c, e, "stream join");
     e = cudaEventRecord(c->done, st);
     if (e != cudaSuccess) return cuda_err(c, e, "event record");
     c->pending = true;
