@@ -25,6 +25,9 @@ MUTANTS = {
     "alg4_no_max_with_s": ("int timeDiff = newTime - imax(c[resIdx], s);", "int timeDiff = newTime - c[resIdx];"),
     # Alg. 4 shifted copy taken one element late
     "alg4_copy_offset": ("if (copyIdx >= r) newTime", "if (copyIdx > r) newTime"),
+    # Alg. 4 counting only the entries it touches instead of every loop step
+    "alg4_counts_touched_only": ("            }\n            resIdx = resIdx + 1;\n            ++steps;",
+                                 "                ++steps;\n            }\n            resIdx = resIdx + 1;"),
     # Alg. 5 window not restarted on an insufficient step
     "alg5_no_restart": ("{ loadTime = 0; sufficient = 0; }", "{ sufficient = 0; }"),
     # Eq. 8 with the quality and intactness weights swapped
@@ -158,3 +161,11 @@ def test_mutant_cooperation_breaks_restatement(oracle, tmp_path, name):
     import test_oracle_coop_restated as coop
     with mutant(oracle, tmp_path, name):
         assert sum(coop.coop_mismatches(oracle, mode)[0] for mode in (1, 2)) > 0
+
+
+def test_mutant_alg4_step_count_breaks_work_pins(oracle, tmp_path):
+    with mutant(oracle, tmp_path, "alg4_counts_touched_only"):
+        with pytest.raises(AssertionError):
+            pins.test_capacity_work_counter_matches_envelopes(oracle)
+        with pytest.raises(AssertionError):
+            pins.test_alg4_equals_upper_envelope(oracle)

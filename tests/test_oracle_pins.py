@@ -154,6 +154,8 @@ def test_alg4_equals_upper_envelope(oracle):
         if r and d:
             contrib = [a - max(b, s) for a, b in zip(out, c) if a != b]
             assert sum(contrib) == r * d
+            # the loop runs up to the last entry the update changes
+            assert steps == max(j for j in range(R) if out[j] != c[j]) + 1
         else:
             assert out.tolist() == list(c) and steps == 0
 
@@ -181,6 +183,39 @@ def decode_by_envelope(inst, W):
                 env[k, s:s + inst.dur[i]] += r[k]
                 env[k] = np.maximum.accumulate(env[k][::-1])[::-1]
     return int(max(S + inst.dur)), S
+
+
+def capacity_work_by_envelope(inst, W):
+    """Alg. 4 loop steps of a capacity-indexed decode, from explicit usage
+    envelopes: per activity and used resource, the capacity-indexed state is
+    c[j] = min{t : env(t) <= j}, and the update runs up to the last entry
+    it changes."""
+    H = int(inst.dur.sum()) + 2
+    env = np.zeros((inst.m, H), np.int64)
+    S = np.zeros(inst.n, np.int64)
+    preds = {j: [] for j in range(inst.n)}
+    for i, j in inst.arcs():
+        preds[j].append(i)
+
+    def state(e, R):
+        return [min(t for t in range(H) if e[t] <= j) for j in range(R)]
+    work = 0
+    for i in W:
+        es = max([S[p] + inst.dur[p] for p in preds[i]], default=0)
+        r = inst.req[i * inst.m:(i + 1) * inst.m]
+        t = 0
+        while any(r[k] > 0 and env[k, t] + r[k] > inst.cap[k] for k in range(inst.m)):
+            t += 1
+        s = max(es, t)
+        S[i] = s
+        for k in range(inst.m):
+            if r[k] and inst.dur[i]:
+                before = state(env[k], int(inst.cap[k]))
+                env[k, s:s + inst.dur[i]] += r[k]
+                env[k] = np.maximum.accumulate(env[k][::-1])[::-1]
+                after = state(env[k], int(inst.cap[k]))
+                work += max(j for j in range(len(after)) if after[j] != before[j]) + 1
+    return work
 
 
 def earliest_fit_violations(inst, W, S):
@@ -225,6 +260,16 @@ def test_decoders_on_random_lists(oracle):
             c_cap, S_c, _ = oracle.decode(inst, W, 2)
             c_env, S_env = decode_by_envelope(inst, W)
             assert c_cap == c_env and S_c.tolist() == S_env.tolist()
+
+
+def test_capacity_work_counter_matches_envelopes(oracle):
+    """The capacity-indexed work count (Alg. 4 loop steps) equals the one
+    read off explicit usage envelopes."""
+    rng = np.random.default_rng(17)
+    for inst in medium_instances(16, first=230):
+        for _ in range(2):
+            W = random_feasible_list(inst, rng)
+            assert oracle.decode(inst, W, 2)[2] == capacity_work_by_envelope(inst, W)
 
 
 def test_brute_force_small(oracle):
