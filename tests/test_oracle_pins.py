@@ -91,6 +91,9 @@ def test_table1_order_makespan(oracle, mode):
     assert cmax == vals["cmax"][0] == 22
     rc, c2 = oracle.check_schedule(inst, S)
     assert rc == 0 and c2 == 22 and S[inst.n - 1] == 22
+    # the start times themselves (the example's resource chart is a figure): the
+    # serial SGS restated by earliest fit gives the same schedule
+    assert S.tolist() == sgs_earliest_fit(inst, W)[1].tolist()
 
 
 def test_table1_optimum_by_both_brute_forces(oracle):
