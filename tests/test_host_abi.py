@@ -117,3 +117,40 @@ def test_generator_is_deterministic():
     assert int(np.sum(x.succ_off[1:-1] - x.succ_off[:-2] > 0)) >= 30   # every non-dummy has a successor
     t = I.Instance.from_text(x.to_text())
     assert t.digest() == x.digest()
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every ctypes mirror of a public struct has the C size and the C
+    offset of each field (a C program compiled against include/rcpsp.h
+    prints them)."""
+    import ctypes as C
+    import subprocess
+    from paper_1711_04556_gb300 import rcpsp as R
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    mirrors = {"rcpsp_instance": R.Instance, "rcpsp_params": R.Params, "rcpsp_coop_params": R.CoopParams,
+               "rcpsp_stats": R.Stats, "rcpsp_allocator": R.Allocator, "rcpsp_server_config": R.ServerConfig,
+               "rcpsp_completion": R.Completion, "rcpsp_server_stats": R.ServerStats}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "rcpsp.h"', 'int main(void) {']
+    for cname, py in mirrors.items():
+        lines.append(f'    printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for field, _ in py._fields_:
+            lines.append(f'    printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ['    return 0;', '}']
+    src = tmp_path / "probe.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(root, "include"), "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in filter(None, out):
+        cname, field, value = line.split()
+        got[(cname, field)] = int(value)
+    for cname, py in mirrors.items():
+        assert got[(cname, "sizeof")] == C.sizeof(py), cname
+        for field, _ in py._fields_:
+            assert got[(cname, field)] == getattr(py, field).offset, (cname, field)
+    # the numpy images used to fill and read many records at once
+    for dt, cname in ((R._INSTANCE_DTYPE, "rcpsp_instance"), (R._STATS_DTYPE, "rcpsp_stats")):
+        assert dt.itemsize == got[(cname, "sizeof")]
+        for field in dt.names:
+            assert dt.fields[field][1] == got[(cname, field)], (cname, field)
