@@ -154,3 +154,78 @@ def test_binding_structs_match_the_header(tmp_path):
         assert dt.itemsize == got[(cname, "sizeof")]
         for field in dt.names:
             assert dt.fields[field][1] == got[(cname, field)], (cname, field)
+
+
+def _reaches_avoiding(succ, a, b):
+    """b reachable from a by a path of two or more arcs."""
+    stack = [x for x in succ[a] if x != b]
+    seen = set(stack)
+    while stack:
+        x = stack.pop()
+        if x == b:
+            return True
+        for y in succ[x]:
+            if y not in seen:
+                seen.add(y)
+                stack.append(y)
+    return False
+
+
+def test_generator_follows_the_stated_recipe():
+    """Durations and demands in range (demands used with probability 0.5),
+    round(NC n) arcs among the non-dummy activities, a transitively reduced
+    graph with the source and sink joined to exactly the activities without
+    predecessors / successors, the capacities of the resource-strength
+    formula from the earliest-start profile, and the parameter grid of the
+    batches."""
+    from fractions import Fraction
+    used = cells = 0
+    fams = (("j30_batch", 48, 10), ("j120_batch", 10, 10), ("mixed_batch", 12, 50))
+    for fam, cnt, dmax in fams:
+        for s, x in enumerate(I.config_batch(fam, cnt)):
+            N, m, n = x.n, x.m, x.n - 2
+            nc, rs = x.meta["nc100"], x.meta["rs100"]
+            if fam == "j30_batch":
+                assert (nc, rs) == ((150, 180, 210)[s % 3], (20, 50, 70, 100)[(s // 3) % 4])
+            assert x.dur[0] == 0 and x.dur[-1] == 0 and 1 <= x.dur[1:-1].min() and x.dur.max() <= dmax
+            req = x.req.reshape(N, m)
+            assert not req[0].any() and not req[-1].any()
+            assert ((req[1:-1] == 0) | ((req[1:-1] >= 1) & (req[1:-1] <= 10))).all()
+            used += int((req[1:-1] > 0).sum())
+            cells += n * m
+            succ = [list(x.successors(i)) for i in range(N)]
+            pred = [[] for _ in range(N)]
+            for a, b in x.arcs():
+                pred[b].append(a)
+            inner = [(a, b) for a, b in x.arcs() if a != 0 and b != N - 1]
+            assert len(inner) == (nc * n + 50) // 100
+            for i in range(1, N - 1):
+                assert (0 in pred[i]) == (not [p for p in pred[i] if p != 0])
+                assert (N - 1 in succ[i]) == (not [q for q in succ[i] if q != N - 1])
+            for a, b in x.arcs():
+                assert not _reaches_avoiding(succ, a, b), (fam, s, a, b)
+            # earliest starts in a topological order of the arcs (Kahn)
+            indeg = [len(p) for p in pred]
+            order, ready = [], [0]
+            while ready:
+                a = ready.pop()
+                order.append(a)
+                for b in succ[a]:
+                    indeg[b] -= 1
+                    if indeg[b] == 0:
+                        ready.append(b)
+            assert len(order) == N
+            es = [0] * N
+            for a in order:
+                for b in succ[a]:
+                    es[b] = max(es[b], es[a] + int(x.dur[a]))
+            for k in range(m):
+                kmin = int(req[:, k].max())
+                if kmin == 0:
+                    assert x.cap[k] == 1
+                    continue
+                kmax = max(sum(int(req[i, k]) for i in range(N) if es[i] <= t < es[i] + x.dur[i])
+                           for t in range(max(es) + 1))
+                want = kmin + int(Fraction(rs, 100) * (kmax - kmin) + Fraction(1, 2))
+                assert x.cap[k] == want, (fam, s, k)
+    assert abs(used / cells - 0.5) < 0.03
