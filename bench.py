@@ -202,9 +202,18 @@ def cpu_baseline(sample: int, iterations: int):
     res = O.tabu_search_batch(insts, oracle_params(O, I, insts, iterations), cores)
     dt = time.perf_counter() - t0
     ev = sum(r["evaluated"] for r in res)
+    # the same oracle on one host thread, on the first instances of the sample
+    one = insts[:max(1, min(len(insts), 16))]
+    t1 = time.perf_counter()
+    res1 = O.tabu_search_batch(one, oracle_params(O, I, one, iterations), 1)
+    dt1 = time.perf_counter() - t1
+    ev1 = sum(r["evaluated"] for r in res1)
     return {"value": ev / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"first {sample} of the {WORKLOAD['count']} instances, {iterations} "
-                      f"iterations each, one search per host thread ({ev} schedules in {dt:.2f} s)"}
+                      f"iterations each, one search per host thread ({ev} schedules in {dt:.2f} s)",
+            "single_core": {"value": ev1 / dt1, "unit": UNIT, "cores": 1,
+                            "sample": f"first {len(one)} instances, {iterations} iterations each "
+                                      f"({ev1} schedules in {dt1:.2f} s)"}}
 
 
 def run_reference(args):
@@ -595,7 +604,8 @@ def main():
                     help="run only the serving measurement and print its JSON object")
     ap.add_argument("--plain-sample", type=int, default=48)
     ap.add_argument("--latency-reps", type=int, default=100)
-    ap.add_argument("--cpu-sample", type=int, default=160)
+    ap.add_argument("--cpu-sample", type=int, default=480,
+                    help="instances of the oracle's timed sample (480: the whole j30 batch)")
     ap.add_argument("--cpu-iterations", type=int, default=0, help="iterations of the oracle sample (0: the step's)")
     ap.add_argument("--reference-sample", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
