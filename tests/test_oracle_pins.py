@@ -538,3 +538,30 @@ def test_tabu_search_equals_restatement(oracle, mode):
     bad, empty, dup = restatement_mismatches(oracle, mode)
     assert bad == 0
     assert empty > 0 and dup > 0
+
+
+# ------------------------------------------------- evaluator selection (R8)
+def chain_instance(durs, cap):
+    """Source, the activities in one chain, sink; one resource."""
+    n = len(durs)
+    succ_sets = [[1]] + [[i + 2] for i in range(n)] + [[]]
+    off = np.r_[0, np.cumsum([len(s) for s in succ_sets])].astype(np.int32)
+    return Instance(n + 2, 1, np.r_[0, durs, 0].astype(np.int32), np.array([cap], np.int32),
+                    np.r_[0, np.ones(n), 0].astype(np.int32), off,
+                    np.array([x for s in succ_sets for x in s], np.int32))
+
+
+def test_selection_rule(oracle):
+    """Capacity-indexed exactly when CP * M > 24 * sum R_k (reading R8), the
+    critical path taken by path enumeration; equality stays time-indexed."""
+    long_low = [generate(s, 10 + s % 5, 1 + s % 2, 210, 10, dmax=50, rmax=2, stream=96) for s in range(30)]
+    seen = set()
+    for inst in medium_instances(30, first=1200) + long_low:
+        cp = max(sum(int(inst.dur[x]) for x in p[:-1]) for p in all_paths(inst, 0, inst.n - 1))
+        want = 2 if cp * inst.m > 24 * int(inst.cap.sum()) else 1
+        assert oracle.select_mode(inst) == want
+        seen.add(want)
+    assert seen == {1, 2}
+    for R in (1, 2, 5):
+        assert oracle.select_mode(chain_instance([12 * R, 12 * R], R)) == 1          # CP = 24 R
+        assert oracle.select_mode(chain_instance([12 * R, 12 * R + 1], R)) == 2      # CP = 24 R + 1
