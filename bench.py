@@ -347,7 +347,8 @@ def coop_run(solver, R, I, insts, ids, ref_res, kw, st, args):
                     f"Phi_max 3, Phi_steps 20; the same instances as the main step",
             "schedules_per_s": ev / t, "ms_per_step": 1000 * t, "schedules_per_step": ev,
             "mean_best_cmax": cm, "mean_best_cmax_independent": ind,
-            "mean_cp_dev_pct": float(np.mean([100.0 * (r["best_cmax"] - r["cp"]) / r["cp"] for r in res if r["cp"] > 0])),
+            "mean_cp_dev_pct": float(np.mean([100.0 * (r["best_cmax"] - r["cp"]) / r["cp"]
+                                              for r in res if r["cp"] > 0])),
             "better_instances": int(sum(a["best_cmax"] < b["best_cmax"] for a, b in zip(res, ref_res))),
             "worse_instances": int(sum(a["best_cmax"] > b["best_cmax"] for a, b in zip(res, ref_res)))}
 
@@ -515,7 +516,9 @@ def run_ours(args):
         extra["latency_ms"] = {
             "single_instance_e2e": {"p50": p50, "p99": p99, "reps": args.latency_reps,
                                     "what": "1 instance, 100 iterations, load+search+results through the C API"},
-            "in_batch_completion": {"p50": b50, "p99": b99, "what": "device time from the first search start to each instance's results, one batched step"},
+            "in_batch_completion": {"p50": b50, "p99": b99,
+                                    "what": "device time from the first search start to each instance's results, "
+                                            "one batched step"},
             "in_batch_service": {"p50": s50, "p99": s99, "what": "device time from each search start to its results"}}
 
     if rank != 0:

@@ -25,6 +25,12 @@ MUTANTS = {
     "alg4_no_max_with_s": ("int timeDiff = newTime - imax(c[resIdx], s);", "int timeDiff = newTime - c[resIdx];"),
     # Alg. 4 shifted copy taken one element late
     "alg4_copy_offset": ("if (copyIdx >= r) newTime", "if (copyIdx > r) newTime"),
+    # Eq. 4 with closed intervals: an activity still uses its resources at its finish time
+    "checker_closed_interval": ("if (S[i] <= t && t < S[i] + in->dur[i]) used",
+                                "if (S[i] <= t && t <= S[i] + in->dur[i]) used"),
+    # Eq. 3 refusing a successor that starts exactly at its predecessor's finish
+    "checker_strict_precedence": ("if (S[in->succ[e]] < S[i] + in->dur[i]) return 1;",
+                                  "if (S[in->succ[e]] <= S[i] + in->dur[i]) return 1;"),
     # Alg. 4 counting only the entries it touches instead of every loop step
     "alg4_counts_touched_only": ("            }\n            resIdx = resIdx + 1;\n            ++steps;",
                                  "                ++steps;\n            }\n            resIdx = resIdx + 1;"),
@@ -72,7 +78,8 @@ def mutant(oracle, tmp_path, name):
     mut.write_text(src.replace(old, new))
     (tmp_path / "rcpsp_oracle.h").write_text(open(oracle.HDR).read())
     so = tmp_path / f"lib{name}.so"
-    subprocess.run(["gcc", "-O1", "-std=c11", "-ffp-contract=off", "-shared", "-fPIC", "-pthread", "-o", str(so), str(mut)],
+    subprocess.run(["gcc", "-O1", "-std=c11", "-ffp-contract=off", "-shared", "-fPIC", "-pthread", "-o", str(so),
+                    str(mut)],
                    check=True)
     saved = oracle._handle
     oracle._handle = oracle.load(str(so))
@@ -169,3 +176,10 @@ def test_mutant_alg4_step_count_breaks_work_pins(oracle, tmp_path):
             pins.test_capacity_work_counter_matches_envelopes(oracle)
         with pytest.raises(AssertionError):
             pins.test_alg4_equals_upper_envelope(oracle)
+
+
+@pytest.mark.parametrize("name", ["checker_closed_interval", "checker_strict_precedence"])
+def test_mutant_checker_breaks_its_pins(oracle, tmp_path, name):
+    with mutant(oracle, tmp_path, name):
+        with pytest.raises(AssertionError):
+            pins.test_checker_rejects_violations(oracle)

@@ -565,3 +565,33 @@ def test_selection_rule(oracle):
     for R in (1, 2, 5):
         assert oracle.select_mode(chain_instance([12 * R, 12 * R], R)) == 1          # CP = 24 R
         assert oracle.select_mode(chain_instance([12 * R, 12 * R + 1], R)) == 2      # CP = 24 R + 1
+
+
+# ------------------------------------------------- checker: negative cases
+def test_checker_rejects_violations(oracle):
+    """Eqs. 3-4 with their boundaries: a successor may start exactly at its
+    predecessor's finish, one step earlier is a precedence violation; an
+    activity may start where another with the full capacity ends (intervals
+    are half-open), one step of overlap overloads; negative starts are
+    refused."""
+    inst, vals = table1()
+    W = np.array(vals["W"], np.int32)
+    S = oracle.decode(inst, W, 1)[1].astype(np.int32)
+    assert oracle.check_schedule(inst, S)[0] == 0
+    tight = [(i, j) for i, j in inst.arcs() if S[j] == S[i] + inst.dur[i] and S[j] > 0 and inst.dur[i] > 0]
+    assert tight
+    for i, j in tight:
+        bad = S.copy()
+        bad[j] -= 1
+        assert oracle.check_schedule(inst, bad)[0] == 1
+    neg = S.copy()
+    neg[0] = -1
+    assert oracle.check_schedule(inst, neg)[0] == 3
+    # two unrelated activities that each take the whole capacity
+    succ_sets = [[1, 2], [3], [3], []]
+    off = np.r_[0, np.cumsum([len(s) for s in succ_sets])].astype(np.int32)
+    two = Instance(4, 1, np.array([0, 2, 3, 0], np.int32), np.array([4], np.int32),
+                   np.array([0, 4, 4, 0], np.int32), off, np.array([x for s in succ_sets for x in s], np.int32))
+    assert oracle.check_schedule(two, np.array([0, 0, 2, 5], np.int32)) == (0, 5)
+    assert oracle.check_schedule(two, np.array([0, 0, 1, 4], np.int32))[0] == 2
+    assert oracle.check_schedule(two, np.array([0, 0, 2, 4], np.int32))[0] == 1      # sink before b ends
