@@ -134,7 +134,8 @@ typedef struct rcpsp_ctx rcpsp_ctx;
  * RCPSP_E_INVALID_ARG, RCPSP_E_CUDA. */
 int rcpsp_create(rcpsp_ctx **ctx, int device, const rcpsp_allocator *alloc);
 
-/* Waits for the context's work, frees its device memory and the context. */
+/* Waits for the context's work, frees its device memory and the context.
+ * RCPSP_E_INVALID_ARG for a NULL context. */
 int rcpsp_destroy(rcpsp_ctx *ctx);
 
 /* Validates `count` instances (host memory), computes for each the critical
@@ -150,7 +151,9 @@ int rcpsp_destroy(rcpsp_ctx *ctx);
 int rcpsp_load_instances(rcpsp_ctx *ctx, const rcpsp_instance *inst, int32_t count,
                          int32_t *out_ids);
 
-/* Frees the device memory of loaded instances (their ids become unknown). */
+/* Frees the device memory of loaded instances (their ids become unknown),
+ * after the context's running search.  ids: host, [count].  An unknown id
+ * gives RCPSP_E_NOT_FOUND; the ids before it in the list are freed. */
 int rcpsp_free_instances(rcpsp_ctx *ctx, const int32_t *ids, int32_t count);
 
 /* Runs one tabu search per listed instance (Sec. 6: neighbourhood of swap
@@ -166,7 +169,12 @@ int rcpsp_free_instances(rcpsp_ctx *ctx, const int32_t *ids, int32_t count);
  * the decoder state of the current list every K positions and starts each
  * neighbour's decode from the last state before its first swapped position
  * (prefix reuse; results and counts are those of full decodes).  The call
- * is asynchronous.  Results stay on the device until rcpsp_get_schedules. */
+ * is asynchronous.  Results stay on the device until rcpsp_get_schedules.
+ * ids: host, [count], loaded instances.  Errors, before anything is
+ * launched: RCPSP_E_INVALID_ARG (a parameter out of range, resume without a
+ * state kept with the same swap distance, tabu length and evaluator),
+ * RCPSP_E_NOT_FOUND (id), RCPSP_E_TOO_LARGE (a search state that does not
+ * fit in shared memory at the shape asked for), RCPSP_E_CUDA. */
 int rcpsp_tabu_search(rcpsp_ctx *ctx, const int32_t *ids, int32_t count,
                       const rcpsp_params *params, void *cuda_stream);
 
@@ -276,7 +284,9 @@ int rcpsp_get_schedules(rcpsp_ctx *ctx, const int32_t *ids, int32_t count,
  * record_trace = 1: [iterations][3] = (u, v, C_max after the move), (0, 0)
  * for an iteration without an admissible move.  `capacity` is the number of
  * int32 elements of `trace` (host); *written gets the number of iterations
- * of that call (for a resumed search: the iterations it added). */
+ * of that call (for a resumed search: the iterations it added).  Errors:
+ * RCPSP_E_NOT_FOUND (id), RCPSP_E_INVALID_ARG (no trace recorded, or
+ * `capacity` below 3 x those iterations). */
 int rcpsp_get_trace(rcpsp_ctx *ctx, int32_t id, int32_t *trace, int32_t capacity,
                     int32_t *written);
 
