@@ -147,6 +147,31 @@ def algorithmic_ops(insts, results):
     return ops
 
 
+def algorithmic_smem_bytes(insts, results):
+    """Shared-memory bytes the decodes need at the least, with the search
+    state in shared memory in its packed form.  Time-indexed: every Alg. 5
+    step reads the step's profile words (WPS words of 4 bytes: resources in
+    8-bit fields, 16-bit when a capacity exceeds 127), and each of the d_i
+    steps of Alg. 6 reads and writes them.  Capacity-indexed: one 4-byte read
+    per used resource (Eq. 7), a read and a write per Alg. 4 loop step.  Both
+    read the list (N words) and |E| finish times.  ``work`` and ``evaluated``
+    are the kernel's exact counts."""
+    total = 0
+    for inst, r in zip(insts, results):
+        ev = r["evaluated"]
+        arcs = int(inst.succ_off[-1])
+        if r["mode"] == 1:
+            fields = 4 if int(inst.cap.max()) <= 127 else 2
+            wps = -(-inst.m // fields)
+            wps = 1 if wps <= 1 else (2 if wps <= 2 else 4)
+            total += 4 * wps * (r["work"] + 2 * ev * int(inst.dur.sum()))
+        else:
+            used = int(np.count_nonzero(inst.req))
+            total += 8 * r["work"] + 4 * ev * used
+        total += 4 * ev * (inst.n + arcs)
+    return total
+
+
 def kernel_hash():
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
@@ -409,6 +434,7 @@ def run_ours(args):
     assert all(r["status"] == 0 for r in ref_res), "a search reported an error"
     ev_step = sum(r["evaluated"] for r in ref_res)
     ops_step = algorithmic_ops(insts, ref_res)
+    smem_bytes_step = algorithmic_smem_bytes(insts, ref_res)
 
     # ---------------- timed region: K steps, device time by CUDA events
     barrier()
@@ -560,6 +586,13 @@ def run_ours(args):
                      "ops_per_launch": ops_step,
                      "peak_basis": f"{sms} SMs x 128 INT32 lanes x {max_mhz:.0f} MHz (derived, not measured)",
                      "smem": smem,
+                     "smem_algorithmic": {
+                         "bytes_per_launch": smem_bytes_step,
+                         "achieved_gbs": smem_bytes_step / per_launch_s / 1e9,
+                         "peak_gbs": sms * 128 * max_mhz * 1e6 / 1e9,
+                         "frac": smem_bytes_step / per_launch_s / (sms * 128 * max_mhz * 1e6),
+                         "basis": "least shared-memory bytes of the decodes from the exact work counts; peak = "
+                                  "SMs x 128 bytes per clock (derived)"},
                      **({} if WORKLOAD["family"] == "j30_batch" else
                         {"note": "ops count full decodes; where prefix reuse is on (several decode rounds per "
                                  "iteration) the kernel skips part of them, so this fraction overstates"})},
