@@ -110,8 +110,9 @@ def test_default_line_has_every_key():
         assert k in d, k
     assert d["scaling"] == "weak" and d["steps"] == 3 and d["warmup"] == 3 and d["n_gpus"] == 1
     assert d["gpu_launches"] == 3 and d["config"]["launch_shape"]["chosen_by"] == "rcpsp_autotune"
-    for k in ("bound", "achieved", "peak", "unit", "frac", "traffic"):
+    for k in ("bound", "achieved", "peak", "unit", "frac", "traffic", "smem", "smem_algorithmic"):
         assert k in d["roofline"], k
+    assert 0 < d["roofline"]["smem_algorithmic"]["frac"] < 1
     assert set(d["e2e"]) >= {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"}
     assert d["quality"]["instances"] == 480
 
