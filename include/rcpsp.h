@@ -242,7 +242,13 @@ int rcpsp_coop_search(rcpsp_ctx *ctx, const int32_t *ids, int32_t count, const r
  * rcpsp_get_schedules.  Limits: at most as many instances per call as the
  * array holds (8190; more gives RCPSP_E_TOO_LARGE), no trace, no graph
  * capture and no checkpoints (record_trace, use_graph, checkpoint or resume
- * = 1 gives RCPSP_E_INVALID_ARG).  The
+ * = 1 gives RCPSP_E_INVALID_ARG).  The call makes one launch with one
+ * launch shape for all its instances: no launch classes, no prefix reuse
+ * and one CTA per search (cluster_size other than 0 or 1 gives
+ * RCPSP_E_INVALID_ARG), because the per-class queues, the kept prefix
+ * states and the cluster plan would need context memory.  Results are the
+ * same as rcpsp_tabu_search's; throughput on batches of uneven sizes can be
+ * lower.  The
  * first call on a device also looks up the array's device address with
  * that device current; make that first call before any stream capture.
  * Every call shares the one array and resets its counter: calls whose

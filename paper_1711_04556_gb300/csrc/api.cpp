@@ -1035,6 +1035,8 @@ int rcpsp_tabu_search_noalloc(rcpsp_ctx *c, const int32_t *ids, int32_t count, c
     if (p->record_trace || p->use_graph || p->checkpoint || p->resume)
         return set_err(c, RCPSP_E_INVALID_ARG,
                        "the no-allocation search keeps no trace or state and captures no graph");
+    if (p->cluster_size != 0 && p->cluster_size != 1)
+        return set_err(c, RCPSP_E_INVALID_ARG, "the no-allocation search runs one CTA per search (cluster_size 0 or 1)");
     if (count > rcpsp::noalloc_max_items())
         return set_err(c, RCPSP_E_TOO_LARGE, "the no-allocation search takes at most " +
                                                  std::to_string(rcpsp::noalloc_max_items()) + " instances per call");
@@ -1091,7 +1093,9 @@ int rcpsp_tabu_search_noalloc(rcpsp_ctx *c, const int32_t *ids, int32_t count, c
     LaunchItem *plan = nullptr;
     cudaError_t e = rcpsp::noalloc_scratch(c->device, &queue, &plan);
     if (e != cudaSuccess) return cuda_err(c, e, "scratch address");
-    e = rcpsp::prepare_search(G, smem);
+    // the same process-wide limit rcpsp_tabu_search sets, so that the value
+    // only ever goes up for a launch on another thread or context
+    e = rcpsp::prepare_search(G, smem_limit);
     if (e != cudaSuccess) return cuda_err(c, e, "kernel attributes");
     int per_sm = 0;
     e = rcpsp::search_occupancy(G, threads, smem, 1, &per_sm);

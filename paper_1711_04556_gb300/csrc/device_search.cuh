@@ -363,42 +363,51 @@ __device__ int decode_capacity(const SInst &I, const int *W, int u, int v, bool 
         er = g.max(er);
         const int s = ::max(es, er);
         const int d = I.dur[i];
-        // Alg. 4, one lane per used resource (resources k = lane, lane+G, ...),
-        // as a per-index closed form of its result:
-        //   j <  r : c'[j] = max(c[j], s+d)
-        //   j >= r : c'[j] = c[j-r] <= s ? c[j] : max(c[j], min(c[j-r], s+d))
-        // c_k is non-increasing, so a = #{j : c[j] > s} is found by binary
-        // search and nothing at j >= r + a changes (there c[j-r] <= s).  The
-        // lane updates [0, r+a) from the top down, so that c[j-r] is still old
-        // when it is read; the first change it meets is Alg. 4's last one.
+        // Alg. 4, one lane per used resource (resources k = lane, lane+G, ...).
+        // With T = s+d, a = #{j : c[j] > s} and b = #{j : c[j] >= T} (c_k is
+        // non-increasing, and s >= c[R-r] by Eq. 7, so b <= a <= R-r), the
+        // result of Alg. 4 is c with r copies of T inserted at b and the r
+        // entries from a on dropped:
+        //   c' = c[0..b) ++ T^r ++ c[b..a) ++ c[r+a..R),
+        // and its last change is at index r+a-1, so it runs r+a loop steps.
+        // (Both facts follow from the per-index form j < r: max(c[j], T);
+        // j >= r: c[j-r] <= s ? c[j] : max(c[j], min(c[j-r], T)).)  The lane
+        // finds a and b by two interleaved binary searches, shifts c[b..a)
+        // up by r from the top down (a batch of reads before its writes, so
+        // every read sees the old value) and writes T into [b, b+r).
         if (act && d > 0)
             for (int k = g.lane; k < m; k += G) {
                 const int r = I.reqk[i * m + k];
                 if (r == 0) continue;
                 const int R = I.cap[k];
+                const int T = s + d;
                 int *ck = cst + I.cbase[k] * NG;
-                int lo = 0, hi = R;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (ck[mid * NG] > s) lo = mid + 1;
-                    else hi = mid;
-                }
-                int last = -1;
-                for (int j = ::min(R, r + lo) - 1; j >= 0; --j) {
-                    const int old = ck[j * NG];
-                    int nv;
-                    if (j < r) {
-                        nv = ::max(old, s + d);
-                    } else {
-                        const int prev = ck[(j - r) * NG];
-                        nv = prev <= s ? old : ::max(old, ::min(prev, s + d));
+                int alo = 0, ahi = R - r, blo = 0, bhi = R - r;
+                while (alo < ahi || blo < bhi) {
+                    const int am = (alo + ahi) >> 1, bm = (blo + bhi) >> 1;
+                    const int ca = ck[am * NG], cb = ck[bm * NG];
+                    if (alo < ahi) {
+                        if (ca > s) alo = am + 1;
+                        else ahi = am;
                     }
-                    if (nv != old) {
-                        ck[j * NG] = nv;
-                        if (last < 0) last = j;
+                    if (blo < bhi) {
+                        if (cb >= T) blo = bm + 1;
+                        else bhi = bm;
                     }
                 }
-                wk += last + 1;                         // Alg. 4 stops after its last change
+                const int a = alo, b = blo;
+                int j = r + a - 1;
+                for (; j - 3 >= r + b; j -= 4) {
+                    const int x0 = ck[(j - r) * NG], x1 = ck[(j - 1 - r) * NG];
+                    const int x2 = ck[(j - 2 - r) * NG], x3 = ck[(j - 3 - r) * NG];
+                    ck[j * NG] = x0;
+                    ck[(j - 1) * NG] = x1;
+                    ck[(j - 2) * NG] = x2;
+                    ck[(j - 3) * NG] = x3;
+                }
+                for (; j >= r + b; --j) ck[j * NG] = ck[(j - r) * NG];
+                for (int x = b; x < b + r; ++x) ck[x * NG] = T;
+                wk += r + a;                            // Alg. 4's loop steps
             }
         if (act) {
             if (S_out && g.lane == 0) S_out[i] = s;
