@@ -179,7 +179,8 @@ template <int G>
 __global__ void __launch_bounds__(512, 2) coop_kernel(const CoopItem *__restrict__ items, int count,
                                                     int *__restrict__ queue, int move_cap, CoopConfig cfg) {
     extern __shared__ __align__(16) int sm[];
-    __shared__ int s_item, s_nmoves, s_C, s_Cbb, s_widx, s_it, s_err, s_improved;
+    __shared__ int s_mq[2];
+    __shared__ int s_item, s_C, s_Cbb, s_widx, s_it, s_err, s_improved;
     __shared__ unsigned long long s_best, s_t0;
     __shared__ long long s_eval, s_work;
     __shared__ int s_pub[2], s_pub_div[2];            // this CTA's best since its read, by parity
@@ -367,7 +368,7 @@ __global__ void __launch_bounds__(512, 2) coop_kernel(const CoopItem *__restrict
             if (tid == 0) s_best = ~0ull;
             const unsigned long long my_key =
                 best_admissible_key<G>(I, mode, W, pos, fsp, lpp, tc, moves, area, n, delta, nslots, dmagic,
-                                       move_cap, s_Cstar, 1, 0u, &s_nmoves, &s_eval, my_work, err);
+                                       move_cap, s_Cstar, 1, 0u, s_mq, &s_eval, my_work, err);
             const unsigned long long wk = warp_min_u64(my_key);
             if (wl == 0 && wk != ~0ull) atomicMin(&s_best, wk);
             __syncthreads();

@@ -476,28 +476,34 @@ __device__ __forceinline__ void tc_put(unsigned *tc, int u, int v, int delta, bo
 // ---------------------------------------------------------------------------
 // Steps 1-3 of an iteration (Sec. 6) on the CTA's current list W: the first
 // successor / last predecessor position of every position (and, with prefix
-// reuse, the kept decoder states of W, see Prefix), then, stripe by
-// stripe of move_cap potential moves, the feasible moves (with csize > 1
-// only this cluster rank's chunks of 32 slots) ballot-compacted into
-// `moves` and decoded by the groups.  Returns the thread's smallest key
-// (C_max << 32 | u << 16 | v) among admissible moves -- not tabu, or
-// C_max < aspiration -- or ~0 when it saw none.  Thread 0 adds the number
-// of decoded neighbours to *s_eval; every thread adds its decode work to
-// my_work.  Starts and ends with a __syncthreads, so the caller may reset
-// its reduction word before the call.
+// reuse, the kept decoder states of W, see Prefix), then the feasible moves
+// (with csize > 1 only this cluster rank's chunks of 32 slots),
+// ballot-compacted into `moves` and decoded by the groups.  The potential
+// moves are filtered in passes of up to nthr slots while the list has room
+// for a whole pass (it holds move_cap moves), then the warps drain the list:
+// each warp takes the next NG moves from the counter s_mq[1] and decodes
+// them in lockstep, so a warp with short decodes takes more of them and the
+// block meets at one barrier per full list instead of one per round.  The
+// list is in (u, v) order up to the order of the warps inside a pass, so the
+// longest decodes (small u, with prefix reuse) go first.  Returns the
+// thread's smallest key (C_max << 32 | u << 16 | v) among admissible moves
+// -- not tabu, or C_max < aspiration -- or ~0 when it saw none.  Thread 0
+// adds the number of decoded neighbours to *s_eval; every thread adds its
+// decode work to my_work.  Starts and ends with a __syncthreads, so the
+// caller may reset its reduction word before the call.
 // ---------------------------------------------------------------------------
 template <int G, bool PFX = false>
 __device__ __forceinline__ unsigned long long best_admissible_key(
         const SInst &I, int mode, const int *W, const int *pos, int *fsp, int *lpp, const unsigned *tc,
         int *moves, int *area, int n, int delta, int nslots, unsigned dmagic, int move_cap, int aspiration,
-        int csize, unsigned crank, int *s_nmoves, long long *s_eval, long long &my_work, int &err,
+        int csize, unsigned crank, int *s_mq, long long *s_eval, long long &my_work, int &err,
         const Prefix &px = Prefix{nullptr, 1, 0, 0}) {
     constexpr int NG = 32 / G;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int warp = tid >> 5, wl = tid & 31;
-    const int ngroups = (nthr >> 5) * NG;
     const int gw = wl / G;
     const Group<G> g;
+    (void)warp;
     // 1. first successor / last predecessor position of every position
     for (int p = tid; p < n; p += nthr) {
         const int a = W[p];
@@ -515,17 +521,21 @@ __device__ __forceinline__ unsigned long long best_admissible_key(
     }
     __syncthreads();
     unsigned long long my_key = ~0ull;
-    for (int base = 0; base < nslots; base += move_cap) {
-        const int stripe = ::min(move_cap, nslots - base);
-        if (tid == 0) *s_nmoves = 0;
+    const int pass = ::min(nthr, move_cap);      // slots of one filter pass (<= move_cap)
+    int base = 0;
+    while (base < nslots) {
+        if (tid == 0) {
+            s_mq[0] = 0;                          // compaction cursor
+            s_mq[1] = 0;                          // drain cursor
+        }
         __syncthreads();
-        // 2. feasible moves of the stripe, compacted
-        for (int k0 = 0; k0 < stripe; k0 += nthr) {
-            const int k = k0 + tid;
+        // 2. feasible moves, compacted, pass by pass while a pass still fits
+        int nm = 0;
+        while (base < nslots && nm + pass <= move_cap) {
             bool ok = false;
             int code = 0;
-            if (k < stripe) {
-                const int slot = base + k;
+            if (tid < pass && base + tid < nslots) {
+                const int slot = base + tid;
                 const int q = delta > 1 ? static_cast<int>(__umulhi(static_cast<unsigned>(slot), dmagic)) : slot;
                 const int u = 1 + q;
                 const int v = u + 1 + (slot - q * delta);
@@ -537,15 +547,19 @@ __device__ __forceinline__ unsigned long long best_admissible_key(
             }
             const unsigned b = __ballot_sync(kFull, ok);
             int wb = 0;
-            if (wl == 0 && b) wb = atomicAdd(s_nmoves, __popc(b));
+            if (wl == 0 && b) wb = atomicAdd(&s_mq[0], __popc(b));
             wb = __shfl_sync(kFull, wb, 0);
             if (ok) moves[wb + __popc(b & ((1u << wl) - 1u))] = code;
+            nm += __syncthreads_count(ok);        // the same count in every thread
+            base += pass;
         }
-        __syncthreads();
-        const int nm = *s_nmoves;
-        // 3. decode the neighbours
-        // (the groups of a warp take consecutive moves and decode them in lockstep)
-        for (int q0 = warp * NG; q0 < nm; q0 += ngroups) {
+        // 3. decode the neighbours: the groups of a warp take NG consecutive
+        // moves at a time and decode them in lockstep
+        for (;;) {
+            int q0 = 0;
+            if (wl == 0) q0 = atomicAdd(&s_mq[1], NG);
+            q0 = __shfl_sync(kFull, q0, 0);
+            if (q0 >= nm) break;
             const int q = q0 + gw;
             const bool act = q < nm;
             const int code = act ? moves[q] : 0;

@@ -50,7 +50,8 @@ __global__ void __launch_bounds__(NT, 2) search_kernel(const LaunchItem *__restr
                                                       int *__restrict__ queue, int move_cap, int csize,
                                                       int *__restrict__ gsnap, int gsnap_words) {
     extern __shared__ __align__(16) int sm[];
-    __shared__ int s_item, s_nmoves, s_C, s_Cbest, s_widx, s_it, s_improved, s_err, s_it0, s_it_end;
+    __shared__ int s_mq[2];
+    __shared__ int s_item, s_C, s_Cbest, s_widx, s_it, s_improved, s_err, s_it0, s_it_end;
     __shared__ unsigned long long s_bestp[2], s_t0;      // best key of the iteration, by parity
     __shared__ long long s_eval, s_work;
     const unsigned crank = csize > 1 ? cg::this_cluster().block_rank() : 0u;
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(NT, 2) search_kernel(const LaunchItem *__restr
             if (tid == 0) s_bestp[par] = ~0ull;
             const unsigned long long my_key =
                 best_admissible_key<G, PFX>(I, mode, W, pos, fsp, lpp, tc, moves, area, n, delta, nslots, dmagic,
-                                       move_cap, s_Cbest, csize, crank, &s_nmoves, &s_eval, my_work, err, px);
+                                       move_cap, s_Cbest, csize, crank, s_mq, &s_eval, my_work, err, px);
             // 4. best admissible move of the block, then of the cluster
             const unsigned long long wk = warp_min_u64(my_key);
             if (wl == 0 && wk != ~0ull) atomicMin(&s_bestp[par], wk);
