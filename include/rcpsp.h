@@ -117,6 +117,23 @@ typedef struct {
     int32_t status;             /* 0, or a negative RCPSP_E_* code              */
     int64_t t_start_ns;         /* device global timer when the search started   */
     int64_t t_end_ns;           /* device global timer when its results were out */
+    /* Work the decodes of the last call performed, for throughput
+     * accounting (a resumed search counts only its own call).  With prefix
+     * reuse a neighbour's decode restores the decoder state of the current
+     * list before its first swapped position instead of placing those
+     * activities again; the positions it restores are not counted here,
+     * while `evaluated` and `work` above count every neighbour in full.
+     * Counted: the neighbour decodes and the decodes of the current list
+     * that produce the kept states (not the first and last decode of a
+     * search). */
+    int64_t placements;         /* activities placed (serial SGS steps, Alg. 7) */
+    int64_t steps_done;         /* Alg. 5 / Alg. 4 loop steps of those placements */
+    int64_t update_units;       /* time-indexed: Alg. 6 update steps (sum of
+                                   d_i); capacity-indexed: Eq. 7 reads (one per
+                                   resource with r_{i,k} > 0)                  */
+    int64_t succ_pushes;        /* successor updates (|succ(i)| per placement)  */
+    int64_t kept_words;         /* 32-bit words of kept decoder states written
+                                   and read (device memory, L2-resident)       */
 } rcpsp_stats;
 
 /* Optional device allocator.  alloc returns device memory of `bytes` bytes
@@ -339,6 +356,49 @@ int rcpsp_transfer_bytes(const rcpsp_ctx *ctx, int64_t *h2d, int64_t *d2h);
  * counterpart in the paper. */
 int rcpsp_kernel_launches(const rcpsp_ctx *ctx, int64_t *launches);
 
+/* Launch plan of the context's last rcpsp_tabu_search: one entry per
+ * launch class of that call (see rcpsp_tabu_search), in launch order
+ * (classes of more estimated work first). */
+typedef struct {
+    int32_t searches;           /* searches of the class                          */
+    int32_t group_size;         /* lanes per neighbour decode                      */
+    int32_t warps;              /* warps per CTA                                   */
+    int32_t cluster_size;       /* CTAs per search                                 */
+    int32_t ctas;               /* CTAs launched (persistent)                      */
+    int32_t prefix_reuse;       /* 1: neighbours start from kept decoder states    */
+    int32_t shape_source;       /* 0: built-in defaults, 1: the context's table of
+                                   measured shapes (rcpsp_autotune), 2: the caller */
+    int32_t reserved;
+    int64_t smem_bytes;         /* dynamic shared memory per CTA                   */
+} rcpsp_launch_info;
+
+/* Copies up to `capacity` entries of that plan to `out` (host; NULL with
+ * capacity 0 to ask only for the count); *count gets the number of
+ * classes.  An accounting call with no counterpart in the paper. */
+int rcpsp_last_launches(const rcpsp_ctx *ctx, rcpsp_launch_info *out, int32_t capacity, int32_t *count);
+
+/* Measured ceilings of the integer search path on one GPU, for its
+ * roofline: the 32-bit integer ALU rate (independent chains of a logical
+ * and an add per link, registers only; ops counted per thread) and the
+ * shared-memory load bandwidth (16-byte loads, consecutive lanes at
+ * consecutive words, no bank conflicts).  Each rate is the best of five
+ * launches of one full wave (the blocks every SM holds at once), timed with
+ * CUDA events, at the clocks of the run. */
+typedef struct {
+    double int32_ops_per_s;        /* whole GPU                                  */
+    double smem_bytes_per_s;       /* whole GPU                                  */
+    double int32_ms;               /* event time of the best integer launch      */
+    double smem_ms;                /* event time of the best shared-memory launch */
+    int32_t sms;                   /* SMs of the device                          */
+} rcpsp_peaks;
+
+/* Runs the two measurements on CUDA device `device` (a few tens of ms,
+ * synchronous; it allocates and frees a few bytes of device memory and
+ * restores the calling thread's current device).  Errors:
+ * RCPSP_E_INVALID_ARG (NULL `out`, bad device), RCPSP_E_CUDA.  A measuring
+ * call with no counterpart in the paper. */
+int rcpsp_measure_peaks(int device, rcpsp_peaks *out);
+
 /* ------------------------------------------------------------------------
  * Continuous-batching solve server.  Requests are admitted while others run,
  * as launch slots and device memory free up, and their searches overlap on
@@ -364,6 +424,10 @@ typedef struct {
                                    searches take turns with newer requests;
                                    results are those of an uninterrupted search.
                                    0 = no slicing                                 */
+    int32_t max_pending;        /* > 0: most requests waiting for admission; a
+                                   submission beyond it is refused with
+                                   RCPSP_E_TOO_LARGE and counted as rejected (load
+                                   shedding under overload).  0 = no limit        */
 } rcpsp_server_config;
 
 typedef struct {
@@ -387,7 +451,10 @@ typedef struct {
 
 /* Starts a server on `device` (cfg may be NULL for the defaults).  It owns
  * `slots` library contexts whose device memory comes from stream-ordered
- * allocations on their own streams, and one worker thread. */
+ * allocations on their own streams, and one worker thread.  Before it
+ * returns it maps the memory budget in the server's pool, sizes every
+ * slot's pinned staging and launch plan for a full batch and loads the
+ * search kernels, so that the first requests do not pay for that. */
 int rcpsp_server_create(rcpsp_server **srv, int device, const rcpsp_server_config *cfg);
 /* Stops the worker after the batches in flight and frees everything. */
 int rcpsp_server_destroy(rcpsp_server *srv);

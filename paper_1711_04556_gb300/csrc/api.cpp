@@ -107,6 +107,7 @@ struct rcpsp_ctx {
     size_t coop_host_cap = 0;
     // measured launch shapes: workload signature -> (G, warps, CTAs per search)
     std::vector<std::pair<std::string, std::array<int, 3>>> tuned;
+    std::vector<rcpsp_launch_info> last_launches;   // plan of the last search call
 };
 
 namespace {
@@ -169,8 +170,11 @@ void default_shape(const std::vector<LaunchItem> &items, int *G, int *warps) {
     *warps = std::max(1, std::min(rcpsp::kSearchMaxWarps, w));
 }
 
-// Potential moves one stripe examines: the largest (N-3)*delta of the batch,
-// rounded up to a warp, at most kDefaultMoveCap.
+// Entries of the move list of a launch: the largest number of potential
+// moves (N-3)*delta of the batch, rounded up to a warp, at most
+// kDefaultMoveCap (the list is filled over several filter passes and
+// drained when the next pass might not fit; searches with more feasible
+// moves take several such batches per iteration).
 int launch_move_cap(const std::vector<LaunchItem> &items) {
     int m = 32;
     for (const LaunchItem &it : items) m = std::max(m, it.h.n > 3 ? (it.h.n - 3) * it.delta : 0);
@@ -232,6 +236,8 @@ struct ClassLaunch {
     int snap_words = 0;          // kept-state words per CTA
     size_t snap_off = 0;         // its first word in the context's scratch
     size_t smem = 0;
+    int shape_source = 0;        // rcpsp_launch_info.shape_source
+    double cost = 0;             // estimated work of the class
 };
 
 // CTAs that share one search: 1 unless the class has few searches for the
@@ -325,6 +331,33 @@ namespace rcpsp {
 
 // 1 when the context's last search has finished (or none is pending), 0 while
 // it runs, a negative RCPSP_E_* code when the device reported an error.
+// Sizes the context's pinned upload staging (bytes) and launch plan (items,
+// pinned and device) ahead of use, so that later calls of up to that size
+// allocate nothing there.
+int ctx_reserve(rcpsp_ctx *c, size_t staging_bytes, int plan_items) {
+    cudaSetDevice(c->device);
+    if (c->load_host_cap < staging_bytes) {
+        if (c->load_host) cudaFreeHost(c->load_host);
+        c->load_host = nullptr;
+        c->load_host_cap = 0;
+        if (cudaMallocHost(reinterpret_cast<void **>(&c->load_host), staging_bytes) != cudaSuccess)
+            return set_err(c, RCPSP_E_CUDA, "pinned staging");
+        c->load_host_cap = staging_bytes;
+    }
+    const size_t ibytes = sizeof(LaunchItem) * static_cast<size_t>(std::max(1, plan_items));
+    if (c->items_cap < ibytes) {
+        dev_free(c, c->items_dev, c->items_cap, nullptr);
+        if (c->items_host) cudaFreeHost(c->items_host);
+        c->items_host = nullptr;
+        c->items_dev = static_cast<LaunchItem *>(dev_alloc(c, ibytes, nullptr));
+        c->items_cap = c->items_dev ? ibytes : 0;
+        if (!c->items_dev) return set_err(c, RCPSP_E_CUDA, "plan allocation failed");
+        if (cudaMallocHost(reinterpret_cast<void **>(&c->items_host), ibytes) != cudaSuccess)
+            return set_err(c, RCPSP_E_CUDA, "pinned staging");
+    }
+    return RCPSP_OK;
+}
+
 int ctx_search_done(rcpsp_ctx *c) {
     if (!c->pending) return 1;
     const cudaError_t e = cudaEventQuery(c->done);
@@ -410,6 +443,14 @@ int rcpsp_transfer_bytes(const rcpsp_ctx *c, int64_t *h2d, int64_t *d2h) {
     if (!c) return RCPSP_E_INVALID_ARG;
     if (h2d) *h2d = c->h2d;
     if (d2h) *d2h = c->d2h;
+    return RCPSP_OK;
+}
+
+int rcpsp_last_launches(const rcpsp_ctx *c, rcpsp_launch_info *out, int32_t capacity, int32_t *count) {
+    if (!c || !count || capacity < 0 || (capacity > 0 && !out)) return RCPSP_E_INVALID_ARG;
+    const int n = static_cast<int>(c->last_launches.size());
+    for (int k = 0; k < n && k < capacity; ++k) out[k] = c->last_launches[k];
+    *count = n;
     return RCPSP_OK;
 }
 
@@ -534,6 +575,8 @@ int rcpsp_free_instances(rcpsp_ctx *c, const int32_t *ids, int32_t count) {
             return set_err(c, RCPSP_E_NOT_FOUND, "unknown instance id");
         Inst &in = c->insts[id];
         in.alive = false;
+        std::vector<int32_t>().swap(in.succ_off);     // a long-lived context keeps no host copies
+        std::vector<int32_t>().swap(in.succ);
         dev_free(c, in.trace, in.trace_bytes, nullptr);
         in.trace = nullptr;
         in.trace_bytes = 0;
@@ -643,7 +686,9 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
         int G = gs, warps = p->warps_per_cta;
         int dG, dW, dC = default_cluster(part, c->prop.multiProcessorCount);
         default_shape(part, &dG, &dW);
-        if (!gs && !warps) tuned_shape(c, shape_key(part), &dG, &dW, &dC);
+        L.shape_source = gs || warps ? 2 : 0;
+        if (!gs && !warps && tuned_shape(c, shape_key(part), &dG, &dW, &dC)) L.shape_source = 1;
+        for (int k : idx) L.cost += cost[k];
         if (!G) G = dG;
         if (!warps) warps = std::max(dW, (G + 31) / 32);
         L.csize = cs ? cs : dC;
@@ -674,6 +719,10 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
                                 : L.csize * std::max(1, std::min(L.count, units));
         launches.push_back(L);
     }
+    // classes of more work launch first, so that the long searches of a call
+    // are not queued behind short classes for SMs
+    std::stable_sort(launches.begin(), launches.end(),
+                     [](const ClassLaunch &a, const ClassLaunch &b) { return a.cost > b.cost; });
     // kept prefix states: one region per CTA of every class that uses them
     {
         size_t need = 0;
@@ -773,6 +822,10 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
         if (e != cudaSuccess) return cuda_err(c, e, "search launch");
     }
     c->kernels += static_cast<long long>(launches.size());
+    c->last_launches.clear();
+    for (const ClassLaunch &L : launches)
+        c->last_launches.push_back(rcpsp_launch_info{L.count, L.G, L.threads / 32, L.csize, L.blocks, L.prefix ? 1 : 0,
+                                                     L.shape_source, 0, static_cast<int64_t>(L.smem)});
     if (p->checkpoint)
         for (const LaunchItem &it : items) {
             // items[] holds the ids' searches in call order
@@ -1284,6 +1337,11 @@ int rcpsp_get_schedules(rcpsp_ctx *c, const int32_t *ids, int32_t count, int32_t
             x.status = s[rcpsp::kOutStatus];
             x.t_start_ns = (static_cast<int64_t>(s[rcpsp::kOutT0Hi]) << 32) | static_cast<uint32_t>(s[rcpsp::kOutT0Lo]);
             x.t_end_ns = (static_cast<int64_t>(s[rcpsp::kOutT1Hi]) << 32) | static_cast<uint32_t>(s[rcpsp::kOutT1Lo]);
+            int64_t *ta[rcpsp::kTallies] = {&x.placements, &x.steps_done, &x.update_units, &x.succ_pushes,
+                                            &x.kept_words};
+            for (int t = 0; t < rcpsp::kTallies; ++t)
+                *ta[t] = (static_cast<int64_t>(s[rcpsp::kOutPlacedLo + 2 * t + 1]) << 32) |
+                         static_cast<uint32_t>(s[rcpsp::kOutPlacedLo + 2 * t]);
         }
         if (s[rcpsp::kOutStatus] != 0) status = RCPSP_E_DEVICE;
     }

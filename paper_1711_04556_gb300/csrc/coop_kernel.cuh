@@ -183,6 +183,7 @@ __global__ void __launch_bounds__(512, 2) coop_kernel(const CoopItem *__restrict
     __shared__ int s_item, s_C, s_Cbb, s_widx, s_it, s_err, s_improved;
     __shared__ unsigned long long s_best, s_t0;
     __shared__ long long s_eval, s_work;
+    __shared__ long long s_tally[kTallies];   // work counters of the decodes (TallyRef)
     __shared__ int s_pub[2], s_pub_div[2];            // this CTA's best since its read, by parity
     // replicated bookkeeping: identical in every CTA of the cluster
     __shared__ int s_slotC[kMaxWorkingSet], s_slotPhi[kMaxWorkingSet], s_winner[kMaxWorkingSet];
@@ -231,6 +232,7 @@ __global__ void __launch_bounds__(512, 2) coop_kernel(const CoopItem *__restrict
         const int nslots = n > 3 ? (n - 3) * delta : 0;
         const unsigned dmagic = slot_magic(delta);
         const uint32_t *words = ci.words ? ci.words + static_cast<long long>(crank) * cfg.words_per_block : nullptr;
+        if (tid < kTallies) s_tally[tid] = 0;
         if (tid == 0) {
             s_t0 = global_timer_ns();
             s_eval = 0;
@@ -368,7 +370,8 @@ __global__ void __launch_bounds__(512, 2) coop_kernel(const CoopItem *__restrict
             if (tid == 0) s_best = ~0ull;
             const unsigned long long my_key =
                 best_admissible_key<G>(I, mode, W, pos, fsp, lpp, tc, moves, area, n, delta, nslots, dmagic,
-                                       move_cap, s_Cstar, 1, 0u, s_mq, &s_eval, my_work, err);
+                                       move_cap, s_Cstar, 1, 0u, s_mq, &s_eval, my_work, err,
+                                       Prefix{nullptr, 1, 0, 0}, TallyRef{s_tally, nullptr});
             const unsigned long long wk = warp_min_u64(my_key);
             if (wl == 0 && wk != ~0ull) atomicMin(&s_best, wk);
             __syncthreads();
@@ -507,10 +510,13 @@ __global__ void __launch_bounds__(512, 2) coop_kernel(const CoopItem *__restrict
         if (crank == 0 && tid == 0) {
             long long ev = s_eval, wsum = s_work;
             int e = s_err;
+            long long ta[kTallies];
+            for (int x = 0; x < kTallies; ++x) ta[x] = s_tally[x];
             for (int r = 1; r < B; ++r) {
                 ev += *cl.map_shared_rank(&s_eval, r);
                 wsum += *cl.map_shared_rank(&s_work, r);
                 e |= *cl.map_shared_rank(&s_err, r);
+                for (int x = 0; x < kTallies; ++x) ta[x] += *cl.map_shared_rank(&s_tally[x], r);
             }
             int32_t *st = out + 2 * n;
             st[kOutEvalLo] = static_cast<int32_t>(ev & 0xffffffffll);
@@ -519,6 +525,11 @@ __global__ void __launch_bounds__(512, 2) coop_kernel(const CoopItem *__restrict
             st[kOutWorkHi] = static_cast<int32_t>(wsum >> 32);
             st[kOutIters] = s_it * B;
             st[kOutIters0] = 0;
+            ta[kTallySteps] += wsum;                      // loop steps performed
+            for (int x = 0; x < kTallies; ++x) {
+                st[kOutPlacedLo + 2 * x] = static_cast<int32_t>(ta[x] & 0xffffffffll);
+                st[kOutPlacedLo + 2 * x + 1] = static_cast<int32_t>(ta[x] >> 32);
+            }
             st[kOutMode] = mode;
             st[kOutStatus] = e ? RCPSP_E_DEVICE : 0;
             const unsigned long long t1 = global_timer_ns();

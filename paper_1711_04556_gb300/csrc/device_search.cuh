@@ -64,6 +64,7 @@ struct SInst {
     const int *soff;
     const int *slist;
     int n, m, ub, wps, sum_cap;
+    int n_arcs, sum_used;
     uint32_t hi;     // high bit of every packed field
 };
 
@@ -85,6 +86,8 @@ __device__ SInst bind_instance(const int *sm, const InstHeader &h) {
     I.ub = h.ub;
     I.wps = h.wps;
     I.sum_cap = h.sum_cap;
+    I.n_arcs = h.n_arcs;
+    I.sum_used = h.sum_used;
     I.hi = h.lane_bits == 8 ? 0x80808080u : 0x80008000u;
     return I;
 }
@@ -135,13 +138,69 @@ __device__ __forceinline__ void clear_es(int *es, int n, int NG, bool active, co
 // Kept decoder states of the current list (prefix reuse, see prefix_count),
 // in the CTA's own global scratch (L2-resident, read and written past L1):
 // snapshot j (1..count) is the state before position j*K, at base +
-// (j-1)*stride: [0] frontier F, [1] makespan so far, [2] work so far, then
-// the profile (time-indexed: WPS planes of UB words; capacity-indexed: the
-// c_k) and the N earliest starts.  base == nullptr: no prefix reuse.
+// (j-1)*stride: the kPxMeta meta words, then the profile (time-indexed: WPS
+// planes of UB words; capacity-indexed: the c_k) and the N earliest starts.
+// base == nullptr: no prefix reuse.
 struct Prefix {
     int *base;
     int K, count, stride;
 };
+
+// Work counters of the decodes of a CTA (kTally* order; see rcpsp_stats):
+// `t` accumulates placements, Alg. 6 update steps or Eq. 7 reads, successor
+// pushes and kept-state words, and at kTallySteps the correction that turns
+// the work counter (which counts every neighbour in full) into the loop
+// steps performed: plus the producer's decodes, minus the steps restored
+// from kept states.  `hist` counts the neighbour decodes of the current
+// batch of moves by the kept state they restored (0: none).  t == nullptr:
+// no counting.
+struct TallyRef {
+    long long *t;
+    int *hist;
+};
+
+// Alg. 6 update steps (time-indexed: d_i) or Eq. 7 reads (capacity-indexed:
+// resources with r_{i,k} > 0) and successor pushes of the activities at
+// positions [p0, p1) of W, summed over the group; every lane of the warp
+// calls it.
+template <int G>
+__device__ __forceinline__ void position_sums(const SInst &I, const int *W, int p0, int p1, bool cap,
+                                              const Group<G> &g, int &upd, int &succ) {
+    int a_u = 0, a_s = 0;
+    for (int q = p0 + g.lane; q < p1; q += G) {
+        const int a = W[q];
+        if (cap) {
+            for (int k = 0; k < I.m; ++k) a_u += I.reqk[a * I.m + k] > 0 ? 1 : 0;
+        } else {
+            a_u += I.dur[a];
+        }
+        a_s += I.soff[a + 1] - I.soff[a];
+    }
+    upd = g.sum(a_u);
+    succ = g.sum(a_s);
+}
+
+// Keeps the meta words of snapshot j (lane 0 of the producing group): the
+// running sums of the positions before j*K -- those of [(j-1)K, jK) added to
+// snapshot j-1's -- and the words of the state.
+template <int G>
+__device__ __forceinline__ void keep_meta(const SInst &I, const int *W, const Prefix &px, int j, int *sn, bool cap,
+                                          int F, int cmax, int work, int words, bool active, const Group<G> &g) {
+    int upd, succ;
+    position_sums<G>(I, W, (j - 1) * px.K, j * px.K, cap, g, upd, succ);
+    if (active && g.lane == 0) {
+        if (j >= 2) {
+            upd += __ldcg(sn - px.stride + kPxUpd);
+            succ += __ldcg(sn - px.stride + kPxSucc);
+        }
+        __stcg(sn + kPxF, F);
+        __stcg(sn + kPxCmax, cmax);
+        __stcg(sn + kPxWork, work);
+        __stcg(sn + kPxUpd, upd);
+        __stcg(sn + kPxSucc, succ);
+        __stcg(sn + kPxWords, words);
+    }
+}
 
 // First position a neighbour decode of swap(u, v) must place itself.
 __device__ __forceinline__ int prefix_start(const Prefix &px, int u, bool produce) {
@@ -174,13 +233,14 @@ __device__ int decode_time(const SInst &I, const int *W, int u, int v, bool acti
         // start from the kept state of the current list before position p0
         const int *sn = px.base + (p0 / px.K - 1) * px.stride;
         if (active) {
-            F = __ldcg(sn);
-            cmax = __ldcg(sn + 1);
-            work += __ldcg(sn + 2);
+            F = __ldcg(sn + kPxF);
+            cmax = __ldcg(sn + kPxCmax);
+            work += __ldcg(sn + kPxWork);
 #pragma unroll
             for (int w = 0; w < WPS; ++w)
-                for (int t = g.lane; t < F; t += G) prof[(w * ubs + t) * NG] = __ldcg(sn + 4 + w * ubs + t);
-            for (int x = g.lane; x < n; x += G) esa[x * NG] = __ldcg(sn + 4 + WPS * ubs + x);
+                for (int t = g.lane; t < F; t += G)
+                    prof[(w * ubs + t) * NG] = __ldcg(sn + kPxMeta + w * ubs + t);
+            for (int x = g.lane; x < n; x += G) esa[x * NG] = __ldcg(sn + kPxMeta + WPS * ubs + x);
         }
         __syncwarp();
     } else {
@@ -197,14 +257,10 @@ __device__ int decode_time(const SInst &I, const int *W, int u, int v, bool acti
 #pragma unroll
                 for (int w = 0; w < WPS; ++w)
                     for (int t = g.lane; t < F; t += G)
-                        __stcg(sn + 4 + w * ubs + t, static_cast<int>(prof[(w * ubs + t) * NG]));
-                for (int x = g.lane; x < n; x += G) __stcg(sn + 4 + WPS * ubs + x, esa[x * NG]);
-                if (g.lane == 0) {
-                    __stcg(sn, F);
-                    __stcg(sn + 1, cmax);
-                    __stcg(sn + 2, work);
-                }
+                        __stcg(sn + kPxMeta + w * ubs + t, static_cast<int>(prof[(w * ubs + t) * NG]));
+                for (int x = g.lane; x < n; x += G) __stcg(sn + kPxMeta + WPS * ubs + x, esa[x * NG]);
             }
+            keep_meta<G>(I, W, px, p / px.K, sn, false, F, cmax, work, kPxMeta + WPS * F + n, active, g);
             __syncwarp();
         }
         const int inext = activity_at<G>(W, p + 1 < n ? p + 1 : p, u, v);
@@ -321,10 +377,10 @@ __device__ int decode_capacity(const SInst &I, const int *W, int u, int v, bool 
         // start from the kept state of the current list before position p0
         const int *sn = px.base + (p0 / px.K - 1) * px.stride;
         if (active) {
-            cmax = __ldcg(sn + 1);
-            if (g.lane == 0) wk = __ldcg(sn + 2);
-            for (int j = g.lane; j < sc; j += G) cst[j * NG] = __ldcg(sn + 4 + j);
-            for (int x = g.lane; x < n; x += G) esa[x * NG] = __ldcg(sn + 4 + sc + x);
+            cmax = __ldcg(sn + kPxCmax);
+            if (g.lane == 0) wk = __ldcg(sn + kPxWork);
+            for (int j = g.lane; j < sc; j += G) cst[j * NG] = __ldcg(sn + kPxMeta + j);
+            for (int x = g.lane; x < n; x += G) esa[x * NG] = __ldcg(sn + kPxMeta + sc + x);
         }
         __syncwarp();
     } else {
@@ -341,14 +397,10 @@ __device__ int decode_capacity(const SInst &I, const int *W, int u, int v, bool 
             int *sn = px.base + (p / px.K - 1) * px.stride;
             const int wsum = g.sum(wk);
             if (active) {
-                for (int j = g.lane; j < sc; j += G) __stcg(sn + 4 + j, cst[j * NG]);
-                for (int x = g.lane; x < n; x += G) __stcg(sn + 4 + sc + x, esa[x * NG]);
-                if (g.lane == 0) {
-                    __stcg(sn, 0);
-                    __stcg(sn + 1, cmax);
-                    __stcg(sn + 2, wsum);
-                }
+                for (int j = g.lane; j < sc; j += G) __stcg(sn + kPxMeta + j, cst[j * NG]);
+                for (int x = g.lane; x < n; x += G) __stcg(sn + kPxMeta + sc + x, esa[x * NG]);
             }
+            keep_meta<G>(I, W, px, p / px.K, sn, true, 0, cmax, wsum, kPxMeta + sc + n, active, g);
             __syncwarp();
         }
         const int inext = activity_at<G>(W, p + 1 < n ? p + 1 : p, u, v);
@@ -489,7 +541,8 @@ __device__ __forceinline__ void tc_put(unsigned *tc, int u, int v, int delta, bo
 // thread's smallest key (C_max << 32 | u << 16 | v) among admissible moves
 // -- not tabu, or C_max < aspiration -- or ~0 when it saw none.  Thread 0
 // adds the number of decoded neighbours to *s_eval; every thread adds its
-// decode work to my_work.  Starts and ends with a __syncthreads, so the
+// decode work to my_work; with tally.t, warp 0 adds the work counters of
+// the decodes (see TallyRef) once per batch of moves.  Starts and ends with a __syncthreads, so the
 // caller may reset its reduction word before the call.
 // ---------------------------------------------------------------------------
 template <int G, bool PFX = false>
@@ -497,7 +550,7 @@ __device__ __forceinline__ unsigned long long best_admissible_key(
         const SInst &I, int mode, const int *W, const int *pos, int *fsp, int *lpp, const unsigned *tc,
         int *moves, int *area, int n, int delta, int nslots, unsigned dmagic, int move_cap, int aspiration,
         int csize, unsigned crank, int *s_mq, long long *s_eval, long long &my_work, int &err,
-        const Prefix &px = Prefix{nullptr, 1, 0, 0}) {
+        const Prefix &px = Prefix{nullptr, 1, 0, 0}, TallyRef tally = TallyRef{nullptr, nullptr}) {
     constexpr int NG = 32 / G;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int warp = tid >> 5, wl = tid & 31;
@@ -513,11 +566,27 @@ __device__ __forceinline__ unsigned long long best_admissible_key(
         fsp[p] = f;
         lpp[p] = l;
     }
-    if (PFX && warp == 0) {
+    const int upd_all = mode == RCPSP_EVAL_CAPACITY ? I.sum_used : I.ub;
+    if (PFX && px.base && warp == 0) {
         // prefix reuse: one group decodes the current list and keeps its
         // state before positions K, 2K, ... (its work is not a neighbour's)
         long long w0 = 0;
         decode<G, PFX>(I, mode, W, 0, 0, gw == 0, area, NG, g, w0, err, nullptr, px, true);
+        if (tally.t) {
+            // a full decode, and the kept states it wrote
+            __syncwarp();
+            int kw = 0;
+            for (int j = 1 + wl; j <= px.count; j += 32) kw += __ldcg(px.base + (j - 1) * px.stride + kPxWords);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) kw += __shfl_xor_sync(kFull, kw, o);
+            if (wl == 0) {
+                tally.t[kTallyPlaced] += n;
+                tally.t[kTallyUpd] += upd_all;
+                tally.t[kTallySucc] += I.n_arcs;
+                tally.t[kTallyKept] += kw;
+                tally.t[kTallySteps] += w0;
+            }
+        }
     }
     __syncthreads();
     unsigned long long my_key = ~0ull;
@@ -565,6 +634,7 @@ __device__ __forceinline__ unsigned long long best_admissible_key(
             const int code = act ? moves[q] : 0;
             const int u = code & 0xffff, v = code >> 16;
             const int c = decode<G, PFX>(I, mode, W, u, v, act, area, NG, g, my_work, err, nullptr, px);
+            if (PFX && px.base && tally.t && act && g.lane == 0) atomicAdd(&tally.hist[::min(u / px.K, px.count)], 1);
             if (act && (!tc_get(tc, u, v, delta) || c < aspiration)) {
                 const unsigned long long key =
                     (static_cast<unsigned long long>(c) << 32) | static_cast<unsigned>(code & 0xffff) << 16 |
@@ -574,6 +644,38 @@ __device__ __forceinline__ unsigned long long best_admissible_key(
         }
         if (tid == 0) *s_eval += nm;
         __syncthreads();
+        if (tally.t && warp == 0) {
+            // the batch's neighbour decodes: full ones, and those that
+            // restored kept state j before position j*K (hist[j])
+            long long v[kTallies] = {0, 0, 0, 0, 0};
+            if (PFX && px.base) {
+                for (int j = wl; j <= px.count; j += 32) {
+                    const long long c = tally.hist[j];
+                    tally.hist[j] = 0;
+                    if (c == 0) continue;
+                    if (j == 0) {
+                        v[kTallyPlaced] += c * n;
+                        v[kTallyUpd] += c * upd_all;
+                        v[kTallySucc] += c * I.n_arcs;
+                    } else {
+                        const int *sn = px.base + (j - 1) * px.stride;
+                        v[kTallyPlaced] += c * (n - j * px.K);
+                        v[kTallyUpd] += c * (upd_all - __ldcg(sn + kPxUpd));
+                        v[kTallySucc] += c * (I.n_arcs - __ldcg(sn + kPxSucc));
+                        v[kTallyKept] += c * __ldcg(sn + kPxWords);
+                        v[kTallySteps] -= c * __ldcg(sn + kPxWork);
+                    }
+                }
+#pragma unroll
+                for (int x = 0; x < kTallies; ++x) v[x] = warp_sum_i64(v[x]);
+            } else {
+                v[kTallyPlaced] = static_cast<long long>(nm) * n;
+                v[kTallyUpd] = static_cast<long long>(nm) * upd_all;
+                v[kTallySucc] = static_cast<long long>(nm) * I.n_arcs;
+            }
+            if (wl == 0)
+                for (int x = 0; x < kTallies; ++x) tally.t[x] += v[x];
+        }
     }
     return my_key;
 }

@@ -171,6 +171,8 @@ int prepare_instance(const rcpsp_instance &in, PackedInstance &out, std::string 
     h.lane_bits = lane_bits;
     h.sum_cap = 0;
     for (int k = 0; k < m; ++k) h.sum_cap += in.cap[k];
+    h.sum_used = 0;
+    for (int i = 0; i < n * m; ++i) h.sum_used += in.req[i] > 0 ? 1 : 0;
     h.n_arcs = E;
     const InstLayout L = inst_layout(n, m, wps, E);
     h.inst_words = L.words;

@@ -18,7 +18,7 @@
 
 namespace rcpsp {
 
-constexpr int kDefaultMoveCap = 2048;   // potential moves examined per stripe
+constexpr int kDefaultMoveCap = 1024;   // feasible moves one batch of decodes holds
 constexpr int kSearchMaxWarps = 16;     // largest search CTA (512 threads)
 constexpr int kSearchNarrowThreads = 384;   // CTAs up to this size run the 384-thread build of the kernel
 
@@ -32,7 +32,8 @@ struct InstHeader {
     int32_t n_arcs;             // |E|
     int32_t inst_words;         // words of the shared-memory section
     int32_t record_words;       // inst_words + initial list, multiple of 4
-    int32_t pad[5];
+    int32_t sum_used;           // number of (activity, resource) pairs with r_{i,k} > 0
+    int32_t pad[4];
 };
 static_assert(sizeof(InstHeader) == 64, "InstHeader is 64 bytes");
 
@@ -88,8 +89,20 @@ enum : int {
     kOutIters, kOutCmax, kOutMode, kOutStatus,
     kOutT0Lo, kOutT0Hi, kOutT1Lo, kOutT1Hi,
     kOutIters0,                 // iterations before the call (a resumed search)
+    // work the decodes of this call performed (positions restored from a
+    // kept state excluded; see TallyRef)
+    kOutPlacedLo, kOutPlacedHi, kOutStepsLo, kOutStepsHi, kOutUpdLo, kOutUpdHi,
+    kOutSuccLo, kOutSuccHi, kOutKeptLo, kOutKeptHi,
     kOutStats
 };
+
+// Work counters of the decodes, in the order of the kOutPlaced.. words:
+// activities placed, Alg. 5 (time-indexed) or Alg. 4 (capacity-indexed)
+// loop steps of those placements, their Alg. 6 update steps (sum of d_i,
+// time-indexed) or Eq. 7 reads (used resources, capacity-indexed),
+// successor pushes (|succ(i)| per placement), and 32-bit words of kept
+// decoder states written and read (prefix reuse).
+enum : int { kTallyPlaced = 0, kTallySteps, kTallyUpd, kTallySucc, kTallyKept, kTallies };
 
 RC_HD int align4(int x) { return (x + 3) & ~3; }
 
@@ -130,12 +143,15 @@ RC_HD int profile_words(int mode, int wps, int ub, int sum_cap) {
 
 // Prefix reuse: a swap (u, v) leaves list positions below u as they are, so
 // a neighbour's decode may start from the decoder state of the current list
-// before position floor(u/K)*K.  These states -- frontier, makespan so far,
-// work so far, the profile (or capacity state) and the earliest starts --
-// are kept before positions K, 2K, ..., count*K < N, in a global scratch
-// region of each CTA.
+// before position floor(u/K)*K.  These states -- a meta block, the profile
+// (or capacity state) and the earliest starts -- are kept before positions
+// K, 2K, ..., count*K < N, in a global scratch region of each CTA.  Meta
+// words: frontier F, makespan so far, work so far, the Alg. 6 update steps
+// (or Eq. 7 reads) and successor pushes of the positions before, and the
+// words of this state.
+enum : int { kPxF = 0, kPxCmax, kPxWork, kPxUpd, kPxSucc, kPxWords, kPxMeta = 8 };
 RC_HD int prefix_count(int n, int K) { return K > 0 ? (n - 1) / K : 0; }
-RC_HD int prefix_stride(int n, int prof_words) { return align4(4 + prof_words + n); }
+RC_HD int prefix_stride(int n, int prof_words) { return align4(kPxMeta + prof_words + n); }
 RC_HD int prefix_words(int n, int prof_words, int K) { return prefix_count(n, K) * prefix_stride(n, prof_words); }
 
 RC_HD StateLayout state_layout(int inst_words, int n, int tabu_len, int delta, int move_cap,

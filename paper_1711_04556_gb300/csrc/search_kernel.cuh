@@ -54,6 +54,8 @@ __global__ void __launch_bounds__(NT, 2) search_kernel(const LaunchItem *__restr
     __shared__ int s_item, s_C, s_Cbest, s_widx, s_it, s_improved, s_err, s_it0, s_it_end;
     __shared__ unsigned long long s_bestp[2], s_t0;      // best key of the iteration, by parity
     __shared__ long long s_eval, s_work;
+    __shared__ long long s_tally[kTallies];   // work counters of the decodes (TallyRef)
+    __shared__ int s_hist[32];
     const unsigned crank = csize > 1 ? cg::this_cluster().block_rank() : 0u;
 
     constexpr int NG = 32 / G;
@@ -109,6 +111,8 @@ __global__ void __launch_bounds__(NT, 2) search_kernel(const LaunchItem *__restr
             }
             for (int x = tid; x < tl; x += nthr) stl[x] = sv[CL.stl + x];
             for (int x = tid; x < tcw; x += nthr) tc[x] = static_cast<unsigned>(sv[CL.tc + x]);
+            if (tid < kTallies) s_tally[tid] = 0;
+            if (tid < 32) s_hist[tid] = 0;
             if (tid == 0) {
                 s_t0 = global_timer_ns();
                 s_widx = sv[kCkWidx];
@@ -136,6 +140,8 @@ __global__ void __launch_bounds__(NT, 2) search_kernel(const LaunchItem *__restr
             }
             for (int x = tid; x < tl; x += nthr) stl[x] = 0;             // (0,0) = empty move
             for (int x = tid; x < tcw; x += nthr) tc[x] = 0u;
+            if (tid < kTallies) s_tally[tid] = 0;
+            if (tid < 32) s_hist[tid] = 0;
             if (tid == 0) {
                 s_t0 = global_timer_ns();
                 s_widx = 0;
@@ -167,7 +173,8 @@ __global__ void __launch_bounds__(NT, 2) search_kernel(const LaunchItem *__restr
             if (tid == 0) s_bestp[par] = ~0ull;
             const unsigned long long my_key =
                 best_admissible_key<G, PFX>(I, mode, W, pos, fsp, lpp, tc, moves, area, n, delta, nslots, dmagic,
-                                       move_cap, s_Cbest, csize, crank, s_mq, &s_eval, my_work, err, px);
+                                       move_cap, s_Cbest, csize, crank, s_mq, &s_eval, my_work, err, px,
+                                       TallyRef{s_tally, s_hist});
             // 4. best admissible move of the block, then of the cluster
             const unsigned long long wk = warp_min_u64(my_key);
             if (wl == 0 && wk != ~0ull) atomicMin(&s_bestp[par], wk);
@@ -228,6 +235,7 @@ __global__ void __launch_bounds__(NT, 2) search_kernel(const LaunchItem *__restr
                     s_eval += *cg::this_cluster().map_shared_rank(&s_eval, r);
                     s_work += *cg::this_cluster().map_shared_rank(&s_work, r);
                     s_err |= *cg::this_cluster().map_shared_rank(&s_err, r);
+                    for (int x = 0; x < kTallies; ++x) s_tally[x] += *cg::this_cluster().map_shared_rank(&s_tally[x], r);
                 }
             __syncthreads();
         }
@@ -255,6 +263,12 @@ __global__ void __launch_bounds__(NT, 2) search_kernel(const LaunchItem *__restr
             st[kOutWorkHi] = static_cast<int32_t>(s_work >> 32);
             st[kOutIters] = s_it;
             st[kOutIters0] = s_it0;
+            for (int x = 0; x < kTallies; ++x) {
+                // loop steps performed = the work counter plus its correction
+                const long long t = x == kTallySteps ? s_work + s_tally[x] : s_tally[x];
+                st[kOutPlacedLo + 2 * x] = static_cast<int32_t>(t & 0xffffffffll);
+                st[kOutPlacedLo + 2 * x + 1] = static_cast<int32_t>(t >> 32);
+            }
             st[kOutMode] = mode;
             st[kOutStatus] = s_err ? RCPSP_E_DEVICE : 0;
             const unsigned long long t1 = global_timer_ns();

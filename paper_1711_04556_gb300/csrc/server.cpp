@@ -41,8 +41,11 @@
 #include "../../include/rcpsp.h"
 #include "host_prep.h"
 
+#include "kernels.h"
+
 namespace rcpsp {
 int ctx_search_done(rcpsp_ctx *c);
+int ctx_reserve(rcpsp_ctx *c, size_t staging_bytes, int plan_items);
 }
 
 namespace {
@@ -363,6 +366,7 @@ int rcpsp_server_create(rcpsp_server **out, int device, const rcpsp_server_confi
         if (cfg->memory_budget > 0) s->cfg.memory_budget = cfg->memory_budget;
         if (cfg->poll_us > 0) s->cfg.poll_us = cfg->poll_us;
         if (cfg->slice_iterations > 0) s->cfg.slice_iterations = cfg->slice_iterations;
+        if (cfg->max_pending > 0) s->cfg.max_pending = cfg->max_pending;
     }
     if (cudaSetDevice(device) != cudaSuccess) {
         delete s;
@@ -391,10 +395,32 @@ int rcpsp_server_create(rcpsp_server **out, int device, const rcpsp_server_confi
         sl.mem.stream = sl.stream;
         sl.mem.pool = s->pool;
         s->allocs[k] = rcpsp_allocator{slot_alloc, slot_release, &sl.mem};
-        const int rc = rcpsp_create(&sl.ctx, device, &s->allocs[k]);
+        int rc = rcpsp_create(&sl.ctx, device, &s->allocs[k]);
+        // pinned staging and launch plan for a full batch of the largest
+        // instances (N up to RCPSP_MAX_N, M up to 8: records of at most a few
+        // tens of KB), so that admission never waits on cudaMallocHost
+        if (rc == RCPSP_OK) rc = rcpsp::ctx_reserve(sl.ctx, size_t(8) << 20, std::min(s->cfg.max_batch, 256));
         if (rc != RCPSP_OK) {
             rcpsp_server_destroy(s);
             return rc;
+        }
+    }
+    // map the memory budget in the pool once (it stays mapped: the release
+    // threshold is the budget), and load the search kernels of every group
+    // size with the device's shared-memory limit
+    {
+        cudaDeviceProp prop{};
+        void *p = nullptr;
+        cudaError_t e = cudaGetDeviceProperties(&prop, device);
+        if (e == cudaSuccess)
+            e = cudaMallocFromPoolAsync(&p, static_cast<size_t>(s->cfg.memory_budget), s->pool, s->slots[0].stream);
+        if (e == cudaSuccess) e = cudaFreeAsync(p, s->slots[0].stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->slots[0].stream);
+        const size_t smem_limit = prop.sharedMemPerBlockOptin > 1024 ? prop.sharedMemPerBlockOptin - 1024 : 0;
+        for (int G = 1; G <= 32 && e == cudaSuccess; G *= 2) e = rcpsp::prepare_search(G, smem_limit);
+        if (e != cudaSuccess) {
+            rcpsp_server_destroy(s);
+            return RCPSP_E_CUDA;
         }
     }
     s->worker = std::thread(run, s);
@@ -428,6 +454,16 @@ int rcpsp_server_submit(rcpsp_server *s, const rcpsp_instance *inst, const rcpsp
         s->st.rejected++;
         s->err = msg;
         return rc;
+    }
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        int64_t waiting = 0;
+        for (const auto &q : s->pending) waiting += static_cast<int64_t>(q.size());
+        if (s->cfg.max_pending > 0 && waiting >= s->cfg.max_pending) {
+            s->st.rejected++;
+            s->err = "pending queue full";
+            return RCPSP_E_TOO_LARGE;
+        }
     }
     Request r;
     r.tag = tag;

@@ -24,7 +24,7 @@ EXPORTS = ("rcpsp_create", "rcpsp_destroy", "rcpsp_load_instances", "rcpsp_free_
            "rcpsp_tabu_search", "rcpsp_tabu_search_noalloc", "rcpsp_coop_search", "rcpsp_autotune",
            "rcpsp_get_schedules", "rcpsp_get_trace", "rcpsp_evaluate_lists",
            "rcpsp_prepare_instance", "rcpsp_transfer_bytes", "rcpsp_kernel_launches", "rcpsp_get_state",
-           "rcpsp_set_state", "rcpsp_server_create", "rcpsp_server_destroy",
+           "rcpsp_set_state", "rcpsp_measure_peaks", "rcpsp_last_launches", "rcpsp_server_create", "rcpsp_server_destroy",
            "rcpsp_server_submit", "rcpsp_server_poll", "rcpsp_server_get_stats", "rcpsp_last_error")
 
 
@@ -57,18 +57,33 @@ class CoopParams(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("evaluated", C.c_int64), ("work", C.c_int64), ("iterations", C.c_int32),
                 ("eval_mode", C.c_int32), ("critical_path", C.c_int32), ("status", C.c_int32),
-                ("t_start_ns", C.c_int64), ("t_end_ns", C.c_int64)]
+                ("t_start_ns", C.c_int64), ("t_end_ns", C.c_int64), ("placements", C.c_int64),
+                ("steps_done", C.c_int64), ("update_units", C.c_int64), ("succ_pushes", C.c_int64),
+                ("kept_words", C.c_int64)]
 
 
 # numpy image of rcpsp_stats, for reading many at once
 _STATS_DTYPE = np.dtype([("evaluated", "<i8"), ("work", "<i8"), ("iterations", "<i4"), ("eval_mode", "<i4"),
-                         ("critical_path", "<i4"), ("status", "<i4"), ("t_start_ns", "<i8"), ("t_end_ns", "<i8")])
+                         ("critical_path", "<i4"), ("status", "<i4"), ("t_start_ns", "<i8"), ("t_end_ns", "<i8"),
+                         ("placements", "<i8"), ("steps_done", "<i8"), ("update_units", "<i8"),
+                         ("succ_pushes", "<i8"), ("kept_words", "<i8")])
 assert _STATS_DTYPE.itemsize == C.sizeof(Stats)
+
+
+class LaunchInfo(C.Structure):
+    _fields_ = [("searches", C.c_int32), ("group_size", C.c_int32), ("warps", C.c_int32),
+                ("cluster_size", C.c_int32), ("ctas", C.c_int32), ("prefix_reuse", C.c_int32),
+                ("shape_source", C.c_int32), ("reserved", C.c_int32), ("smem_bytes", C.c_int64)]
+
+
+class Peaks(C.Structure):
+    _fields_ = [("int32_ops_per_s", C.c_double), ("smem_bytes_per_s", C.c_double), ("int32_ms", C.c_double),
+                ("smem_ms", C.c_double), ("sms", C.c_int32)]
 
 
 class ServerConfig(C.Structure):
     _fields_ = [("slots", C.c_int32), ("max_batch", C.c_int32), ("memory_budget", C.c_int64),
-                ("poll_us", C.c_int32), ("slice_iterations", C.c_int32)]
+                ("poll_us", C.c_int32), ("slice_iterations", C.c_int32), ("max_pending", C.c_int32)]
 
 
 class Completion(C.Structure):
@@ -126,6 +141,8 @@ def library(path: Optional[str] = None):
                                              P(C.c_int32), C.c_char_p, C.c_int32]),
         "rcpsp_transfer_bytes": (C.c_int, [C.c_void_p, P(C.c_int64), P(C.c_int64)]),
         "rcpsp_kernel_launches": (C.c_int, [C.c_void_p, P(C.c_int64)]),
+        "rcpsp_measure_peaks": (C.c_int, [C.c_int, P(Peaks)]),
+        "rcpsp_last_launches": (C.c_int, [C.c_void_p, P(LaunchInfo), C.c_int32, P(C.c_int32)]),
         "rcpsp_get_state": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_size_t, P(C.c_size_t)]),
         "rcpsp_set_state": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_size_t]),
         "rcpsp_server_create": (C.c_int, [P(C.c_void_p), C.c_int, P(ServerConfig)]),
@@ -212,6 +229,16 @@ def _torch_allocator():
             torch.cuda.caching_allocator_delete(ptr)
 
     return ALLOC_FN(alloc), FREE_FN(release)
+
+
+def measure_peaks(device: int = 0, lib_path: Optional[str] = None) -> dict:
+    """rcpsp_measure_peaks: the measured integer-ALU and shared-memory ceilings."""
+    lib = library(lib_path)
+    pk = Peaks()
+    rc = lib.rcpsp_measure_peaks(device, C.byref(pk))
+    if rc != 0:
+        raise RcpspError(rc, "rcpsp_measure_peaks failed")
+    return {f: getattr(pk, f) for f, _ in Peaks._fields_}
 
 
 def prepare(inst, level_key=None, lib_path: Optional[str] = None) -> dict:
@@ -357,9 +384,10 @@ class Solver:
         cm = cmax.tolist()
         out, at = [], 0
         for k, n in enumerate(ns):
-            ev, wk, it, md, cp, stt, t0, t1 = (c[k] for c in cols)
+            ev, wk, it, md, cp, stt, t0, t1, pl, sd, ud, sp, kw = (c[k] for c in cols)
             out.append(dict(best_W=order[at:at + n], best_S=start[at:at + n], best_cmax=cm[k], evaluated=ev,
-                            work=wk, iterations=it, mode=md, cp=cp, status=stt, t_start_ns=t0, t_end_ns=t1))
+                            work=wk, iterations=it, mode=md, cp=cp, status=stt, t_start_ns=t0, t_end_ns=t1,
+                            placements=pl, steps_done=sd, update_units=ud, succ_pushes=sp, kept_words=kw))
             at += n
         return out
 
@@ -380,6 +408,13 @@ class Solver:
         """rcpsp_set_state: give instance `id_` a kept state (from get_state)."""
         buf = C.create_string_buffer(state, len(state))
         self._check(self.lib.rcpsp_set_state(self.ctx, int(id_), buf, len(state)))
+
+    def last_launches(self) -> List[dict]:
+        """rcpsp_last_launches: the launch classes of the last search call."""
+        buf = (LaunchInfo * 16)()
+        cnt = C.c_int32(0)
+        self._check(self.lib.rcpsp_last_launches(self.ctx, buf, 16, C.byref(cnt)))
+        return [{f: getattr(buf[k], f) for f, _ in LaunchInfo._fields_} for k in range(min(cnt.value, 16))]
 
     def kernel_launches(self) -> int:
         n = C.c_int64(0)
@@ -409,22 +444,29 @@ class Server:
     """Continuous-batching solve server (rcpsp_server_* in include/rcpsp.h)."""
 
     def __init__(self, device: int = 0, slots: int = 8, max_batch: int = 256, memory_budget: int = 1 << 30,
-                 poll_us: int = 100, lib_path: Optional[str] = None, slice_iterations: int = 0):
+                 poll_us: int = 100, lib_path: Optional[str] = None, slice_iterations: int = 0,
+                 max_pending: int = 0):
         self.lib = library(lib_path)
         self.srv = C.c_void_p()
-        cfg = ServerConfig(slots, max_batch, memory_budget, poll_us, slice_iterations)
+        cfg = ServerConfig(slots, max_batch, memory_budget, poll_us, slice_iterations, max_pending)
         rc = self.lib.rcpsp_server_create(C.byref(self.srv), device, C.byref(cfg))
         if rc != 0:
             raise RcpspError(rc, "server create")
+        self.max_pending = max_pending
         self._buf = (Completion * 4096)()
 
     def submit(self, inst, tag: int, iterations: int = 1000, delta: int = 0, tabu_len: int = 0,
-               mode: int = EVAL_AUTO, stop_at_cp: bool = True, level_key=None) -> None:
+               mode: int = EVAL_AUTO, stop_at_cp: bool = True, level_key=None) -> bool:
+        """Queues one request; False when the server's pending queue is full
+        (max_pending), an error for anything else."""
         m = _Marshalled(inst, level_key)
         p = Params(iterations, delta, tabu_len, mode, int(stop_at_cp), 0, 0, 0, 0, 0)
         rc = self.lib.rcpsp_server_submit(self.srv, C.byref(m.s), C.byref(p), int(tag))
+        if rc == E_TOO_LARGE and self.max_pending > 0:
+            return False
         if rc != 0:
             raise RcpspError(rc, "submit")
+        return True
 
     def poll(self, wait_ms: int = 0, capacity: int = 4096) -> List[dict]:
         cnt = C.c_int32(0)

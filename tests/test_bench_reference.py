@@ -10,7 +10,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def test_reference_arm_prints_one_line():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                        "--warmup", "3", "--reference-sample", "4", "--iterations", "50"],
+                        "--warmup", "3", "--reference-sample", "4", "--reference-iterations", "5"],
                        capture_output=True, text=True, timeout=600, cwd=ROOT)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.strip()]
@@ -20,21 +20,18 @@ def test_reference_arm_prints_one_line():
     assert d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 3
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
-    assert d["config"]["iterations"] == 50 and "j30_batch" in d["config"]["workload"]
+    assert d["config"]["iterations"] == 1000 and d["config"]["workload"].startswith("mixed_batch")
+    assert d["config"]["reference_sample"] == 4 and d["config"]["reference_iterations"] == 5
 
 
 def test_committed_counters_match_the_kernel_source():
-    """The ncu figures the bench line quotes (DRAM traffic, shared-memory
-    wavefronts) are used only while the kernel source is the one captured;
-    after a change of the kernel they read as null until it is captured
-    again."""
+    """The ncu DRAM figures the bench line quotes are used only while the
+    kernel source is the one captured; after a change of the kernel they
+    read as null until it is captured again."""
     import pytest
     sys.path.insert(0, ROOT)
     import bench
     c = bench.load_counters()
     if c is None:
-        pytest.skip("the kernel changed since its ncu capture: the bench line reports no counters")
-    assert c["dram_bytes_per_launch"] > 0 and c["smem_wavefronts_per_launch"] > 0
-    s = bench.smem_roofline(c, 0.0407, 152, 2070.0)
-    assert abs(s["frac"] - c["smem_wavefronts_per_launch"] / 0.0407 / (152 * 2070e6)) < 1e-12
-    assert 0 < s["frac"] < 1
+        pytest.skip("the kernel changed since its ncu capture: the bench line reports no DRAM traffic")
+    assert c["dram_bytes_per_launch"] > 0

@@ -1,0 +1,63 @@
+"""GPU parity on the paths the full workloads take, bit-exact against the
+CPU reference: searches long enough to wrap the 800-entry tabu list and its
+banded cache (Sec. 4.5, Algs. 2-3), the largest instances of the uneven
+batch (N = 302, M = 8, durations up to 50), and precedence graphs with arcs
+that skip layers."""
+import os
+
+import pytest
+
+from paper_1711_04556_gb300 import instances as I
+from paper_1711_04556_gb300 import rcpsp as R
+from skip_arc_instances import skip_arc_batch, with_skip_arcs
+from test_gpu_parity import compare_search
+
+pytestmark = pytest.mark.gpu
+
+NPROC = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module")
+def solver():
+    from paper_1711_04556_gb300 import build as B
+    B.build()
+    s = R.Solver(0)
+    yield s
+    s.close()
+
+
+def run_and_compare(solver, oracle, insts, iterations, delta, tabu_len, mode, **kw):
+    ids = solver.load(insts)
+    solver.search(ids, iterations=iterations, delta=delta, tabu_len=tabu_len, mode=mode, trace=True, **kw)
+    got = solver.results(ids)
+    params = [(iterations, delta or I.search_params(x.n - 2)[0], tabu_len or I.search_params(x.n - 2)[1], mode, 1)
+              for x in insts]
+    ref = oracle.tabu_search_batch(insts, params, NPROC, trace=True)
+    for k, (g, r) in enumerate(zip(got, ref)):
+        compare_search(oracle, g, r, solver.trace(ids[k], g["iterations"]))
+    solver.free(ids)
+    return got
+
+
+@pytest.mark.parametrize("mode", [R.EVAL_TIME, R.EVAL_CAPACITY])
+def test_j120_long_search_wraps_the_tabu_list(solver, oracle, mode):
+    insts = I.config_batch("j120_batch", 16, first=300)
+    got = run_and_compare(solver, oracle, insts, 1200, 60, 800, mode)
+    # most searches run past 800 iterations: the tabu ring and its cache evict
+    assert sum(g["iterations"] > 800 for g in got) >= 8
+
+
+@pytest.mark.parametrize("mode", [R.EVAL_TIME, R.EVAL_CAPACITY])
+def test_largest_uneven_instances(solver, oracle, mode):
+    insts = [x for x in I.config_batch("mixed_batch", 160) if x.n == 302 and x.m == 8][:3]
+    assert len(insts) == 3 and all(int(x.dur.max()) > 40 for x in insts)
+    got = run_and_compare(solver, oracle, insts, 200, 0, 0, mode)
+    assert sum(g["iterations"] == 200 for g in got) >= 2      # a search may stop early at the bound
+
+
+@pytest.mark.parametrize("mode", [R.EVAL_AUTO, R.EVAL_TIME, R.EVAL_CAPACITY])
+def test_layer_skipping_arcs(solver, oracle, mode):
+    small = skip_arc_batch(24)
+    run_and_compare(solver, oracle, small, 300, 20, 60, mode)
+    large = [with_skip_arcs(s, 120, 4, 180, 20, extra=40, relabel=bool(s % 2)) for s in range(4)]
+    run_and_compare(solver, oracle, large, 150, 60, 800, mode)

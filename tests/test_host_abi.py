@@ -129,7 +129,8 @@ def test_binding_structs_match_the_header(tmp_path):
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     mirrors = {"rcpsp_instance": R.Instance, "rcpsp_params": R.Params, "rcpsp_coop_params": R.CoopParams,
                "rcpsp_stats": R.Stats, "rcpsp_allocator": R.Allocator, "rcpsp_server_config": R.ServerConfig,
-               "rcpsp_completion": R.Completion, "rcpsp_server_stats": R.ServerStats}
+               "rcpsp_completion": R.Completion, "rcpsp_server_stats": R.ServerStats, "rcpsp_peaks": R.Peaks,
+               "rcpsp_launch_info": R.LaunchInfo}
     lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "rcpsp.h"', 'int main(void) {']
     for cname, py in mirrors.items():
         lines.append(f'    printf("{cname} sizeof %zu\\n", sizeof({cname}));')
