@@ -177,12 +177,16 @@ int rcpsp_free_instances(rcpsp_ctx *ctx, const int32_t *ids, int32_t count);
  * moves with Eqs. 5-6 filtering, serial-SGS decoding with the chosen
  * evaluator, best admissible move under the simple tabu list (Algs. 2-3)
  * and the aspiration rule).  The searches are grouped into launch classes
- * by footprint (per-group scratch up to 2K, up to 8K, above 8K words) and
+ * by footprint (per-group scratch up to 512, 2K, 8K, above 8K words) and
  * size (N up to 64, up to 160, larger); each class is one persistent launch
  * with its own shape -- lanes per decode, warps per CTA, CTAs per search --
  * the first on `cuda_stream` (a cudaStream_t; NULL = legacy default stream),
  * the others on streams of the context forked from it and joined back into
- * it.  A class whose iterations take several decode rounds per CTA keeps
+ * it, classes of more estimated work first.  With cluster_size = 0, a class
+ * of one CTA per search whose neighbourhoods mostly fit one decode round
+ * gives its few outliers (at most 1/16 of the class, initial list with more
+ * feasible swaps than the CTA has decoding groups) a launch of their own
+ * with clusters of 2-8 CTAs, started first.  A class whose iterations take several decode rounds per CTA keeps
  * the decoder state of the current list every K positions and starts each
  * neighbour's decode from the last state before its first swapped position
  * (prefix reuse; results and counts are those of full decodes).  The call

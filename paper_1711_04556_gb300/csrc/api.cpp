@@ -46,6 +46,8 @@ struct Inst {
     int trace_iters = -1;    // iterations recorded by the last traced search, -1 = none
     bool alive = false;
     std::vector<int32_t> succ_off, succ;   // host copy of the arcs, to check caller lists
+    std::vector<int32_t> w0;               // host copy of the initial list
+    int feas_delta = -1, feas0 = 0;        // feasible swaps of w0 at that swap distance
     int32_t *ckpt = nullptr;               // kept search state (CkptLayout), device
     size_t ckpt_bytes = 0;
     bool ckpt_valid = false;               // holds a state for the parameters below
@@ -62,8 +64,9 @@ struct HostRange {
     HostRange &operator=(const HostRange &) = delete;
 };
 
-constexpr int kClasses = 9;                  // launch classes of one call (see footprint_class)
-constexpr int kAuxStreams = kClasses - 1;
+constexpr int kClasses = rcpsp::kLaunchClasses;   // launch classes of one call (see footprint_class)
+constexpr int kMaxLaunches = 2 * kClasses;   // each class and its launch of clustered outliers
+constexpr int kAuxStreams = kMaxLaunches - 1;
 
 }  // namespace
 
@@ -216,18 +219,12 @@ bool prefix_pays(const std::vector<LaunchItem> &items, int ngroups, int csize) {
     return feas >= 3.0 * ngroups * std::max(1, csize);
 }
 
-// Launch class of a search: its footprint -- per-group scratch words (profile
-// or capacity state plus N earliest starts) up to 2K, up to 8K, or more --
-// times its size (N up to 64, up to 160, larger).  Each class of a call gets
+// Launch class of a search (rcpsp::launch_class).  Each class of a call gets
 // its own launch shape, so that small instances are not run at the group
 // count the largest one allows, and a few large searches can share clusters
 // of CTAs while many small ones take one CTA each.
-
 int footprint_class(const LaunchItem &it) {
-    const int gw = rcpsp::profile_words(it.mode, it.h.wps, it.h.ub, it.h.sum_cap) + it.h.n;
-    const int fp = gw <= 2048 ? 0 : (gw <= 8192 ? 1 : 2);
-    const int sz = it.h.n <= 64 ? 0 : (it.h.n <= 160 ? 1 : 2);
-    return fp * 3 + sz;
+    return rcpsp::launch_class(rcpsp::profile_words(it.mode, it.h.wps, it.h.ub, it.h.sum_cap) + it.h.n, it.h.n);
 }
 
 struct ClassLaunch {
@@ -238,7 +235,29 @@ struct ClassLaunch {
     size_t smem = 0;
     int shape_source = 0;        // rcpsp_launch_info.shape_source
     double cost = 0;             // estimated work of the class
+    bool outliers = false;       // the clustered outliers of a class (see split_outliers)
 };
+
+// Feasible swaps (u, v), 1 <= u < v <= N-2, v - u <= delta, of the list W:
+// swap(u, v) keeps every arc pointing forward iff no successor of W[u] sits
+// at a position up to v and no predecessor of W[v] at a position from u on
+// (Eqs. 5-6), i.e. firstSucc(u) > v and lastPred(v) < u.
+int feasible_swaps(const std::vector<int32_t> &succ_off, const std::vector<int32_t> &succ,
+                   const std::vector<int32_t> &W, int delta) {
+    const int n = static_cast<int>(W.size());
+    std::vector<int> pos(n), fsp(n, n), lpp(n, -1);
+    for (int p = 0; p < n; ++p) pos[W[p]] = p;
+    for (int a = 0; a < n; ++a)
+        for (int e = succ_off[a]; e < succ_off[a + 1]; ++e) {
+            const int b = succ[e];
+            fsp[pos[a]] = std::min(fsp[pos[a]], pos[b]);
+            lpp[pos[b]] = std::max(lpp[pos[b]], pos[a]);
+        }
+    int cnt = 0;
+    for (int u = 1; u <= n - 3; ++u)
+        for (int v = u + 1; v <= std::min(u + delta, n - 2); ++v) cnt += fsp[u] > v && lpp[v] < u;
+    return cnt;
+}
 
 // CTAs that share one search: 1 unless the class has few searches for the
 // GPU and each has a large neighbourhood.
@@ -398,7 +417,7 @@ int rcpsp_create(rcpsp_ctx **ctx, int device, const rcpsp_allocator *alloc) {
         return RCPSP_E_CUDA;
     }
     load_tune_cache(c);
-    c->queue_dev = static_cast<int *>(dev_alloc(c, 64, nullptr));          // one counter per class
+    c->queue_dev = static_cast<int *>(dev_alloc(c, 4 * kMaxLaunches, nullptr));   // one counter per launch
     if (!c->queue_dev) {
         cudaEventDestroy(c->done);
         delete c;
@@ -420,7 +439,7 @@ int rcpsp_destroy(rcpsp_ctx *c) {
     }
     for (Block &b : c->blocks) dev_free(c, b.ptr, b.bytes, nullptr);
     dev_free(c, c->items_dev, c->items_cap, nullptr);
-    dev_free(c, c->queue_dev, 64, nullptr);
+    dev_free(c, c->queue_dev, 4 * kMaxLaunches, nullptr);
     dev_free(c, c->coop_dev, c->coop_cap, nullptr);
     dev_free(c, c->snap_dev, c->snap_cap, nullptr);
     if (c->items_host) cudaFreeHost(c->items_host);
@@ -556,6 +575,7 @@ int rcpsp_load_instances(rcpsp_ctx *c, const rcpsp_instance *inst, int32_t count
         in.alive = true;
         in.succ_off.assign(inst[k].succ_off, inst[k].succ_off + inst[k].n + 1);
         in.succ.assign(inst[k].succ, inst[k].succ + inst[k].succ_off[inst[k].n]);
+        in.w0 = packed[k].initial;
         ro += packed[k].record.size();
         oo += out_words(in.h.n);
         out_ids[k] = static_cast<int32_t>(c->insts.size());
@@ -577,6 +597,7 @@ int rcpsp_free_instances(rcpsp_ctx *c, const int32_t *ids, int32_t count) {
         in.alive = false;
         std::vector<int32_t>().swap(in.succ_off);     // a long-lived context keeps no host copies
         std::vector<int32_t>().swap(in.succ);
+        std::vector<int32_t>().swap(in.w0);
         dev_free(c, in.trace, in.trace_bytes, nullptr);
         in.trace = nullptr;
         in.trace_bytes = 0;
@@ -664,7 +685,7 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
         } else {
             in.trace_iters = -1;
         }
-        cost[k] = rcpsp::estimate_cost(in.h, it.mode, it.iterations, it.delta);
+        cost[k] = rcpsp::estimate_cost(in.h, it.mode, it.iterations, it.delta, it.stop_at_cp != 0);
     }
     // footprint classes, each ordered longest first (LPT) on its own queue
     std::vector<LaunchItem> sorted;
@@ -717,12 +738,65 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
         if (units < 1) return set_err(c, RCPSP_E_TOO_LARGE, "launch shape does not fit on the GPU");
         L.blocks = L.csize == 1 ? std::max(1, std::min(L.count, units * c->prop.multiProcessorCount))
                                 : L.csize * std::max(1, std::min(L.count, units));
+        // Outliers: in a class whose searches take one CTA each and decode
+        // their neighbourhood in about one round, a few searches whose
+        // initial list has more feasible swaps than the CTA has decoding
+        // groups need several rounds per iteration and would set the call's
+        // length.  They get a launch of their own with clusters of 2-8 CTAs
+        // that split their neighbourhoods (same results: the cluster search
+        // follows the one-CTA trajectory), and it starts first.
+        if (!cs && L.csize == 1 && !L.prefix && L.count >= 16) {
+            const int ngroups = warps * (32 / G);
+            std::vector<int> out;
+            int worst = 0;
+            for (int k = L.offset; k < L.offset + L.count; ++k) {
+                Inst &in = c->insts[ids[idx[k - L.offset]]];
+                if (in.feas_delta != sorted[k].delta) {
+                    in.feas0 = feasible_swaps(in.succ_off, in.succ, in.w0, sorted[k].delta);
+                    in.feas_delta = sorted[k].delta;
+                }
+                if (in.feas0 > ngroups) {
+                    out.push_back(k);
+                    worst = std::max(worst, in.feas0);
+                }
+            }
+            int oc = 2;
+            while (oc < 8 && oc * ngroups < worst) oc *= 2;
+            int ounits = 0;
+            if (!out.empty() && 16 * static_cast<int>(out.size()) <= L.count &&
+                rcpsp::search_occupancy(G, L.threads, smem, oc, &ounits, false) == cudaSuccess && ounits >= 1) {
+                // the outliers move to the end of the class's part of the plan
+                std::vector<LaunchItem> keep, moved;
+                std::vector<double> kc, mc;
+                size_t o = 0;
+                for (int k = L.offset; k < L.offset + L.count; ++k) {
+                    if (o < out.size() && out[o] == k) {
+                        moved.push_back(sorted[k]);
+                        ++o;
+                    } else {
+                        keep.push_back(sorted[k]);
+                    }
+                }
+                std::copy(keep.begin(), keep.end(), sorted.begin() + L.offset);
+                std::copy(moved.begin(), moved.end(), sorted.begin() + L.offset + keep.size());
+                ClassLaunch O = L;
+                O.offset = L.offset + static_cast<int>(keep.size());
+                O.count = static_cast<int>(moved.size());
+                O.csize = oc;
+                O.outliers = true;
+                O.blocks = oc * std::max(1, std::min(O.count, ounits));
+                L.count = static_cast<int>(keep.size());
+                L.blocks = std::max(1, std::min(L.count, units * c->prop.multiProcessorCount));
+                launches.push_back(O);
+            }
+        }
         launches.push_back(L);
     }
-    // classes of more work launch first, so that the long searches of a call
-    // are not queued behind short classes for SMs
-    std::stable_sort(launches.begin(), launches.end(),
-                     [](const ClassLaunch &a, const ClassLaunch &b) { return a.cost > b.cost; });
+    // launches of clustered outliers first, then classes of more work, so
+    // that the long searches of a call are not queued behind short ones for SMs
+    std::stable_sort(launches.begin(), launches.end(), [](const ClassLaunch &a, const ClassLaunch &b) {
+        return a.outliers != b.outliers ? a.outliers : a.cost > b.cost;
+    });
     // kept prefix states: one region per CTA of every class that uses them
     {
         size_t need = 0;
@@ -776,7 +850,7 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
     // queue reset, then one persistent launch per class; classes after the
     // first run on forked streams and join back before the done event
     auto launch_all = [&](cudaStream_t s0) -> cudaError_t {
-        cudaError_t r = cudaMemsetAsync(c->queue_dev, 0, sizeof(int) * kClasses, s0);
+        cudaError_t r = cudaMemsetAsync(c->queue_dev, 0, sizeof(int) * kMaxLaunches, s0);
         if (r != cudaSuccess) return r;
         if (launches.size() > 1 && (r = cudaEventRecord(c->fork, s0)) != cudaSuccess) return r;
         for (size_t q = 0; q < launches.size(); ++q) {
@@ -942,7 +1016,7 @@ int rcpsp_coop_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
         it.iterations = p->iterations;
         it.stop_at_cp = p->stop_at_cp ? 1 : 0;
         in.trace_iters = -1;
-        cost[k] = B * rcpsp::estimate_cost(in.h, it.mode, it.iterations, it.delta);
+        cost[k] = B * rcpsp::estimate_cost(in.h, it.mode, it.iterations, it.delta, it.stop_at_cp != 0);
         key_off[k] = keys_total;
         keys_total += static_cast<size_t>(F) * in.h.n;
     }
@@ -1048,7 +1122,7 @@ int rcpsp_coop_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
     if (random_words)
         std::memcpy(hb + plan_bytes + lists_bytes, random_words, static_cast<size_t>(count) * B * P * 4);
     e = cudaMemcpyAsync(db, hb, up_bytes, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->queue_dev, 0, sizeof(int) * kClasses, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->queue_dev, 0, sizeof(int) * kMaxLaunches, st);
     if (e != cudaSuccess) return cuda_err(c, e, "co-operative search upload");
     c->h2d += static_cast<long long>(up_bytes);
     // one launch per class; classes after the first run on forked streams
@@ -1119,7 +1193,7 @@ int rcpsp_tabu_search_noalloc(rcpsp_ctx *c, const int32_t *ids, int32_t count, c
         it.iterations = p->iterations;
         it.stop_at_cp = p->stop_at_cp ? 1 : 0;
         in.trace_iters = -1;
-        cost[k] = rcpsp::estimate_cost(in.h, it.mode, it.iterations, it.delta);
+        cost[k] = rcpsp::estimate_cost(in.h, it.mode, it.iterations, it.delta, it.stop_at_cp != 0);
     }
     std::vector<int> order(count);
     std::iota(order.begin(), order.end(), 0);
@@ -1230,7 +1304,8 @@ int rcpsp_autotune(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcpsp_
         for (int G : gsz)
             for (int W : wcnt) {
                 const int ng = W * (32 / G);
-                const int min_groups = cls == 0 ? 8 : (cls == 1 ? 2 : 1);   // large states fit few groups
+                const int fp = cls / 3, sz = cls % 3;                        // large states fit few groups
+                const int min_groups = fp <= 1 ? (sz == 0 ? 8 : 2) : (fp == 2 ? 2 : 1);
                 if (ng < min_groups || ng > 256) continue;
                 if (C > 1 && (G < 4 || W < 4)) continue;                     // fewer trials for clusters
                 q.group_size = G;

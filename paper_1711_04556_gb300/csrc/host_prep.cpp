@@ -173,6 +173,32 @@ int prepare_instance(const rcpsp_instance &in, PackedInstance &out, std::string 
     for (int k = 0; k < m; ++k) h.sum_cap += in.cap[k];
     h.sum_used = 0;
     for (int i = 0; i < n * m; ++i) h.sum_used += in.req[i] > 0 ? 1 : 0;
+    // Does the earliest-start schedule (infinite capacities) respect every
+    // capacity?  Then the serial SGS of the level-ordered list places every
+    // activity at its earliest start (its predecessors come first, and what
+    // is placed before it uses no more than the earliest-start profile), so
+    // the initial makespan is the critical path and a search that stops at
+    // the critical path ends before its first iteration.  Only the queue
+    // order uses this.
+    {
+        h.es_fits = 1;
+        const int horizon_cp = es[n - 1] + 1;
+        std::vector<int64_t> prof(static_cast<size_t>(horizon_cp) + 1);
+        for (int k = 0; k < m && h.es_fits; ++k) {
+            std::fill(prof.begin(), prof.end(), 0);
+            for (int i = 0; i < n; ++i) {
+                const int r = in.req[i * m + k], d = in.dur[i];
+                if (r <= 0 || d <= 0) continue;
+                prof[es[i]] += r;
+                prof[std::min(es[i] + d, horizon_cp)] -= r;
+            }
+            int64_t run = 0;
+            for (int t = 0; t < horizon_cp && h.es_fits; ++t) {
+                run += prof[t];
+                if (run > in.cap[k]) h.es_fits = 0;
+            }
+        }
+    }
     h.n_arcs = E;
     const InstLayout L = inst_layout(n, m, wps, E);
     h.inst_words = L.words;
@@ -214,10 +240,12 @@ void default_search_params(int n, int *delta, int *tabu_len) {
     else { *delta = 60; *tabu_len = 800; }
 }
 
-double estimate_cost(const InstHeader &h, int mode, int iterations, int delta) {
+double estimate_cost(const InstHeader &h, int mode, int iterations, int delta, bool stop_at_cp) {
     const double slots = h.n > 3 ? static_cast<double>(h.n - 3) * delta : 0.0;
     const double per_decode = mode == RCPSP_EVAL_CAPACITY ? h.n * (1.0 + h.sum_cap / 2.0)
                                                           : h.n * 4.0 + 2.0 * h.ub * h.wps;
+    // a search that stops at the critical path and starts there does no iteration
+    if (stop_at_cp && h.es_fits && mode == RCPSP_EVAL_TIME) iterations = 0;
     return (iterations + 1.0) * (slots * 0.15 + 1.0) * per_decode;
 }
 

@@ -31,6 +31,6 @@ int select_evaluator(int m, const int32_t *cap, int critical_path);
 void default_search_params(int n, int *delta, int *tabu_len);
 
 // Relative cost of one search, for longest-first ordering of the queue.
-double estimate_cost(const InstHeader &h, int mode, int iterations, int delta);
+double estimate_cost(const InstHeader &h, int mode, int iterations, int delta, bool stop_at_cp);
 
 }  // namespace rcpsp

@@ -33,7 +33,8 @@ struct InstHeader {
     int32_t inst_words;         // words of the shared-memory section
     int32_t record_words;       // inst_words + initial list, multiple of 4
     int32_t sum_used;           // number of (activity, resource) pairs with r_{i,k} > 0
-    int32_t pad[4];
+    int32_t es_fits;            // 1: the earliest-start schedule respects every capacity
+    int32_t pad[3];
 };
 static_assert(sizeof(InstHeader) == 64, "InstHeader is 64 bytes");
 
@@ -153,6 +154,20 @@ enum : int { kPxF = 0, kPxCmax, kPxWork, kPxUpd, kPxSucc, kPxWords, kPxMeta = 8 
 RC_HD int prefix_count(int n, int K) { return K > 0 ? (n - 1) / K : 0; }
 RC_HD int prefix_stride(int n, int prof_words) { return align4(kPxMeta + prof_words + n); }
 RC_HD int prefix_words(int n, int prof_words, int K) { return prefix_count(n, K) * prefix_stride(n, prof_words); }
+
+// Launch class of a search: its footprint -- per-group scratch words `gw`
+// (profile or capacity state plus N earliest starts) up to 512, 2K, 8K, or
+// more -- times its size (N up to 64, up to 160, larger).  Searches of one
+// class share a launch and its shape; the finest footprint level keeps the
+// capacity-indexed searches (a few hundred words per group) apart from the
+// time-indexed ones of the same size, whose profiles would otherwise size
+// every CTA of the launch.
+constexpr int kLaunchClasses = 12;
+RC_HD int launch_class(int gw, int n) {
+    const int fp = gw <= 512 ? 0 : (gw <= 2048 ? 1 : (gw <= 8192 ? 2 : 3));
+    const int sz = n <= 64 ? 0 : (n <= 160 ? 1 : 2);
+    return fp * 3 + sz;
+}
 
 RC_HD StateLayout state_layout(int inst_words, int n, int tabu_len, int delta, int move_cap,
                                int prof_words, int ngroups) {

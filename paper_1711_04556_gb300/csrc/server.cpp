@@ -132,7 +132,7 @@ struct rcpsp_server {
     std::vector<rcpsp_allocator> allocs;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
-    std::deque<Request> pending[9];      // one FIFO per launch class
+    std::deque<Request> pending[rcpsp::kLaunchClasses];   // one FIFO per launch class
     std::deque<Completion> done;
     std::vector<Completion> handed;      // returned by the last poll, owned until the next one
     std::thread worker;
@@ -228,17 +228,14 @@ void harvest(rcpsp_server *s, Slot &sl) {
     sl.bytes = 0;
 }
 
-// Launch class of a request: footprint (per-group scratch words up to 2K,
-// 8K, more) times size (N up to 64, 160, more), as rcpsp_tabu_search splits
-// a call.  Batches take one class, so small requests do not wait for the
+// Launch class of a request: footprint (per-group scratch words up to 512,
+// 2K, 8K, more) times size (N up to 64, 160, more), as rcpsp_tabu_search
+// splits a call (rcpsp::launch_class).  Batches take one class, so small requests do not wait for the
 // completion of large ones, and large requests come in small batches that
 // can share clusters of CTAs.
 int request_class(const rcpsp::PackedInstance &pk, const rcpsp_params &p) {
     const int mode = p.eval_mode == RCPSP_EVAL_AUTO ? pk.h.sel_mode : p.eval_mode;
-    const int gw = rcpsp::profile_words(mode, pk.h.wps, pk.h.ub, pk.h.sum_cap) + pk.h.n;
-    const int fp = gw <= 2048 ? 0 : (gw <= 8192 ? 1 : 2);
-    const int sz = pk.h.n <= 64 ? 0 : (pk.h.n <= 160 ? 1 : 2);
-    return fp * 3 + sz;
+    return rcpsp::launch_class(rcpsp::profile_words(mode, pk.h.wps, pk.h.ub, pk.h.sum_cap) + pk.h.n, pk.h.n);
 }
 
 int batch_limit(const rcpsp_server *s, int cls) {
@@ -258,7 +255,7 @@ bool admit(rcpsp_server *s, Slot &sl) {
         for (const Slot &o : s->slots) large_busy += o.busy && o.cls % 3 == 2;
         const bool large_ok = 2 * (large_busy + 1) <= static_cast<int>(s->slots.size()) || large_busy == 0;
         int cls = -1;
-        for (int q = 0; q < 9; ++q)
+        for (int q = 0; q < rcpsp::kLaunchClasses; ++q)
             if (!s->pending[q].empty() && (large_ok || q % 3 != 2) &&
                 (cls < 0 || s->pending[q].front().t_submit < s->pending[cls].front().t_submit))
                 cls = q;

@@ -61,3 +61,20 @@ def test_layer_skipping_arcs(solver, oracle, mode):
     run_and_compare(solver, oracle, small, 300, 20, 60, mode)
     large = [with_skip_arcs(s, 120, 4, 180, 20, extra=40, relabel=bool(s % 2)) for s in range(4)]
     run_and_compare(solver, oracle, large, 150, 60, 800, mode)
+
+
+def test_clustered_outliers_of_a_class(solver, oracle):
+    """At 96 decoding groups per CTA (G = 4, 12 warps) the few j30
+    searches whose initial neighbourhood is larger get their own launch with
+    clusters; their results are those of one-CTA searches."""
+    insts = I.config_batch("j30_batch", 480)
+    ids = solver.load(insts)
+    solver.search(ids, iterations=300, delta=20, tabu_len=60, mode=R.EVAL_AUTO, group_size=4, warps_per_cta=12)
+    plan = solver.last_launches()
+    got = solver.results(ids)
+    assert len(plan) == 2 and plan[0]["cluster_size"] >= 2 and plan[1]["cluster_size"] == 1
+    assert plan[0]["searches"] + plan[1]["searches"] == 480 and 1 <= plan[0]["searches"] <= 30
+    ref = oracle.tabu_search_batch(insts, [(300, 20, 60, oracle.AUTO, 1)] * len(insts), NPROC)
+    for g, r in zip(got, ref):
+        compare_search(oracle, g, r)
+    solver.free(ids)
