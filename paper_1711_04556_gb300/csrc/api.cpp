@@ -1025,6 +1025,9 @@ int rcpsp_coop_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
     struct CoopLaunch {
         int offset = 0, count = 0, G = 0, warps = 0, move_cap = 0, nclusters = 0;
         size_t smem = 0;
+        bool prefix = false;         // prefix reuse (kernel variant, kept states per CTA)
+        int snap_words = 0;
+        size_t snap_off = 0;
     };
     std::vector<int> order;
     order.reserve(count);
@@ -1058,8 +1061,15 @@ int rcpsp_coop_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
         }
         if (smem > smem_limit)
             return set_err(c, RCPSP_E_TOO_LARGE, "instance state does not fit in shared memory at this launch shape");
+        // every CTA of a cluster evaluates the whole neighbourhood of its own
+        // list, so prefix reuse pays as it does for a one-CTA search
+        if (prefix_pays(part, warps * (32 / G), 1)) {
+            L.prefix = true;
+            L.snap_words = prefix_words_max(part);
+            for (int k : idx) items[k].prefix_k = prefix_k_for(items[k].h.n);
+        }
         int clusters = 0;
-        e = rcpsp::coop_occupancy(G, warps * 32, smem, B, &clusters);
+        e = rcpsp::coop_occupancy(G, warps * 32, smem, B, &clusters, L.prefix);
         if (e != cudaSuccess) return cuda_err(c, e, "co-operative occupancy");
         if (clusters < 1)
             return set_err(c, RCPSP_E_TOO_LARGE, "a cluster of this many CTAs does not fit at this shape");
@@ -1068,6 +1078,21 @@ int rcpsp_coop_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
         L.smem = smem;
         L.nclusters = std::max(1, std::min(L.count, clusters));
         launches.push_back(L);
+    }
+    // kept prefix states: one region per CTA of every launch that uses them
+    {
+        size_t need = 0;
+        for (CoopLaunch &L : launches)
+            if (L.prefix) {
+                L.snap_off = need;
+                need += static_cast<size_t>(L.nclusters) * B * L.snap_words;
+            }
+        if (need * 4 > c->snap_cap) {
+            dev_free(c, c->snap_dev, c->snap_cap, nullptr);
+            c->snap_dev = static_cast<int32_t *>(dev_alloc(c, need * 4, nullptr));
+            c->snap_cap = c->snap_dev ? need * 4 : 0;
+            if (!c->snap_dev) return set_err(c, RCPSP_E_CUDA, "prefix scratch allocation failed");
+        }
     }
     // device block: [plan][initial lists][random words][working sets]; the
     // first three are uploaded, the working sets are written by the kernel
@@ -1135,7 +1160,8 @@ int rcpsp_coop_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
         cudaStream_t sq = q == 0 ? st : c->aux[q - 1];
         if (q > 0 && (e = cudaStreamWaitEvent(sq, c->fork, 0)) != cudaSuccess) return cuda_err(c, e, "stream fork");
         e = rcpsp::launch_coop(L.G, reinterpret_cast<const rcpsp::CoopItem *>(db) + L.offset, L.count,
-                               c->queue_dev + q, L.move_cap, cfg, L.nclusters * B, L.warps * 32, L.smem, sq);
+                               c->queue_dev + q, L.move_cap, cfg, L.nclusters * B, L.warps * 32, L.smem, sq,
+                               L.prefix, L.prefix ? c->snap_dev + L.snap_off : nullptr, L.snap_words);
         if (e != cudaSuccess) return cuda_err(c, e, "co-operative search launch");
         c->kernels += 1;
         if (q > 0 && (e = cudaEventRecord(c->join[q - 1], sq)) != cudaSuccess) return cuda_err(c, e, "event record");

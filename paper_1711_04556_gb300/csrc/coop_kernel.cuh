@@ -175,11 +175,16 @@ __device__ void fbi_warp(const SInst &I, int mode, int *W, int *Wx, int *pos, in
     __syncwarp();
 }
 
-template <int G>
+// PFX: the variant with prefix reuse -- every CTA keeps the decoder states
+// of its own current list at gsnap + blockIdx.x * gsnap_words (see Prefix),
+// for the items with prefix_k > 0.
+template <int G, bool PFX>
 __global__ void __launch_bounds__(512, 2) coop_kernel(const CoopItem *__restrict__ items, int count,
-                                                    int *__restrict__ queue, int move_cap, CoopConfig cfg) {
+                                                    int *__restrict__ queue, int move_cap, CoopConfig cfg,
+                                                    int *__restrict__ gsnap, int gsnap_words) {
     extern __shared__ __align__(16) int sm[];
     __shared__ int s_mq[2];
+    __shared__ int s_hist[32];
     __shared__ int s_item, s_C, s_Cbb, s_widx, s_it, s_err, s_improved;
     __shared__ unsigned long long s_best, s_t0;
     __shared__ long long s_eval, s_work;
@@ -217,6 +222,9 @@ __global__ void __launch_bounds__(512, 2) coop_kernel(const CoopItem *__restrict
         const int pw = profile_words(mode, h.wps, h.ub, h.sum_cap);
         const StateLayout S = state_layout(h.inst_words, n, tl, delta, move_cap, pw, ngroups);
         const SlotLayout SL = slot_layout(n, tl, delta);
+        const int pk = PFX ? it.prefix_k : 0;
+        const Prefix px{pk > 0 ? gsnap + static_cast<long long>(blockIdx.x) * gsnap_words : nullptr,
+                        pk > 0 ? pk : 1, prefix_count(n, pk), prefix_stride(n, pw)};
         const int tcw = (n * delta + 31) / 32;
         stage_instance(sm, it.record, h.inst_words);
         const SInst I = bind_instance(sm, h);
@@ -233,6 +241,7 @@ __global__ void __launch_bounds__(512, 2) coop_kernel(const CoopItem *__restrict
         const unsigned dmagic = slot_magic(delta);
         const uint32_t *words = ci.words ? ci.words + static_cast<long long>(crank) * cfg.words_per_block : nullptr;
         if (tid < kTallies) s_tally[tid] = 0;
+        if (tid < 32) s_hist[tid] = 0;
         if (tid == 0) {
             s_t0 = global_timer_ns();
             s_eval = 0;
@@ -369,9 +378,9 @@ __global__ void __launch_bounds__(512, 2) coop_kernel(const CoopItem *__restrict
             const int par = s_it & 1;
             if (tid == 0) s_best = ~0ull;
             const unsigned long long my_key =
-                best_admissible_key<G>(I, mode, W, pos, fsp, lpp, tc, moves, area, n, delta, nslots, dmagic,
-                                       move_cap, s_Cstar, 1, 0u, s_mq, &s_eval, my_work, err,
-                                       Prefix{nullptr, 1, 0, 0}, TallyRef{s_tally, nullptr});
+                best_admissible_key<G, PFX>(I, mode, W, pos, fsp, lpp, tc, moves, area, n, delta, nslots, dmagic,
+                                            move_cap, s_Cstar, 1, 0u, s_mq, &s_eval, my_work, err, px,
+                                            TallyRef{s_tally, s_hist});
             const unsigned long long wk = warp_min_u64(my_key);
             if (wl == 0 && wk != ~0ull) atomicMin(&s_best, wk);
             __syncthreads();
@@ -542,12 +551,12 @@ __global__ void __launch_bounds__(512, 2) coop_kernel(const CoopItem *__restrict
     }
 }
 
-template <int G>
+template <int G, bool PFX>
 cudaError_t coop_attributes_g(size_t smem, int csize) {
-    cudaError_t e = cudaFuncSetAttribute(coop_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(coop_kernel<G, PFX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e == cudaSuccess && csize > 8)
-        e = cudaFuncSetAttribute(coop_kernel<G>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        e = cudaFuncSetAttribute(coop_kernel<G, PFX>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     return e;
 }
 
@@ -567,33 +576,62 @@ cudaLaunchConfig_t coop_config(int blocks, int threads, size_t smem, cudaStream_
     return cfg;
 }
 
-template <int G>
+template <int G, bool PFX>
 cudaError_t coop_occupancy_g(int threads, size_t smem, int csize, int *clusters) {
-    cudaError_t e = coop_attributes_g<G>(smem, csize);
+    cudaError_t e = coop_attributes_g<G, PFX>(smem, csize);
     if (e != cudaSuccess) return e;
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = coop_config(csize, threads, smem, nullptr, csize, attr);
-    return cudaOccupancyMaxActiveClusters(clusters, coop_kernel<G>, &cfg);
+    return cudaOccupancyMaxActiveClusters(clusters, coop_kernel<G, PFX>, &cfg);
 }
 
-template <int G>
+template <int G, bool PFX>
 cudaError_t launch_coop_g(const CoopItem *items, int count, int *queue, int move_cap, const CoopConfig &cc,
-                          int blocks, int threads, size_t smem, cudaStream_t st) {
-    cudaError_t e = coop_attributes_g<G>(smem, cc.blocks);
+                          int blocks, int threads, size_t smem, cudaStream_t st, int *gsnap, int gsnap_words) {
+    cudaError_t e = coop_attributes_g<G, PFX>(smem, cc.blocks);
     if (e != cudaSuccess) return e;
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = coop_config(blocks, threads, smem, st, cc.blocks, attr);
-    return cudaLaunchKernelEx(&cfg, coop_kernel<G>, items, count, queue, move_cap, cc);
+    return cudaLaunchKernelEx(&cfg, coop_kernel<G, PFX>, items, count, queue, move_cap, cc, gsnap, gsnap_words);
 }
+
+// The entry points of one prefix-reuse variant for a set of group sizes.
+#define RCPSP_COOP_ENTRY_POINTS(NAME, PFX_, G0, G1, G2)                                                        \
+    cudaError_t coop_occupancy_##NAME(int group_size, int threads, size_t smem, int csize, int *clusters) {   \
+        switch (group_size) {                                                                                  \
+            case G0: return coop_occupancy_g<G0, PFX_>(threads, smem, csize, clusters);                         \
+            case G1: return coop_occupancy_g<G1, PFX_>(threads, smem, csize, clusters);                         \
+            case G2: return coop_occupancy_g<G2, PFX_>(threads, smem, csize, clusters);                         \
+            default: return cudaErrorInvalidValue;                                                             \
+        }                                                                                                      \
+    }                                                                                                          \
+    cudaError_t launch_coop_##NAME(int group_size, const CoopItem *items, int count, int *queue, int move_cap, \
+                                   const CoopConfig &cfg, int blocks, int threads, size_t smem,                \
+                                   cudaStream_t st, int *gsnap, int gsnap_words) {                             \
+        switch (group_size) {                                                                                  \
+            case G0: return launch_coop_g<G0, PFX_>(items, count, queue, move_cap, cfg, blocks, threads, smem, \
+                                                     st, gsnap, gsnap_words);                                  \
+            case G1: return launch_coop_g<G1, PFX_>(items, count, queue, move_cap, cfg, blocks, threads, smem, \
+                                                     st, gsnap, gsnap_words);                                  \
+            case G2: return launch_coop_g<G2, PFX_>(items, count, queue, move_cap, cfg, blocks, threads, smem, \
+                                                     st, gsnap, gsnap_words);                                  \
+            default: return cudaErrorInvalidValue;                                                             \
+        }                                                                                                      \
+    }
 
 }  // namespace
 
-// Per-G-set entry points (coop_kernel.cu, coop_kernel_wide.cu).
-cudaError_t coop_occupancy_narrow(int group_size, int threads, size_t smem, int csize, int *clusters);
-cudaError_t launch_coop_narrow(int group_size, const CoopItem *items, int count, int *queue, int move_cap,
-                               const CoopConfig &cfg, int blocks, int threads, size_t smem, cudaStream_t st);
-cudaError_t coop_occupancy_wide(int group_size, int threads, size_t smem, int csize, int *clusters);
-cudaError_t launch_coop_wide(int group_size, const CoopItem *items, int count, int *queue, int move_cap,
-                             const CoopConfig &cfg, int blocks, int threads, size_t smem, cudaStream_t st);
+// Per-variant entry points: coop_kernel.cu (G 1, 2, 4), coop_kernel_wide.cu
+// (G 8, 16, 32), coop_kernel_pfx.cu and coop_kernel_pfx_wide.cu (the same
+// with prefix reuse).
+#define RCPSP_COOP_DECLARE(NAME)                                                                                 \
+    cudaError_t coop_occupancy_##NAME(int group_size, int threads, size_t smem, int csize, int *clusters);     \
+    cudaError_t launch_coop_##NAME(int group_size, const CoopItem *items, int count, int *queue, int move_cap, \
+                                   const CoopConfig &cfg, int blocks, int threads, size_t smem,                \
+                                   cudaStream_t st, int *gsnap, int gsnap_words);
+RCPSP_COOP_DECLARE(narrow)
+RCPSP_COOP_DECLARE(wide)
+RCPSP_COOP_DECLARE(pfx_narrow)
+RCPSP_COOP_DECLARE(pfx_wide)
 
 }  // namespace rcpsp

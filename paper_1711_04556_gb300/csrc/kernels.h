@@ -25,10 +25,12 @@ cudaError_t launch_evaluate(int group_size, const LaunchItem &item, const int32_
 
 // Co-operative search (coop_kernel.cu): clusters of cfg.blocks CTAs, one
 // instance per cluster.  coop_occupancy gives the resident clusters on the
-// whole GPU; blocks = CTAs of the launch, a multiple of cfg.blocks.
-cudaError_t coop_occupancy(int group_size, int threads, size_t smem, int csize, int *clusters);
+// whole GPU; blocks = CTAs of the launch, a multiple of cfg.blocks.  With
+// prefix reuse CTA b keeps its decoder states at gsnap + b * gsnap_words.
+cudaError_t coop_occupancy(int group_size, int threads, size_t smem, int csize, int *clusters, bool prefix = false);
 cudaError_t launch_coop(int group_size, const CoopItem *items, int count, int *queue, int move_cap,
-                        const CoopConfig &cfg, int blocks, int threads, size_t smem, cudaStream_t st);
+                        const CoopConfig &cfg, int blocks, int threads, size_t smem, cudaStream_t st,
+                        bool prefix = false, int *gsnap = nullptr, int gsnap_words = 0);
 
 // Fixed scratch of the no-allocation search (noalloc_scratch.cu): largest
 // plan it holds, and its device address on `device` (queue counter, plan).

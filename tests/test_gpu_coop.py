@@ -149,3 +149,14 @@ def test_invalid_parameters(solver):
             solver.coop_search(ids, **kw)
         assert e.value.code == -1
     solver.free(ids)
+
+
+@pytest.mark.parametrize("mode", [R.EVAL_TIME, R.EVAL_CAPACITY])
+def test_prefix_reuse_in_the_cooperation(solver, oracle, mode):
+    """Four decoding groups per CTA against ~100+ feasible moves: every CTA
+    of a cluster keeps the decoder states of its own list (prefix reuse),
+    and the co-operation is still the CPU reference's, exchange for
+    exchange (the counts include every neighbour in full)."""
+    insts = I.config_batch("j120_batch", 4, first=40) + [
+        x for x in I.config_batch("mixed_batch", 40) if x.n in (92, 122)][:3]
+    run_both(solver, oracle, insts, 40, 0, 0, mode=mode, blocks=4, group_size=8, warps_per_cta=1)
