@@ -360,6 +360,21 @@ int rcpsp_transfer_bytes(const rcpsp_ctx *ctx, int64_t *h2d, int64_t *d2h);
  * counterpart in the paper. */
 int rcpsp_kernel_launches(const rcpsp_ctx *ctx, int64_t *launches);
 
+/* Multi-start (Sec. 4.1): `starts` independent searches of one instance,
+ * start k from the level-ordered list with the shuffle keys of row k of
+ * level_keys ([starts][N], host; NULL or a row of zeros = the unshuffled
+ * order), keeping the one with the lowest best makespan (ties: the lowest
+ * start index).  The instance is loaded `starts` times, searched in one
+ * rcpsp_tabu_search call with `params` (record_trace, checkpoint and resume
+ * must be 0) on cuda_stream, and freed again; the call is synchronous.
+ * Outputs (host; any may be NULL): *best_start, the best start's list
+ * order[N] and start times start[N], makespans[starts] of every start, and
+ * stats of the best start.  Errors: those of rcpsp_load_instances and
+ * rcpsp_tabu_search; RCPSP_E_INVALID_ARG for starts < 1. */
+int rcpsp_multistart(rcpsp_ctx *ctx, const rcpsp_instance *inst, int32_t starts, const int32_t *level_keys,
+                     const rcpsp_params *params, void *cuda_stream, int32_t *best_start, int32_t *order,
+                     int32_t *start, int32_t *makespans, rcpsp_stats *stats);
+
 /* Launch plan of the context's last rcpsp_tabu_search: one entry per
  * launch class of that call (see rcpsp_tabu_search), in launch order
  * (classes of more estimated work first). */

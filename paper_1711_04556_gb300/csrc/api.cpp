@@ -465,6 +465,44 @@ int rcpsp_transfer_bytes(const rcpsp_ctx *c, int64_t *h2d, int64_t *d2h) {
     return RCPSP_OK;
 }
 
+int rcpsp_multistart(rcpsp_ctx *c, const rcpsp_instance *inst, int32_t starts, const int32_t *level_keys,
+                     const rcpsp_params *p, void *stream, int32_t *best_start, int32_t *order, int32_t *start,
+                     int32_t *makespans, rcpsp_stats *stats) {
+    HostRange range("rcpsp_multistart");
+    if (!c) return RCPSP_E_INVALID_ARG;
+    if (!inst || !p || starts < 1) return set_err(c, RCPSP_E_INVALID_ARG, "bad arguments");
+    if (p->record_trace || p->checkpoint || p->resume)
+        return set_err(c, RCPSP_E_INVALID_ARG, "a multi-start keeps no trace or state");
+    const int n = inst->n;
+    std::vector<rcpsp_instance> views(starts, *inst);
+    for (int k = 0; k < starts; ++k) views[k].level_key = level_keys ? level_keys + static_cast<size_t>(k) * n : nullptr;
+    std::vector<int32_t> ids(starts);
+    int rc = rcpsp_load_instances(c, views.data(), starts, ids.data());
+    if (rc != RCPSP_OK) return rc;
+    rc = rcpsp_tabu_search(c, ids.data(), starts, p, stream);
+    std::vector<int32_t> W, S, cm(starts);
+    std::vector<rcpsp_stats> st(starts);
+    if (rc == RCPSP_OK) {
+        W.resize(static_cast<size_t>(starts) * n);
+        S.resize(static_cast<size_t>(starts) * n);
+        rc = rcpsp_get_schedules(c, ids.data(), starts, W.data(), S.data(), cm.data(), st.data());
+    }
+    const std::string msg = c->err;
+    const int frc = rcpsp_free_instances(c, ids.data(), starts);
+    if (rc != RCPSP_OK) return set_err(c, rc, msg);
+    if (frc != RCPSP_OK) return frc;
+    // the lowest best makespan, ties to the lowest start index
+    int best = 0;
+    for (int k = 1; k < starts; ++k)
+        if (cm[k] < cm[best]) best = k;
+    if (best_start) *best_start = best;
+    if (order) std::memcpy(order, W.data() + static_cast<size_t>(best) * n, sizeof(int32_t) * n);
+    if (start) std::memcpy(start, S.data() + static_cast<size_t>(best) * n, sizeof(int32_t) * n);
+    if (makespans) std::memcpy(makespans, cm.data(), sizeof(int32_t) * starts);
+    if (stats) *stats = st[best];
+    return RCPSP_OK;
+}
+
 int rcpsp_last_launches(const rcpsp_ctx *c, rcpsp_launch_info *out, int32_t capacity, int32_t *count) {
     if (!c || !count || capacity < 0 || (capacity > 0 && !out)) return RCPSP_E_INVALID_ARG;
     const int n = static_cast<int>(c->last_launches.size());

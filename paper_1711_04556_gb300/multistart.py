@@ -1,14 +1,13 @@
 """Several independent searches of one instance, keeping the best (Sec. 4.1).
 
 Sec. 4.1 builds alternative initial orders by shuffling the activities of each
-level.  Each start here is the same instance loaded with its own shuffle keys
-(`instances.level_keys(inst, seed + k)`); all starts run as independent
-searches in one launch and the best final makespan wins, ties to the lowest
-start index.
+level.  Each start is the instance with its own shuffle keys
+(`instances.level_keys(inst, seed + k)`); rcpsp_multistart runs all starts
+as independent searches in one launch and keeps the best final makespan,
+ties to the lowest start index.  This module only draws the keys (inputs)
+and marshals the call.
 """
 from __future__ import annotations
-
-from typing import Optional
 
 
 def multistart(solver, inst, starts: int, seed: int = 0, iterations: int = 1000, delta: int = 0,
@@ -20,15 +19,7 @@ def multistart(solver, inst, starts: int, seed: int = 0, iterations: int = 1000,
     """
     from .instances import level_keys
     keys = [None if (first_unshuffled and k == 0) else level_keys(inst, seed + k) for k in range(starts)]
-    ids = solver.load([inst] * starts, keys)
-    try:
-        solver.search(ids, iterations=iterations, delta=delta, tabu_len=tabu_len, mode=mode, stream=stream)
-        res = solver.results(ids)
-    finally:
-        solver.free(ids)
-    best = min(range(starts), key=lambda k: (res[k]["best_cmax"], k))
-    out = dict(res[best])
-    out["start"] = best
-    out["makespans"] = [r["best_cmax"] for r in res]
+    out = solver.multistart(inst, keys, iterations=iterations, delta=delta, tabu_len=tabu_len, mode=mode,
+                            stream=stream)
     out["keys"] = keys
     return out

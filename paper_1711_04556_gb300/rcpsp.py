@@ -24,7 +24,8 @@ EXPORTS = ("rcpsp_create", "rcpsp_destroy", "rcpsp_load_instances", "rcpsp_free_
            "rcpsp_tabu_search", "rcpsp_tabu_search_noalloc", "rcpsp_coop_search", "rcpsp_autotune",
            "rcpsp_get_schedules", "rcpsp_get_trace", "rcpsp_evaluate_lists",
            "rcpsp_prepare_instance", "rcpsp_transfer_bytes", "rcpsp_kernel_launches", "rcpsp_get_state",
-           "rcpsp_set_state", "rcpsp_measure_peaks", "rcpsp_last_launches", "rcpsp_server_create", "rcpsp_server_destroy",
+           "rcpsp_set_state", "rcpsp_measure_peaks", "rcpsp_last_launches", "rcpsp_multistart",
+           "rcpsp_server_create", "rcpsp_server_destroy",
            "rcpsp_server_submit", "rcpsp_server_poll", "rcpsp_server_get_stats", "rcpsp_last_error")
 
 
@@ -143,6 +144,8 @@ def library(path: Optional[str] = None):
         "rcpsp_kernel_launches": (C.c_int, [C.c_void_p, P(C.c_int64)]),
         "rcpsp_measure_peaks": (C.c_int, [C.c_int, P(Peaks)]),
         "rcpsp_last_launches": (C.c_int, [C.c_void_p, P(LaunchInfo), C.c_int32, P(C.c_int32)]),
+        "rcpsp_multistart": (C.c_int, [C.c_void_p, P(Instance), C.c_int32, P(C.c_int32), P(Params), C.c_void_p,
+                                       P(C.c_int32), P(C.c_int32), P(C.c_int32), P(C.c_int32), P(Stats)]),
         "rcpsp_get_state": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_size_t, P(C.c_size_t)]),
         "rcpsp_set_state": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_size_t]),
         "rcpsp_server_create": (C.c_int, [P(C.c_void_p), C.c_int, P(ServerConfig)]),
@@ -408,6 +411,32 @@ class Solver:
         """rcpsp_set_state: give instance `id_` a kept state (from get_state)."""
         buf = C.create_string_buffer(state, len(state))
         self._check(self.lib.rcpsp_set_state(self.ctx, int(id_), buf, len(state)))
+
+    def multistart(self, inst, level_keys, iterations: int = 1000, delta: int = 0, tabu_len: int = 0,
+                   mode: int = EVAL_AUTO, stop_at_cp: bool = True, stream=None) -> dict:
+        """rcpsp_multistart: one search per row of level_keys (None = the
+        unshuffled order); the best start's result and every start's makespan."""
+        starts = len(level_keys)
+        keys = np.zeros((starts, inst.n), np.int32)
+        for k, key in enumerate(level_keys):
+            if key is not None:
+                keys[k] = _i32(key)
+        m = _Marshalled(inst)
+        p = Params(iterations, delta, tabu_len, mode, int(stop_at_cp), 0, 0, 0, 0, 0)
+        best = C.c_int32(0)
+        order = np.zeros(inst.n, np.int32)
+        start = np.zeros(inst.n, np.int32)
+        makespans = np.zeros(starts, np.int32)
+        st = np.zeros(1, _STATS_DTYPE)
+        handle = getattr(stream, "cuda_stream", stream) or None
+        self._check(self.lib.rcpsp_multistart(self.ctx, C.byref(m.s), starts, _ptr(keys), C.byref(p), handle,
+                                              C.byref(best), _ptr(order), _ptr(start), _ptr(makespans),
+                                              st.ctypes.data_as(C.POINTER(Stats))))
+        out = {f: st[f][0].item() for f in _STATS_DTYPE.names}
+        return dict(start=best.value, best_W=order, best_S=start, best_cmax=int(makespans[best.value]),
+                    makespans=makespans.tolist(), evaluated=out["evaluated"], work=out["work"],
+                    iterations=out["iterations"], mode=out["eval_mode"], cp=out["critical_path"],
+                    status=out["status"])
 
     def last_launches(self) -> List[dict]:
         """rcpsp_last_launches: the launch classes of the last search call."""
