@@ -1342,6 +1342,8 @@ int rcpsp_autotune(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcpsp_
     q.checkpoint = 0;
     q.resume = 0;
     int ret_G = 0, ret_W = 0, ret_C = 0, ret_count = -1;
+    std::vector<std::string> tuned_keys;        // signatures of the classes tuned here
+    std::string ret_key;
     // each footprint class is tuned on its own (searches launch them apart)
     for (int cls = 0; cls < kClasses; ++cls) {
         std::vector<int32_t> cids;
@@ -1417,6 +1419,67 @@ int rcpsp_autotune(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcpsp_
             ret_G = bG;
             ret_W = bW;
             ret_C = bC;
+            ret_key = key;
+        }
+        tuned_keys.push_back(key);
+    }
+    // The classes of a call share the GPU, so a cluster size that is best
+    // for a class alone can hold SMs the other classes need: with more than
+    // one class, each class's CTAs per search are refined with the whole
+    // call running (every class at its tuned shape), keeping a change only
+    // if the call gets faster.
+    if (tuned_keys.size() > 1) {
+        q.group_size = q.warps_per_cta = q.cluster_size = 0;
+        std::vector<rcpsp_stats> stats(count);
+        auto time_call = [&](double *ms_out) -> int {
+            double best = 1e30;
+            for (int rep = 0; rep < 2; ++rep) {
+                cudaEventRecord(e0, st);
+                int r = rcpsp_tabu_search(c, ids, count, &q, stream);
+                if (r == RCPSP_OK) {
+                    cudaEventRecord(e1, st);
+                    r = rcpsp_get_schedules(c, ids, count, nullptr, nullptr, nullptr, stats.data());
+                }
+                if (r != RCPSP_OK) return r;
+                float ms = 0.f;
+                cudaEventSynchronize(e1);
+                cudaEventElapsedTime(&ms, e0, e1);
+                best = std::min(best, static_cast<double>(ms));
+            }
+            *ms_out = best;
+            return RCPSP_OK;
+        };
+        double base_ms = 0;
+        int r = time_call(&base_ms);
+        for (size_t t = 0; r == RCPSP_OK && t < tuned_keys.size(); ++t) {
+            std::array<int, 3> *sh = nullptr;
+            for (auto &e : c->tuned)
+                if (e.first == tuned_keys[t]) sh = &e.second;
+            if (!sh) continue;
+            const int orig = (*sh)[2];
+            int keep = orig;
+            for (int C = 1; C <= 8; C *= 2) {
+                if (C == orig || (C > 1 && ((*sh)[0] < 4 || (*sh)[1] < 4))) continue;
+                (*sh)[2] = C;
+                double ms = 0;
+                const int rr = time_call(&ms);
+                if (rr == RCPSP_E_TOO_LARGE) continue;        // does not fit at this cluster size
+                if (rr != RCPSP_OK) {
+                    r = rr;
+                    break;
+                }
+                if (ms < 0.97 * base_ms) {
+                    base_ms = ms;
+                    keep = C;
+                }
+            }
+            (*sh)[2] = keep;
+            if (tuned_keys[t] == ret_key) ret_C = keep;
+        }
+        if (r != RCPSP_OK) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return r;
         }
     }
     cudaEventDestroy(e0);
