@@ -319,7 +319,7 @@ def serving_stream(R, I, device, family, rate, seconds, iterations, pool_size=51
     arrivals = np.cumsum(rng.exponential(1.0 / rate, int(rate * seconds * 1.5) + 16))
     arrivals = arrivals[arrivals < seconds]
     done, accepted, rejected = [], 0, 0
-    with R.Server(device, slots=8, max_batch=256, memory_budget=2 << 30, max_pending=max_pending,
+    with R.Server(device, slots=12, max_batch=256, memory_budget=2 << 30, max_pending=max_pending,
                   slice_iterations=slice_iterations) as srv:
         t0 = time.perf_counter()
         k = 0
@@ -342,8 +342,9 @@ def serving_stream(R, I, device, family, rate, seconds, iterations, pool_size=51
     lat = [(c["t_done_ns"] - c["t_submit_ns"]) / 1e6 for c in ok]
     ev = sum(c["evaluated"] for c in ok)
     p50, p99 = percentiles(lat) if lat else (None, None)
-    return {"workload": f"{family} requests (n 30-300), {iterations} iterations each, Poisson {rate:.0f} req/s for "
-                        f"{seconds:g} s, measured from the stream's first request",
+    return {"workload": f"{family} requests, {iterations} iterations each, Poisson {rate:.0f} req/s for "
+                        f"{seconds:g} s, measured from the stream's first request"
+                        + (f", time-sliced every {slice_iterations} iterations" if slice_iterations else ""),
             "offered_req_s": len(arrivals) / seconds, "submitted": int(len(arrivals)), "accepted": accepted,
             "rejected_queue_full": rejected, "completed": len(ok),
             "completed_req_s": len(ok) / wall, "schedules_per_s": ev / wall, "wall_s": wall,
@@ -359,10 +360,12 @@ def serving_run(R, I, device, args):
     second stream at 0.8 x the rate the first completed, whose p50/p99 is
     the latency of a loaded but not overloaded server."""
     over = serving_stream(R, I, device, args.serving_family, args.serving_rate, args.serving_seconds,
-                          args.serving_iterations, drain_s=args.serving_drain, max_pending=args.serving_max_pending)
+                          args.serving_iterations, drain_s=args.serving_drain, max_pending=args.serving_max_pending,
+                          slice_iterations=args.serving_slice)
     rate2 = max(1.0, 0.8 * over["completed_req_s"])
     under = serving_stream(R, I, device, args.serving_family, rate2, args.serving_seconds2,
-                           args.serving_iterations, seed=6, drain_s=max(60.0, args.serving_drain))
+                           args.serving_iterations, seed=6, drain_s=max(60.0, args.serving_drain),
+                           slice_iterations=args.serving_slice)
     return {"offered_load": over, "at_0.8_completed_rate": under}
 
 
@@ -708,6 +711,8 @@ def main():
     ap.add_argument("--serving-iterations", type=int, default=1000)
     ap.add_argument("--serving-drain", type=float, default=10.0)
     ap.add_argument("--serving-max-pending", type=int, default=4096)
+    ap.add_argument("--serving-slice", type=int, default=0,
+                    help="server time slice in iterations (0: no slicing)")
     ap.add_argument("--serving-only", action="store_true",
                     help="run only the serving measurement and print its JSON object")
     ap.add_argument("--plain-sample", type=int, default=48)

@@ -432,7 +432,7 @@ typedef struct {
     int32_t slots;              /* batches in flight (one stream each), 1..16; 0 = 8 */
     int32_t max_batch;          /* most requests per batch; 0 = 256.  A batch holds
                                    one launch class (footprint x size, see
-                                   rcpsp_tabu_search) and at most 256 / 64 / 16
+                                   rcpsp_tabu_search) and at most 256 / 96 / 32
                                    requests of N up to 64 / 160 / more           */
     int64_t memory_budget;      /* device bytes of admitted requests; 0 = 1 GiB.
                                    A request larger than the budget is admitted

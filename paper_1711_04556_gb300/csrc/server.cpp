@@ -14,7 +14,7 @@
 //      request is oldest, then its requests in arrival order with identical
 //      search parameters, while the footprint fits the budget (a lone request
 //      is admitted even if larger), up to a batch size that shrinks with the
-//      instance size (256 / 64 / 16) and max_batch;
+//      instance size (256 / 96 / 32) and max_batch;
 //   3. sleeps on a condition variable until a submission or the next poll
 //      tick (no GPU spin: completion is an event query).
 // With slice_iterations > 0 a request of more iterations runs in slices:
@@ -240,7 +240,7 @@ int request_class(const rcpsp::PackedInstance &pk, const rcpsp_params &p) {
 
 int batch_limit(const rcpsp_server *s, int cls) {
     const int sz = cls % 3;
-    return std::max(1, std::min(s->cfg.max_batch, sz == 0 ? 256 : (sz == 1 ? 64 : 16)));
+    return std::max(1, std::min(s->cfg.max_batch, sz == 0 ? 256 : (sz == 1 ? 96 : 32)));
 }
 
 // Takes a batch for a free slot: the class whose oldest request is oldest,
