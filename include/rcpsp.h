@@ -286,7 +286,9 @@ int rcpsp_tabu_search_noalloc(rcpsp_ctx *ctx, const int32_t *ids, int32_t count,
  * words per step, swap distance, evaluator mix, batch size).  Instances are
  * tuned per launch class (see rcpsp_tabu_search), the unit a search launches
  * apart; classes with at most half as many searches as the GPU has SMs also
- * try clusters of 2, 4 and 8 CTAs per search.  When the call has more
+ * try clusters of 2, 4 and 8 CTAs per search; the three fastest shapes of
+ * a class are timed again with four times the trial iterations (up to the
+ * search's own) before one is kept.  When the call has more
  * than one class, the CTAs per search of each class are then refined with
  * the whole call running (the classes share the GPU), keeping a change only
  * if the call gets at least 3% faster.  The returned shape (any

@@ -204,7 +204,7 @@ size_t smem_bytes(const std::vector<LaunchItem> &items, int ngroups, int move_ca
     for (const LaunchItem &it : items) {
         const int pw = rcpsp::profile_words(it.mode, it.h.wps, it.h.ub, it.h.sum_cap);
         const rcpsp::StateLayout S =
-            rcpsp::state_layout(it.h.inst_words, it.h.n, it.tabu_len, it.delta, move_cap, pw, ngroups);
+            rcpsp::state_layout(it.h.inst_words, it.h.n, it.tabu_len, it.delta, move_cap, pw, ngroups, it.mode);
         words = std::max(words, S.total);
     }
     return static_cast<size_t>(words) * 4;
@@ -224,7 +224,8 @@ bool prefix_pays(const std::vector<LaunchItem> &items, int ngroups, int csize) {
 // count the largest one allows, and a few large searches can share clusters
 // of CTAs while many small ones take one CTA each.
 int footprint_class(const LaunchItem &it) {
-    return rcpsp::launch_class(rcpsp::profile_words(it.mode, it.h.wps, it.h.ub, it.h.sum_cap) + it.h.n, it.h.n);
+    const int pw = rcpsp::profile_words(it.mode, it.h.wps, it.h.ub, it.h.sum_cap);
+    return rcpsp::launch_class(rcpsp::group_area_words(it.mode, pw, it.h.n), it.h.n);
 }
 
 struct ClassLaunch {
@@ -1359,6 +1360,7 @@ int rcpsp_autotune(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcpsp_
         std::vector<rcpsp_stats> stats(cn);
         double best_rate = -1.0;
         int bG = 0, bW = 0, bC = 1;
+        std::vector<std::pair<double, std::array<int, 3>>> ranked;   // (rate, shape) of every trial
         const int gsz[] = {1, 2, 4, 8, 16, 32};
         const int wcnt[] = {1, 2, 3, 4, 6, 8, 10, 12, 16};
         // clusters pay when the class has fewer searches than the GPU has SMs,
@@ -1395,6 +1397,7 @@ int rcpsp_autotune(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcpsp_
                 long long ev = 0;
                 for (const rcpsp_stats &x : stats) ev += x.evaluated;
                 const double rate = ms > 0 ? static_cast<double>(ev > 0 ? ev : 1) / ms : 0.0;
+                ranked.push_back({rate, {G, W, C}});
                 if (rate > best_rate) {
                     best_rate = rate;
                     bG = G;
@@ -1402,6 +1405,43 @@ int rcpsp_autotune(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcpsp_
                     bC = C;
                 }
             }
+        // short trials can rank shapes by their first iterations only: the
+        // three best are timed again with four times as many iterations
+        if (ranked.size() > 1 && p->iterations > q.iterations) {
+            std::stable_sort(ranked.begin(), ranked.end(),
+                             [](const auto &a, const auto &b) { return a.first > b.first; });
+            rcpsp_params q4 = q;
+            q4.iterations = std::min(p->iterations, 4 * q.iterations);
+            double best4 = -1.0;
+            for (size_t t = 0; t < ranked.size() && t < 3; ++t) {
+                q4.group_size = ranked[t].second[0];
+                q4.warps_per_cta = ranked[t].second[1];
+                q4.cluster_size = ranked[t].second[2];
+                cudaEventRecord(e0, st);
+                int r = rcpsp_tabu_search(c, cids.data(), cn, &q4, stream);
+                if (r == RCPSP_OK) {
+                    cudaEventRecord(e1, st);
+                    r = rcpsp_get_schedules(c, cids.data(), cn, nullptr, nullptr, nullptr, stats.data());
+                }
+                if (r != RCPSP_OK) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return r;
+                }
+                float ms = 0.f;
+                cudaEventSynchronize(e1);
+                cudaEventElapsedTime(&ms, e0, e1);
+                long long ev = 0;
+                for (const rcpsp_stats &x : stats) ev += x.evaluated;
+                const double rate = ms > 0 ? static_cast<double>(ev > 0 ? ev : 1) / ms : 0.0;
+                if (rate > best4) {
+                    best4 = rate;
+                    bG = ranked[t].second[0];
+                    bW = ranked[t].second[1];
+                    bC = ranked[t].second[2];
+                }
+            }
+        }
         if (!bG) {
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
@@ -1620,7 +1660,7 @@ int rcpsp_evaluate_lists(rcpsp_ctx *c, int32_t id, const int32_t *lists, int32_t
     for (const auto &sh : shapes) {
         const int ng = sh[1] * (32 / sh[0]);
         const rcpsp::StateLayout S =
-            rcpsp::state_layout(in.h.inst_words, n, 0, 0, ng * rcpsp::align4(n), pw, ng);
+            rcpsp::state_layout(in.h.inst_words, n, 0, 0, ng * rcpsp::align4(n), pw, ng, it.mode);
         smem = static_cast<size_t>(S.total) * 4;
         if (smem + 1024 <= c->prop.sharedMemPerBlockOptin) {
             G = sh[0];

@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(512, 2) coop_kernel(const CoopItem *__restrict
         const InstHeader &h = it.h;
         const int n = h.n, mode = it.mode, delta = it.delta, tl = it.tabu_len, Ib = it.iterations;
         const int pw = profile_words(mode, h.wps, h.ub, h.sum_cap);
-        const StateLayout S = state_layout(h.inst_words, n, tl, delta, move_cap, pw, ngroups);
+        const StateLayout S = state_layout(h.inst_words, n, tl, delta, move_cap, pw, ngroups, mode);
         const SlotLayout SL = slot_layout(n, tl, delta);
         const int pk = PFX ? it.prefix_k : 0;
         const Prefix px{pk > 0 ? gsnap + static_cast<long long>(blockIdx.x) * gsnap_words : nullptr,

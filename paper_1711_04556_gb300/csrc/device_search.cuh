@@ -104,8 +104,9 @@ __device__ void stage_instance(int *sm, const int32_t *record, int words) {
 // (u == v leaves W unchanged), decoded by one group in lockstep with the
 // other groups of its warp.  A group with active == false follows the loops
 // without writing its scratch.  `area` is the group's interleaved scratch:
-// element e at area[e*NG]; the profile (or capacity state) comes first, then
-// es[i], the precedence earliest start of every activity.  Instead of
+// the time-indexed profile as 32-bit words (element e at area[e*NG]), or the
+// capacity state as 16-bit entries, then es[i], the precedence earliest
+// start of every activity, in 16 bits (see half_area).  Instead of
 // reading the finish times of i's predecessors when i is placed (the
 // precedence part of Alg. 7), every placed activity raises es[] of its successors, so the
 // placement of i starts from one broadcast load; the value is the same
@@ -118,21 +119,31 @@ __device__ __forceinline__ int activity_at(const int *W, int p, int u, int v) {
 }
 
 // es of every successor of i := max(es, f); inactive groups write nothing.
+// Earliest starts are 16-bit (every time value is at most RCPSP_MAX_HORIZON).
 template <int G>
-__device__ __forceinline__ void push_finish(const SInst &I, int i, int f, int *es, int NG, const Group<G> &g,
+__device__ __forceinline__ void push_finish(const SInst &I, int i, int f, short *es, int NG, const Group<G> &g,
                                             bool active) {
     const int e0 = I.soff[i], ns = active ? I.soff[i + 1] - e0 : 0;
     for (int b = g.lane; b < ns; b += G) {
-        int *x = es + I.slist[e0 + b] * NG;
-        *x = ::max(*x, f);
+        short *x = es + I.slist[e0 + b] * NG;
+        *x = static_cast<short>(::max(static_cast<int>(*x), f));
     }
 }
 
 template <int G>
-__device__ __forceinline__ void clear_es(int *es, int n, int NG, bool active, const Group<G> &g) {
+__device__ __forceinline__ void clear_es(short *es, int n, int NG, bool active, const Group<G> &g) {
     if (active)
         for (int x = g.lane; x < n; x += G) es[x * NG] = 0;
     __syncwarp();
+}
+
+// A group's 16-bit scratch from `area` (its first word): element e of
+// group gw of a warp is halfword e*NG + gw of the warp's area, so the groups
+// of a warp stay interleaved element by element as in the 32-bit sections.
+template <int G>
+__device__ __forceinline__ short *half_area(int *area, int word_offset, int NG) {
+    const int gw = (threadIdx.x & 31) / G;
+    return reinterpret_cast<short *>(area - gw + word_offset * NG) + gw;
 }
 
 // Kept decoder states of the current list (prefix reuse, see prefix_count),
@@ -218,7 +229,7 @@ __device__ int decode_time(const SInst &I, const int *W, int u, int v, bool acti
     const int n = I.n, ub = I.ub;
     const int ubs = ub > 0 ? ub : 1;              // stride of one resource-word plane
     uint32_t *prof = reinterpret_cast<uint32_t *>(area);
-    int *esa = area + WPS * ubs * NG;
+    short *esa = half_area<G>(area, WPS * ubs, NG);
     const uint32_t hi = I.hi;
     uint32_t capw[WPS];
 #pragma unroll
@@ -240,7 +251,8 @@ __device__ int decode_time(const SInst &I, const int *W, int u, int v, bool acti
             for (int w = 0; w < WPS; ++w)
                 for (int t = g.lane; t < F; t += G)
                     prof[(w * ubs + t) * NG] = __ldcg(sn + kPxMeta + w * ubs + t);
-            for (int x = g.lane; x < n; x += G) esa[x * NG] = __ldcg(sn + kPxMeta + WPS * ubs + x);
+            for (int x = g.lane; x < n; x += G)
+                esa[x * NG] = static_cast<short>(__ldcg(sn + kPxMeta + WPS * ubs + x));
         }
         __syncwarp();
     } else {
@@ -258,7 +270,7 @@ __device__ int decode_time(const SInst &I, const int *W, int u, int v, bool acti
                 for (int w = 0; w < WPS; ++w)
                     for (int t = g.lane; t < F; t += G)
                         __stcg(sn + kPxMeta + w * ubs + t, static_cast<int>(prof[(w * ubs + t) * NG]));
-                for (int x = g.lane; x < n; x += G) __stcg(sn + kPxMeta + WPS * ubs + x, esa[x * NG]);
+                for (int x = g.lane; x < n; x += G) __stcg(sn + kPxMeta + WPS * ubs + x, static_cast<int>(esa[x * NG]));
             }
             keep_meta<G>(I, W, px, p / px.K, sn, false, F, cmax, work, kPxMeta + WPS * F + n, active, g);
             __syncwarp();
@@ -368,8 +380,8 @@ __device__ int decode_capacity(const SInst &I, const int *W, int u, int v, bool 
                                const Group<G> &g, int &work, int &err, int *S_out, const Prefix &px,
                                bool produce) {
     const int n = I.n, m = I.m, sc = I.sum_cap;
-    int *cst = area;                                   // c_k, concatenated
-    int *esa = area + sc * NG;
+    short *cst = half_area<G>(area, 0, NG);             // c_k, concatenated, 16-bit
+    short *esa = cst + sc * NG;
     int cmax = 0;
     int wk = 0;                                        // this lane's Alg. 4 steps
     const int p0 = PFX ? prefix_start(px, u, produce) : 0;
@@ -379,8 +391,8 @@ __device__ int decode_capacity(const SInst &I, const int *W, int u, int v, bool 
         if (active) {
             cmax = __ldcg(sn + kPxCmax);
             if (g.lane == 0) wk = __ldcg(sn + kPxWork);
-            for (int j = g.lane; j < sc; j += G) cst[j * NG] = __ldcg(sn + kPxMeta + j);
-            for (int x = g.lane; x < n; x += G) esa[x * NG] = __ldcg(sn + kPxMeta + sc + x);
+            for (int j = g.lane; j < sc; j += G) cst[j * NG] = static_cast<short>(__ldcg(sn + kPxMeta + j));
+            for (int x = g.lane; x < n; x += G) esa[x * NG] = static_cast<short>(__ldcg(sn + kPxMeta + sc + x));
         }
         __syncwarp();
     } else {
@@ -397,8 +409,8 @@ __device__ int decode_capacity(const SInst &I, const int *W, int u, int v, bool 
             int *sn = px.base + (p / px.K - 1) * px.stride;
             const int wsum = g.sum(wk);
             if (active) {
-                for (int j = g.lane; j < sc; j += G) __stcg(sn + kPxMeta + j, cst[j * NG]);
-                for (int x = g.lane; x < n; x += G) __stcg(sn + kPxMeta + sc + x, esa[x * NG]);
+                for (int j = g.lane; j < sc; j += G) __stcg(sn + kPxMeta + j, static_cast<int>(cst[j * NG]));
+                for (int x = g.lane; x < n; x += G) __stcg(sn + kPxMeta + sc + x, static_cast<int>(esa[x * NG]));
             }
             keep_meta<G>(I, W, px, p / px.K, sn, true, 0, cmax, wsum, kPxMeta + sc + n, active, g);
             __syncwarp();
@@ -433,7 +445,7 @@ __device__ int decode_capacity(const SInst &I, const int *W, int u, int v, bool 
                 if (r == 0) continue;
                 const int R = I.cap[k];
                 const int T = s + d;
-                int *ck = cst + I.cbase[k] * NG;
+                short *ck = cst + I.cbase[k] * NG;
                 int alo = 0, ahi = R - r, blo = 0, bhi = R - r;
                 while (alo < ahi || blo < bhi) {
                     const int am = (alo + ahi) >> 1, bm = (blo + bhi) >> 1;
@@ -452,13 +464,13 @@ __device__ int decode_capacity(const SInst &I, const int *W, int u, int v, bool 
                 for (; j - 3 >= r + b; j -= 4) {
                     const int x0 = ck[(j - r) * NG], x1 = ck[(j - 1 - r) * NG];
                     const int x2 = ck[(j - 2 - r) * NG], x3 = ck[(j - 3 - r) * NG];
-                    ck[j * NG] = x0;
-                    ck[(j - 1) * NG] = x1;
-                    ck[(j - 2) * NG] = x2;
-                    ck[(j - 3) * NG] = x3;
+                    ck[j * NG] = static_cast<short>(x0);
+                    ck[(j - 1) * NG] = static_cast<short>(x1);
+                    ck[(j - 2) * NG] = static_cast<short>(x2);
+                    ck[(j - 3) * NG] = static_cast<short>(x3);
                 }
                 for (; j >= r + b; --j) ck[j * NG] = ck[(j - r) * NG];
-                for (int x = b; x < b + r; ++x) ck[x * NG] = T;
+                for (int x = b; x < b + r; ++x) ck[x * NG] = static_cast<short>(T);
                 wk += r + a;                            // Alg. 4's loop steps
             }
         if (act) {

@@ -134,9 +134,18 @@ struct StateLayout {
     int W, pos, Wbest, fsp, lpp, stl, tc, moves;
     int groups;          // first word of the per-warp group areas
     int prof_words;      // profile words of one group (time- or capacity-indexed)
-    int group_words;     // profile + finish times of one group
+    int group_words;     // words of one group's scratch (group_area_words)
     int total;           // words of dynamic shared memory
 };
+
+// Words of one decoding group's shared scratch.  Time-indexed: the packed
+// profile (prof_words 32-bit words), then the N earliest starts in 16 bits;
+// capacity-indexed: the capacity state (prof_words = sum R_k entries) and
+// the N earliest starts, all in 16 bits.  Every time value is at most
+// RCPSP_MAX_HORIZON (32767), so 16 bits hold it.
+RC_HD int group_area_words(int mode, int prof_words, int n) {
+    return mode == RCPSP_EVAL_CAPACITY ? (prof_words + n + 1) / 2 : prof_words + (n + 1) / 2;
+}
 
 RC_HD int profile_words(int mode, int wps, int ub, int sum_cap) {
     return mode == RCPSP_EVAL_CAPACITY ? sum_cap : wps * (ub > 0 ? ub : 1);
@@ -156,8 +165,8 @@ RC_HD int prefix_stride(int n, int prof_words) { return align4(kPxMeta + prof_wo
 RC_HD int prefix_words(int n, int prof_words, int K) { return prefix_count(n, K) * prefix_stride(n, prof_words); }
 
 // Launch class of a search: its footprint -- per-group scratch words `gw`
-// (profile or capacity state plus N earliest starts) up to 512, 2K, 8K, or
-// more -- times its size (N up to 64, up to 160, larger).  Searches of one
+// (group_area_words: profile or capacity state plus N earliest starts) up
+// to 512, 2K, 8K, or more -- times its size (N up to 64, up to 160, larger).  Searches of one
 // class share a launch and its shape; the finest footprint level keeps the
 // capacity-indexed searches (a few hundred words per group) apart from the
 // time-indexed ones of the same size, whose profiles would otherwise size
@@ -170,7 +179,7 @@ RC_HD int launch_class(int gw, int n) {
 }
 
 RC_HD StateLayout state_layout(int inst_words, int n, int tabu_len, int delta, int move_cap,
-                               int prof_words, int ngroups) {
+                               int prof_words, int ngroups, int mode) {
     StateLayout S;
     int o = inst_words;
     S.W = o;     o += align4(n);
@@ -183,7 +192,7 @@ RC_HD StateLayout state_layout(int inst_words, int n, int tabu_len, int delta, i
     S.moves = o; o += align4(move_cap);
     S.groups = o;
     S.prof_words = prof_words;
-    S.group_words = prof_words + n;
+    S.group_words = group_area_words(mode, prof_words, n);
     o += ngroups * S.group_words;
     S.total = o;
     return S;

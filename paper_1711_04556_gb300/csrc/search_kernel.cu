@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(512, 2) evaluate_kernel(LaunchItem item, const
     const int n = h.n, mode = item.mode;
     const int pw = profile_words(mode, h.wps, h.ub, h.sum_cap);
     // per-group list buffers take the place of the move buffer
-    const StateLayout S = state_layout(h.inst_words, n, 0, 0, ngroups * align4(n), pw, ngroups);
+    const StateLayout S = state_layout(h.inst_words, n, 0, 0, ngroups * align4(n), pw, ngroups, mode);
     stage_instance(sm, item.record, h.inst_words);
     __syncthreads();
     const SInst I = bind_instance(sm, h);

@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(NT, 2) search_kernel(const LaunchItem *__restr
         const int n = h.n, mode = it.mode, delta = it.delta, tl = it.tabu_len;
         const int pw = profile_words(mode, h.wps, h.ub, h.sum_cap);
         const int pk = PFX ? it.prefix_k : 0;
-        const StateLayout S = state_layout(h.inst_words, n, tl, delta, move_cap, pw, ngroups);
+        const StateLayout S = state_layout(h.inst_words, n, tl, delta, move_cap, pw, ngroups, mode);
         const Prefix px{pk > 0 ? gsnap + static_cast<long long>(blockIdx.x) * gsnap_words : nullptr,
                         pk > 0 ? pk : 1, prefix_count(n, pk), prefix_stride(n, pw)};
         stage_instance(sm, it.record, h.inst_words);

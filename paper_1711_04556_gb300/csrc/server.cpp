@@ -235,7 +235,8 @@ void harvest(rcpsp_server *s, Slot &sl) {
 // can share clusters of CTAs.
 int request_class(const rcpsp::PackedInstance &pk, const rcpsp_params &p) {
     const int mode = p.eval_mode == RCPSP_EVAL_AUTO ? pk.h.sel_mode : p.eval_mode;
-    return rcpsp::launch_class(rcpsp::profile_words(mode, pk.h.wps, pk.h.ub, pk.h.sum_cap) + pk.h.n, pk.h.n);
+    const int pw = rcpsp::profile_words(mode, pk.h.wps, pk.h.ub, pk.h.sum_cap);
+    return rcpsp::launch_class(rcpsp::group_area_words(mode, pw, pk.h.n), pk.h.n);
 }
 
 int batch_limit(const rcpsp_server *s, int cls) {
