@@ -289,9 +289,9 @@ int rcpsp_tabu_search_noalloc(rcpsp_ctx *ctx, const int32_t *ids, int32_t count,
  * try clusters of 2, 4 and 8 CTAs per search; the three fastest shapes of
  * a class are timed again with four times the trial iterations (up to the
  * search's own) before one is kept.  When the call has more
- * than one class, the CTAs per search of each class are then refined with
- * the whole call running (the classes share the GPU), keeping a change only
- * if the call gets at least 3% faster.  The returned shape (any
+ * than one class, each class's three fastest shapes and the other cluster
+ * sizes of its pick are then timed with the whole call running (the classes
+ * share the GPU), keeping a change only if the call gets at least 3% faster.  The returned shape (any
  * output pointer may be NULL) is the one of the largest class.  Later searches with group_size =
  * warps_per_cta = cluster_size = 0 and the same signature use it.  When the
  * environment variable RCPSP_TUNE_CACHE names a file, the table is written

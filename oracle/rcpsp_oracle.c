@@ -40,7 +40,7 @@
  *       path length and the average capacity, and the direction of Sec. 7.2
  *       (capacity-indexed for long schedules with low capacities):
  *       capacity-indexed iff CP > SEL_K * avgCap, compared exactly as
- *       CP * M > SEL_K * sum R_k.  SEL_K = 24 was fitted, as Sec. 5.4 does,
+ *       CP * M > SEL_K * sum R_k.  SEL_K = 12 was fitted, as Sec. 5.4 does,
  *       by timing both evaluators on a grid of instances on the target GPU.
  *   R9  "Evaluated schedules" counts neighbour decodes only (every feasible
  *       move, tabu or not); the initial and final decodes are not counted.
@@ -53,7 +53,7 @@
 #include <string.h>
 
 /* Selection constant of reading R8. */
-#define SEL_K 24
+#define SEL_K 12
 
 static int imax(int a, int b) { return a > b ? a : b; }
 

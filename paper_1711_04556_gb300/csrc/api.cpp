@@ -1344,6 +1344,7 @@ int rcpsp_autotune(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcpsp_
     q.resume = 0;
     int ret_G = 0, ret_W = 0, ret_C = 0, ret_count = -1;
     std::vector<std::string> tuned_keys;        // signatures of the classes tuned here
+    std::vector<std::vector<std::array<int, 3>>> tuned_top;   // their three fastest shapes alone
     std::string ret_key;
     // each footprint class is tuned on its own (searches launch them apart)
     for (int cls = 0; cls < kClasses; ++cls) {
@@ -1462,12 +1463,16 @@ int rcpsp_autotune(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcpsp_
             ret_key = key;
         }
         tuned_keys.push_back(key);
+        std::vector<std::array<int, 3>> top;
+        for (size_t t = 0; t < ranked.size() && t < 3; ++t) top.push_back(ranked[t].second);
+        tuned_top.push_back(top);
     }
-    // The classes of a call share the GPU, so a cluster size that is best
-    // for a class alone can hold SMs the other classes need: with more than
-    // one class, each class's CTAs per search are refined with the whole
-    // call running (every class at its tuned shape), keeping a change only
-    // if the call gets faster.
+    // The classes of a call share the GPU, so a shape that is best for a
+    // class alone can hold SMs the other classes need: with more than one
+    // class, each class's three fastest shapes alone and the other cluster
+    // sizes of its pick are timed with the whole call running (every other
+    // class at its current shape), keeping a change only if the call gets at
+    // least 3% faster.
     if (tuned_keys.size() > 1) {
         q.group_size = q.warps_per_cta = q.cluster_size = 0;
         std::vector<rcpsp_stats> stats(count);
@@ -1496,25 +1501,32 @@ int rcpsp_autotune(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcpsp_
             for (auto &e : c->tuned)
                 if (e.first == tuned_keys[t]) sh = &e.second;
             if (!sh) continue;
-            const int orig = (*sh)[2];
-            int keep = orig;
-            for (int C = 1; C <= 8; C *= 2) {
-                if (C == orig || (C > 1 && ((*sh)[0] < 4 || (*sh)[1] < 4))) continue;
-                (*sh)[2] = C;
+            std::vector<std::array<int, 3>> cand = tuned_top[t];
+            for (int C = 1; C <= 8; C *= 2)
+                if (C != (*sh)[2] && (C == 1 || ((*sh)[0] >= 4 && (*sh)[1] >= 4))) cand.push_back({(*sh)[0], (*sh)[1], C});
+            const std::array<int, 3> orig = *sh;
+            std::array<int, 3> keep = orig;
+            for (const std::array<int, 3> &x : cand) {
+                if (x == orig) continue;
+                *sh = x;
                 double ms = 0;
                 const int rr = time_call(&ms);
-                if (rr == RCPSP_E_TOO_LARGE) continue;        // does not fit at this cluster size
+                if (rr == RCPSP_E_TOO_LARGE) continue;        // does not fit at this shape
                 if (rr != RCPSP_OK) {
                     r = rr;
                     break;
                 }
                 if (ms < 0.97 * base_ms) {
                     base_ms = ms;
-                    keep = C;
+                    keep = x;
                 }
             }
-            (*sh)[2] = keep;
-            if (tuned_keys[t] == ret_key) ret_C = keep;
+            *sh = keep;
+            if (tuned_keys[t] == ret_key) {
+                ret_G = keep[0];
+                ret_W = keep[1];
+                ret_C = keep[2];
+            }
         }
         if (r != RCPSP_OK) {
             cudaEventDestroy(e0);

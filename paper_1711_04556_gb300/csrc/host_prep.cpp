@@ -20,10 +20,10 @@ namespace {
 // critical path length and the average capacity -- and the direction of
 // Sec. 7.2 (capacity-indexed for long schedules with low capacities):
 // capacity-indexed iff CP > K * avgCap, compared exactly as CP * M > K * sumR.
-// K = 24 was fitted by timing both evaluators on a grid of instances on
+// K = 12 was fitted by timing both evaluators on a grid of instances on
 // GB300 (selection_study.py), as Sec. 5.4 derives its classes from
 // measured run times.
-constexpr long long kSelK = 24;
+constexpr long long kSelK = 12;
 
 int fail(std::string &err, int code, const std::string &msg) {
     err = msg;

@@ -552,19 +552,19 @@ def chain_instance(durs, cap):
 
 
 def test_selection_rule(oracle):
-    """Capacity-indexed exactly when CP * M > 24 * sum R_k (reading R8), the
+    """Capacity-indexed exactly when CP * M > 12 * sum R_k (reading R8), the
     critical path taken by path enumeration; equality stays time-indexed."""
     long_low = [generate(s, 10 + s % 5, 1 + s % 2, 210, 10, dmax=50, rmax=2, stream=96) for s in range(30)]
     seen = set()
     for inst in medium_instances(30, first=1200) + long_low:
         cp = max(sum(int(inst.dur[x]) for x in p[:-1]) for p in all_paths(inst, 0, inst.n - 1))
-        want = 2 if cp * inst.m > 24 * int(inst.cap.sum()) else 1
+        want = 2 if cp * inst.m > 12 * int(inst.cap.sum()) else 1
         assert oracle.select_mode(inst) == want
         seen.add(want)
     assert seen == {1, 2}
     for R in (1, 2, 5):
-        assert oracle.select_mode(chain_instance([12 * R, 12 * R], R)) == 1          # CP = 24 R
-        assert oracle.select_mode(chain_instance([12 * R, 12 * R + 1], R)) == 2      # CP = 24 R + 1
+        assert oracle.select_mode(chain_instance([6 * R, 6 * R], R)) == 1            # CP = 12 R
+        assert oracle.select_mode(chain_instance([6 * R, 6 * R + 1], R)) == 2        # CP = 12 R + 1
 
 
 # ------------------------------------------------- checker: negative cases
