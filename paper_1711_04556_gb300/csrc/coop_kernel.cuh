@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(512, 2) coop_kernel(const CoopItem *__restrict
                                                     int *__restrict__ queue, int move_cap, CoopConfig cfg,
                                                     int *__restrict__ gsnap, int gsnap_words) {
     extern __shared__ __align__(16) int sm[];
-    __shared__ int s_mq[2];
+    __shared__ int s_mq[3];   // compaction and drain cursors, kept snapshots
     __shared__ int s_hist[32];
     __shared__ int s_item, s_C, s_Cbb, s_widx, s_it, s_err, s_improved;
     __shared__ unsigned long long s_best, s_t0;
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(512, 2) coop_kernel(const CoopItem *__restrict
         const SlotLayout SL = slot_layout(n, tl, delta);
         const int pk = PFX ? it.prefix_k : 0;
         const Prefix px{pk > 0 ? gsnap + static_cast<long long>(blockIdx.x) * gsnap_words : nullptr,
-                        pk > 0 ? pk : 1, prefix_count(n, pk), prefix_stride(n, pw)};
+                        pk > 0 ? pk : 1, prefix_count(n, pk), prefix_stride(n, pw), pk > 0 ? s_mq + 2 : nullptr};
         const int tcw = (n * delta + 31) / 32;
         stage_instance(sm, it.record, h.inst_words);
         const SInst I = bind_instance(sm, h);

@@ -19,6 +19,14 @@ namespace cg = cooperative_groups;
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kErrHorizon = 1;     // a profile window ran past UB
+constexpr int kErrWait = 4;        // a wait for a kept decoder state gave up
+constexpr unsigned long long kWaitNs = 2000000000ull;   // limit of that wait
+
+__device__ __forceinline__ unsigned long long global_timer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 // G lanes of a warp that decode one neighbour.  All groups of a warp run in
 // lockstep: a loop whose trip count may differ between groups is driven by a
@@ -151,11 +159,48 @@ __device__ __forceinline__ short *half_area(int *area, int word_offset, int NG) 
 // snapshot j (1..count) is the state before position j*K, at base +
 // (j-1)*stride: the kPxMeta meta words, then the profile (time-indexed: WPS
 // planes of UB words; capacity-indexed: the c_k) and the N earliest starts.
-// base == nullptr: no prefix reuse.
+// base == nullptr: no prefix reuse.  `ready` (shared memory) counts the
+// snapshots of the current list kept so far in this iteration: the producing
+// group publishes each one as it is written (release), and a neighbour decode
+// that restores snapshot j waits until ready >= j (acquire), so the
+// neighbours start before the producer has finished.  ready == nullptr: the
+// snapshots are complete before any neighbour decode starts.
 struct Prefix {
     int *base;
     int K, count, stride;
+    int *ready;
 };
+
+__device__ __forceinline__ int load_acquire_cta(const int *x) {
+    int v;
+    asm volatile("ld.acquire.cta.shared::cta.b32 %0, [%1];"
+                 : "=r"(v)
+                 : "r"(static_cast<unsigned>(__cvta_generic_to_shared(x)))
+                 : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void store_release_cta(int *x, int v) {
+    asm volatile("st.release.cta.shared::cta.b32 [%0], %1;"
+                 :
+                 : "r"(static_cast<unsigned>(__cvta_generic_to_shared(x))), "r"(v)
+                 : "memory");
+}
+
+// Waits until *ready >= need, for at most kWaitNs; on giving up sets
+// kErrWait (the search then reports RCPSP_E_DEVICE).  The producer never
+// waits on a consumer, so a correct kernel always gets there.
+__device__ __forceinline__ void wait_kept(const int *ready, int need, int &err) {
+    if (need <= 0 || load_acquire_cta(ready) >= need) return;
+    const unsigned long long t0 = global_timer_ns();
+    while (load_acquire_cta(ready) < need) {
+        if (global_timer_ns() - t0 > kWaitNs) {
+            err |= kErrWait;
+            return;
+        }
+        __nanosleep(64);
+    }
+}
 
 // Work counters of the decodes of a CTA (kTally* order; see rcpsp_stats):
 // `t` accumulates placements, Alg. 6 update steps or Eq. 7 reads, successor
@@ -219,6 +264,24 @@ __device__ __forceinline__ int prefix_start(const Prefix &px, int u, bool produc
     return ::min(u / px.K, px.count) * px.K;
 }
 
+// Before a warp's neighbour decodes restore their kept states: wait until
+// the snapshots they restore (the largest index over the warp's groups) are
+// published.  Every lane of the warp calls it.
+__device__ __forceinline__ void await_prefix(const Prefix &px, int p0, bool active, bool produce, int &err) {
+    if (!px.ready || produce) return;
+    const int need = __reduce_max_sync(kFull, active ? p0 / px.K : 0);
+    wait_kept(px.ready, need, err);
+}
+
+// After the producing warp kept snapshot j: make its stores (every lane's)
+// visible to the block, then publish j.  Every lane of the warp calls it.
+__device__ __forceinline__ void publish_prefix(const Prefix &px, int j) {
+    if (!px.ready) return;
+    __threadfence_block();
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) store_release_cta(px.ready, j);
+}
+
 // Time-indexed decode, WPS = 32-bit words per time step of the packed profile.
 template <int G, int WPS, bool PFX>
 __device__ int decode_time(const SInst &I, const int *W, int u, int v, bool active, int *area, int NG,
@@ -240,6 +303,7 @@ __device__ int decode_time(const SInst &I, const int *W, int u, int v, bool acti
     int F = 0;
     int cmax = 0;
     const int p0 = PFX ? prefix_start(px, u, produce) : 0;
+    if (PFX) await_prefix(px, p0, active, produce, err);
     if (PFX && p0 > 0) {
         // start from the kept state of the current list before position p0
         const int *sn = px.base + (p0 / px.K - 1) * px.stride;
@@ -274,6 +338,7 @@ __device__ int decode_time(const SInst &I, const int *W, int u, int v, bool acti
             }
             keep_meta<G>(I, W, px, p / px.K, sn, false, F, cmax, work, kPxMeta + WPS * F + n, active, g);
             __syncwarp();
+            publish_prefix(px, p / px.K);
         }
         const int inext = activity_at<G>(W, p + 1 < n ? p + 1 : p, u, v);
         const int es = esa[i * NG];
@@ -385,6 +450,7 @@ __device__ int decode_capacity(const SInst &I, const int *W, int u, int v, bool 
     int cmax = 0;
     int wk = 0;                                        // this lane's Alg. 4 steps
     const int p0 = PFX ? prefix_start(px, u, produce) : 0;
+    if (PFX) await_prefix(px, p0, active, produce, err);
     if (PFX && p0 > 0) {
         // start from the kept state of the current list before position p0
         const int *sn = px.base + (p0 / px.K - 1) * px.stride;
@@ -414,6 +480,7 @@ __device__ int decode_capacity(const SInst &I, const int *W, int u, int v, bool 
             }
             keep_meta<G>(I, W, px, p / px.K, sn, true, 0, cmax, wsum, kPxMeta + sc + n, active, g);
             __syncwarp();
+            publish_prefix(px, p / px.K);
         }
         const int inext = activity_at<G>(W, p + 1 < n ? p + 1 : p, u, v);
         const int es = esa[i * NG];
@@ -482,7 +549,6 @@ __device__ int decode_capacity(const SInst &I, const int *W, int u, int v, bool 
         i = inext;
     }
     work += g.sum(wk);
-    (void)err;
     return cmax;
 }
 
@@ -490,7 +556,7 @@ __device__ int decode_capacity(const SInst &I, const int *W, int u, int v, bool 
 template <int G, bool PFX = false>
 __device__ __forceinline__ int decode(const SInst &I, int mode, const int *W, int u, int v, bool active,
                                       int *area, int NG, const Group<G> &g, long long &work, int &err,
-                                      int *S_out = nullptr, const Prefix &px = Prefix{nullptr, 1, 0, 0},
+                                      int *S_out = nullptr, const Prefix &px = Prefix{nullptr, 1, 0, 0, nullptr},
                                       bool produce = false) {
     int wk = 0, c;
     if (mode == RCPSP_EVAL_CAPACITY)
@@ -503,12 +569,6 @@ __device__ __forceinline__ int decode(const SInst &I, int mode, const int *W, in
         c = decode_time<G, 4, PFX>(I, W, u, v, active, area, NG, g, wk, err, S_out, px, produce);
     work += wk;
     return c;
-}
-
-__device__ __forceinline__ unsigned long long global_timer_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
 }
 
 __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long x) {
@@ -562,7 +622,7 @@ __device__ __forceinline__ unsigned long long best_admissible_key(
         const SInst &I, int mode, const int *W, const int *pos, int *fsp, int *lpp, const unsigned *tc,
         int *moves, int *area, int n, int delta, int nslots, unsigned dmagic, int move_cap, int aspiration,
         int csize, unsigned crank, int *s_mq, long long *s_eval, long long &my_work, int &err,
-        const Prefix &px = Prefix{nullptr, 1, 0, 0}, TallyRef tally = TallyRef{nullptr, nullptr}) {
+        const Prefix &px = Prefix{nullptr, 1, 0, 0, nullptr}, TallyRef tally = TallyRef{nullptr, nullptr}) {
     constexpr int NG = 32 / G;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int warp = tid >> 5, wl = tid & 31;
@@ -579,35 +639,16 @@ __device__ __forceinline__ unsigned long long best_admissible_key(
         lpp[p] = l;
     }
     const int upd_all = mode == RCPSP_EVAL_CAPACITY ? I.sum_used : I.ub;
-    if (PFX && px.base && warp == 0) {
-        // prefix reuse: one group decodes the current list and keeps its
-        // state before positions K, 2K, ... (its work is not a neighbour's)
-        long long w0 = 0;
-        decode<G, PFX>(I, mode, W, 0, 0, gw == 0, area, NG, g, w0, err, nullptr, px, true);
-        if (tally.t) {
-            // a full decode, and the kept states it wrote
-            __syncwarp();
-            int kw = 0;
-            for (int j = 1 + wl; j <= px.count; j += 32) kw += __ldcg(px.base + (j - 1) * px.stride + kPxWords);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) kw += __shfl_xor_sync(kFull, kw, o);
-            if (wl == 0) {
-                tally.t[kTallyPlaced] += n;
-                tally.t[kTallyUpd] += upd_all;
-                tally.t[kTallySucc] += I.n_arcs;
-                tally.t[kTallyKept] += kw;
-                tally.t[kTallySteps] += w0;
-            }
-        }
-    }
-    __syncthreads();
     unsigned long long my_key = ~0ull;
     const int pass = ::min(nthr, move_cap);      // slots of one filter pass (<= move_cap)
     int base = 0;
+    if (nslots <= 0) __syncthreads();            // no moves (N <= 3): nothing to keep either
     while (base < nslots) {
+        const bool first = base == 0;
         if (tid == 0) {
             s_mq[0] = 0;                          // compaction cursor
             s_mq[1] = 0;                          // drain cursor
+            if (first && px.ready) *px.ready = 0;   // snapshots of W kept so far
         }
         __syncthreads();
         // 2. feasible moves, compacted, pass by pass while a pass still fits
@@ -635,7 +676,30 @@ __device__ __forceinline__ unsigned long long best_admissible_key(
             base += pass;
         }
         // 3. decode the neighbours: the groups of a warp take NG consecutive
-        // moves at a time and decode them in lockstep
+        // moves at a time and decode them in lockstep.  With prefix reuse,
+        // warp 0 first decodes the current list and keeps its state before
+        // positions K, 2K, ... (its work is not a neighbour's), publishing
+        // each as it goes, while the other warps start on the moves.
+        if (PFX && px.base && first && warp == 0) {
+            long long w0 = 0;
+            decode<G, PFX>(I, mode, W, 0, 0, gw == 0, area, NG, g, w0, err, nullptr, px, true);
+            if (px.ready && wl == 0) store_release_cta(px.ready, px.count);
+            if (tally.t) {
+                // a full decode, and the kept states it wrote
+                __syncwarp();
+                int kw = 0;
+                for (int j = 1 + wl; j <= px.count; j += 32) kw += __ldcg(px.base + (j - 1) * px.stride + kPxWords);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) kw += __shfl_xor_sync(kFull, kw, o);
+                if (wl == 0) {
+                    tally.t[kTallyPlaced] += n;
+                    tally.t[kTallyUpd] += upd_all;
+                    tally.t[kTallySucc] += I.n_arcs;
+                    tally.t[kTallyKept] += kw;
+                    tally.t[kTallySteps] += w0;
+                }
+            }
+        }
         for (;;) {
             int q0 = 0;
             if (wl == 0) q0 = atomicAdd(&s_mq[1], NG);

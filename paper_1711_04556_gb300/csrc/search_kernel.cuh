@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(NT, 2) search_kernel(const LaunchItem *__restr
                                                       int *__restrict__ queue, int move_cap, int csize,
                                                       int *__restrict__ gsnap, int gsnap_words) {
     extern __shared__ __align__(16) int sm[];
-    __shared__ int s_mq[2];
+    __shared__ int s_mq[3];   // compaction and drain cursors, kept snapshots
     __shared__ int s_item, s_C, s_Cbest, s_widx, s_it, s_improved, s_err, s_it0, s_it_end;
     __shared__ unsigned long long s_bestp[2], s_t0;      // best key of the iteration, by parity
     __shared__ long long s_eval, s_work;
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(NT, 2) search_kernel(const LaunchItem *__restr
         const int pk = PFX ? it.prefix_k : 0;
         const StateLayout S = state_layout(h.inst_words, n, tl, delta, move_cap, pw, ngroups, mode);
         const Prefix px{pk > 0 ? gsnap + static_cast<long long>(blockIdx.x) * gsnap_words : nullptr,
-                        pk > 0 ? pk : 1, prefix_count(n, pk), prefix_stride(n, pw)};
+                        pk > 0 ? pk : 1, prefix_count(n, pk), prefix_stride(n, pw), pk > 0 ? s_mq + 2 : nullptr};
         stage_instance(sm, it.record, h.inst_words);
         const SInst I = bind_instance(sm, h);
         int *W = sm + S.W;
