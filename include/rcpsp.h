@@ -104,6 +104,17 @@ typedef struct {
                                    then k2 resumed equal k1+k2 in one call.  The
                                    trace of a resumed call holds its own
                                    iterations.                                    */
+    int32_t slices;             /* scheduling of a launch class with more searches
+                                   than the GPU holds at once (not of the
+                                   results, which are the same either way): each
+                                   search runs in `slices` slices of
+                                   ceil(iterations / slices) iterations, every
+                                   search's first slice before any second one,
+                                   the state kept in device memory in between, so
+                                   that the searches that start last do not run
+                                   alone at the end of the call.  0 = choose
+                                   automatically, 1 = never, 2..64 = that many in
+                                   every class.  Not part of the paper.           */
 } rcpsp_params;
 
 /* Result statistics of one instance. */
@@ -186,11 +197,18 @@ int rcpsp_free_instances(rcpsp_ctx *ctx, const int32_t *ids, int32_t count);
  * of one CTA per search whose neighbourhoods mostly fit one decode round
  * gives its few outliers (at most 1/16 of the class, initial list with more
  * feasible swaps than the CTA has decoding groups) a launch of their own
- * with clusters of 2-8 CTAs, started first.  A class whose iterations take several decode rounds per CTA keeps
- * the decoder state of the current list every K positions and starts each
- * neighbour's decode from the last state before its first swapped position
- * (prefix reuse; results and counts are those of full decodes).  The call
- * is asynchronous.  Results stay on the device until rcpsp_get_schedules.
+ * with clusters of 2-8 CTAs, started first.  A class whose iterations take
+ * several decode rounds per CTA keeps the decoder state of the current list
+ * every K positions and starts each neighbour's decode from the last state
+ * before its first swapped position (prefix reuse; results and counts are
+ * those of full decodes).  A class with at least 1.5 times as many searches
+ * as its launch holds at once is sliced (rcpsp_params.slices): its searches
+ * take turns in slices of iterations, so that the ones that would start last
+ * do not run alone at the end; a CTA that pops a slice whose previous slice
+ * another CTA still runs waits for it, and gives the search up with
+ * status RCPSP_E_DEVICE only if that search makes no progress for 10 s.
+ * Device memory of the call (plan, kept states, slice states) comes from
+ * the context's allocator.  The call is asynchronous.  Results stay on the device until rcpsp_get_schedules.
  * ids: host, [count], loaded instances.  Errors, before anything is
  * launched: RCPSP_E_INVALID_ARG (a parameter out of range, resume without a
  * state kept with the same swap distance, tabu length and evaluator),
@@ -264,10 +282,11 @@ int rcpsp_coop_search(rcpsp_ctx *ctx, const int32_t *ids, int32_t count, const r
  * array holds (8190; more gives RCPSP_E_TOO_LARGE), no trace, no graph
  * capture and no checkpoints (record_trace, use_graph, checkpoint or resume
  * = 1 gives RCPSP_E_INVALID_ARG).  The call makes one launch with one
- * launch shape for all its instances: no launch classes, no prefix reuse
- * and one CTA per search (cluster_size other than 0 or 1 gives
- * RCPSP_E_INVALID_ARG), because the per-class queues, the kept prefix
- * states and the cluster plan would need context memory.  Results are the
+ * launch shape for all its instances: no launch classes, no prefix reuse,
+ * no slices (`slices` is ignored) and one CTA per search (cluster_size
+ * other than 0 or 1 gives RCPSP_E_INVALID_ARG), because the per-class
+ * queues, the kept prefix and slice states and the cluster plan would need
+ * context memory.  Results are the
  * same as rcpsp_tabu_search's; throughput on batches of uneven sizes can be
  * lower.  The
  * first call on a device also looks up the array's device address with
@@ -392,7 +411,7 @@ typedef struct {
     int32_t prefix_reuse;       /* 1: neighbours start from kept decoder states    */
     int32_t shape_source;       /* 0: built-in defaults, 1: the context's table of
                                    measured shapes (rcpsp_autotune), 2: the caller */
-    int32_t reserved;
+    int32_t slices;             /* slices per search (rcpsp_params.slices); 1: none */
     int64_t smem_bytes;         /* dynamic shared memory per CTA                   */
 } rcpsp_launch_info;
 

@@ -67,6 +67,7 @@ struct HostRange {
 constexpr int kClasses = rcpsp::kLaunchClasses;   // launch classes of one call (see footprint_class)
 constexpr int kMaxLaunches = 2 * kClasses;   // each class and its launch of clustered outliers
 constexpr int kAuxStreams = kMaxLaunches - 1;
+constexpr int kAutoSlices = 8;                  // slices per search when a class is sliced automatically
 
 }  // namespace
 
@@ -97,6 +98,8 @@ struct rcpsp_ctx {
     cudaEvent_t fork = nullptr, join[kAuxStreams] = {};
     std::vector<long long> g_launch_sig;
     int32_t *snap_dev = nullptr;        // kept prefix states of the CTAs (prefix reuse)
+    int32_t *slice_dev = nullptr;       // sync counters and slice states of sliced launches
+    size_t slice_cap = 0;
     size_t snap_cap = 0;
     // co-operative searches: plan, initial lists, random words and working sets
     // instance upload: pinned staging and a stream of its own, so that a
@@ -230,6 +233,8 @@ int footprint_class(const LaunchItem &it) {
 
 struct ClassLaunch {
     int offset = 0, count = 0, G = 0, threads = 0, blocks = 0, move_cap = 0, csize = 1;
+    int nslices = 1;             // slices per search (SliceSched); 1: not sliced
+    size_t slice_off = 0;        // first word of its sync counters and slice states in slice_dev
     bool prefix = false;         // prefix reuse (kernel variant, kept states in global scratch)
     int snap_words = 0;          // kept-state words per CTA
     size_t snap_off = 0;         // its first word in the context's scratch
@@ -442,6 +447,7 @@ int rcpsp_destroy(rcpsp_ctx *c) {
     dev_free(c, c->items_dev, c->items_cap, nullptr);
     dev_free(c, c->queue_dev, 4 * kMaxLaunches, nullptr);
     dev_free(c, c->coop_dev, c->coop_cap, nullptr);
+    dev_free(c, c->slice_dev, c->slice_cap, nullptr);
     dev_free(c, c->snap_dev, c->snap_cap, nullptr);
     if (c->items_host) cudaFreeHost(c->items_host);
     if (c->coop_host) cudaFreeHost(c->coop_host);
@@ -660,7 +666,7 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
     if (p->iterations < 0 || p->max_swap_dist < 0 || p->tabu_len < 0 || p->tabu_len > RCPSP_MAX_TABU ||
         p->eval_mode < 0 || p->eval_mode > 2 || p->warps_per_cta < 0 ||
         p->warps_per_cta > rcpsp::kSearchMaxWarps || p->checkpoint < 0 || p->checkpoint > 1 || p->resume < 0 ||
-        p->resume > 1)
+        p->resume > 1 || p->slices < 0 || p->slices > rcpsp::kMaxSlices)
         return set_err(c, RCPSP_E_INVALID_ARG, "bad search parameters");
     const int gs = p->group_size;
     if (gs != 0 && gs != 1 && gs != 2 && gs != 4 && gs != 8 && gs != 16 && gs != 32)
@@ -831,11 +837,43 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
         }
         launches.push_back(L);
     }
+    // Slices (rcpsp_params.slices): automatically when a class has at least
+    // half as many searches again as the CTAs (or clusters) of its launch
+    // hold at once.  With fewer, most of a class runs in one wave anyway and
+    // the searches that start late are mostly short (they reach the
+    // critical path early), while slicing would make long searches wait for
+    // the CTAs of others.
+    for (ClassLaunch &L : launches) {
+        const int held = L.blocks / std::max(1, L.csize);
+        L.nslices = p->slices ? p->slices : (2 * L.count >= 3 * held ? kAutoSlices : 1);
+        if (p->iterations < 2) L.nslices = 1;
+    }
     // launches of clustered outliers first, then classes of more work, so
     // that the long searches of a call are not queued behind short ones for SMs
     std::stable_sort(launches.begin(), launches.end(), [](const ClassLaunch &a, const ClassLaunch &b) {
         return a.outliers != b.outliers ? a.outliers : a.cost > b.cost;
     });
+    // slice scratch: per sliced class, two sync words per search, then the
+    // searches' slice states
+    {
+        size_t need = 0;
+        for (ClassLaunch &L : launches) {
+            if (L.nslices <= 1) continue;
+            L.slice_off = need;
+            size_t o = rcpsp::align4(2 * L.count);
+            for (int k = L.offset; k < L.offset + L.count; ++k) {
+                sorted[k].slice_off = static_cast<int32_t>(o);
+                o += rcpsp::slice_state_words(sorted[k].h.n, sorted[k].tabu_len, sorted[k].delta);
+            }
+            need += o;
+        }
+        if (need * 4 > c->slice_cap) {
+            dev_free(c, c->slice_dev, c->slice_cap, nullptr);
+            c->slice_dev = static_cast<int32_t *>(dev_alloc(c, need * 4, nullptr));
+            c->slice_cap = c->slice_dev ? need * 4 : 0;
+            if (!c->slice_dev) return set_err(c, RCPSP_E_CUDA, "slice scratch allocation failed");
+        }
+    }
     // kept prefix states: one region per CTA of every class that uses them
     {
         size_t need = 0;
@@ -854,8 +892,10 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
     std::vector<long long> sig;
     for (const ClassLaunch &L : launches)
         sig.insert(sig.end(), {L.offset, L.count, L.G, L.threads, L.blocks, L.move_cap, static_cast<long long>(L.smem),
-                               L.csize, L.prefix ? 1 : 0, L.snap_words, static_cast<long long>(L.snap_off)});
+                               L.csize, L.prefix ? 1 : 0, L.snap_words, static_cast<long long>(L.snap_off),
+                               L.nslices, static_cast<long long>(L.slice_off)});
     sig.push_back(reinterpret_cast<long long>(c->snap_dev));
+    sig.push_back(reinterpret_cast<long long>(c->slice_dev));
     // device copy of the plan
     cudaError_t e = cudaSuccess;
     const size_t ibytes = sizeof(LaunchItem) * count;
@@ -891,14 +931,20 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
     auto launch_all = [&](cudaStream_t s0) -> cudaError_t {
         cudaError_t r = cudaMemsetAsync(c->queue_dev, 0, sizeof(int) * kMaxLaunches, s0);
         if (r != cudaSuccess) return r;
+        for (const ClassLaunch &L : launches)
+            if (L.nslices > 1 &&
+                (r = cudaMemsetAsync(c->slice_dev + L.slice_off, 0, sizeof(int) * 2 * L.count, s0)) != cudaSuccess)
+                return r;
         if (launches.size() > 1 && (r = cudaEventRecord(c->fork, s0)) != cudaSuccess) return r;
         for (size_t q = 0; q < launches.size(); ++q) {
             const ClassLaunch &L = launches[q];
             cudaStream_t sq = q == 0 ? s0 : c->aux[q - 1];
             if (q > 0 && (r = cudaStreamWaitEvent(sq, c->fork, 0)) != cudaSuccess) return r;
+            const rcpsp::SliceSched sl{L.nslices, L.nslices > 1 ? c->slice_dev + L.slice_off : nullptr,
+                                       L.nslices > 1 ? c->slice_dev + L.slice_off : nullptr};
             r = rcpsp::launch_search(L.G, c->items_dev + L.offset, L.count, c->queue_dev + q, L.move_cap, L.blocks,
                                      L.threads, L.smem, sq, L.csize, L.prefix,
-                                     L.prefix ? c->snap_dev + L.snap_off : nullptr, L.snap_words);
+                                     L.prefix ? c->snap_dev + L.snap_off : nullptr, L.snap_words, sl);
             if (r != cudaSuccess) return r;
             if (q > 0 && (r = cudaEventRecord(c->join[q - 1], sq)) != cudaSuccess) return r;
         }
@@ -938,7 +984,7 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
     c->last_launches.clear();
     for (const ClassLaunch &L : launches)
         c->last_launches.push_back(rcpsp_launch_info{L.count, L.G, L.threads / 32, L.csize, L.blocks, L.prefix ? 1 : 0,
-                                                     L.shape_source, 0, static_cast<int64_t>(L.smem)});
+                                                     L.shape_source, L.nslices, static_cast<int64_t>(L.smem)});
     if (p->checkpoint)
         for (const LaunchItem &it : items) {
             // items[] holds the ids' searches in call order

@@ -52,7 +52,7 @@ struct LaunchItem {
     int32_t stop_at_cp;
     int32_t ckpt;               // kCkpt* bits: resume from / save to `state`
     int32_t prefix_k;           // > 0: positions between kept prefix states (prefix_*)
-    int32_t pad;
+    int32_t slice_off;          // sliced launch: first word of this search's slice state (SliceSched)
 };
 static_assert(sizeof(LaunchItem) == 128, "LaunchItem is 128 bytes");
 
@@ -221,6 +221,35 @@ RC_HD CkptLayout ckpt_layout(int n, int tabu_len, int delta) {
     L.tc = L.stl + align4(tabu_len);
     L.words = L.tc + align4((n * delta + 31) / 32);
     return L;
+}
+
+// Slicing a launch (SliceSched): with more searches than resident CTAs (or
+// clusters), the searches that start last would run alone at the end of the
+// call while the rest of the GPU idles.  A sliced launch cuts every search
+// into `nslices` runs of L = ceil(iterations / nslices) iterations: queue
+// position q names slice q / count of search q % count, so every search's
+// first slice is popped before any second one, and a CTA may pick up a
+// slice that another CTA's previous slice left in global memory.  Between
+// slices a search's state is kept in its slice state: the CkptLayout of its
+// (N, |TL|, delta) followed by kSlExtra words -- the iteration count before
+// the call, the start timestamp, the error word and the five work counters
+// of the call so far.  sync[2i] counts the slices of search i that are done
+// (nslices once it has finished; kSliceAbandoned set when a CTA gave up
+// waiting for it), sync[2i + 1] its iterations so far, which a waiting CTA
+// watches for progress.  nslices <= 1: no slicing.
+enum : int { kSlIt0 = 0, kSlT0Lo, kSlT0Hi, kSlErr, kSlTally, kSlExtra = 16 };
+static_assert(kSlTally + 2 * kTallies <= kSlExtra, "slice extras fit");
+constexpr int kSliceAbandoned = 1 << 29;
+constexpr int kMaxSlices = 64;
+
+struct SliceSched {
+    int nslices;
+    int *sync;             // [count][2]: slices done, iterations so far (zeroed before the launch)
+    int32_t *states;       // slice states, at LaunchItem::slice_off
+};
+
+RC_HD int slice_state_words(int n, int tabu_len, int delta) {
+    return align4(ckpt_layout(n, tabu_len, delta).words + kSlExtra);
 }
 
 // Words of one working-set slot: the list W, the tabu list (packed pairs),

@@ -82,12 +82,12 @@ cudaError_t search_occupancy(int group_size, int threads, size_t smem, int csize
 
 cudaError_t launch_search(int group_size, const LaunchItem *items, int count, int *queue, int move_cap,
                           int blocks, int threads, size_t smem, cudaStream_t st, int csize, bool prefix,
-                          int *gsnap, int gsnap_words) {
+                          int *gsnap, int gsnap_words, SliceSched sl) {
     if (threads > kSearchNarrowThreads)
         return launch_search_wide(group_size, items, count, queue, move_cap, blocks, threads, smem, st, csize,
-                                  prefix, gsnap, gsnap_words);
+                                  prefix, gsnap, gsnap_words, sl);
     return launch_search_nt<kSearchNarrowThreads>(group_size, items, count, queue, move_cap, blocks, threads, smem,
-                                                  st, csize, prefix, gsnap, gsnap_words);
+                                                  st, csize, prefix, gsnap, gsnap_words, sl);
 }
 
 cudaError_t launch_evaluate(int group_size, const LaunchItem &item, const int32_t *lists, int count,

@@ -26,14 +26,68 @@
 //   4. warp-shuffle min, then a shared-memory atomicMin, give the move;
 //   5. one thread applies it and updates the simple tabu list (Alg. 3).
 //
-// The kernel never spins: the work queue is a single atomicAdd.  Internal
-// inconsistencies set an error word that the host reads as a status.
+// The work queue is a single atomicAdd.  The kernel waits on another CTA in
+// two places only, each bounded: a sliced launch (SliceSched) may pop a
+// slice whose previous slice another CTA is still running, and with prefix
+// reuse a neighbour decode may wait for a kept state that warp 0 is still
+// writing.  Internal inconsistencies set an error word that the host reads
+// as a status.
 #pragma once
 
 #include "device_search.cuh"
 
 namespace rcpsp {
 namespace {
+
+__device__ __forceinline__ int load_acquire_gpu(const int *x) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(x) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int load_relaxed_gpu(const int *x) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(x) : "memory");
+    return v;
+}
+
+// Iteration at which slice `slice` of a search whose call started at
+// iteration it0 and runs `iters` iterations stops: slices are
+// ceil(iters / nsl) iterations long, the last one shorter.
+__device__ __forceinline__ int slice_end(int it0, int iters, int slice, int nsl) {
+    if (nsl <= 1) return it0 + iters;
+    const int per = (iters + nsl - 1) / nsl;
+    return it0 + ::min(iters, (slice + 1) * per);
+}
+
+constexpr unsigned long long kSliceWaitNs = 10000000000ull;   // 10 s without progress
+
+// Before slice s of a search runs: wait until its slice s-1 is done (sync[0]
+// reaches s).  The slice before was popped earlier by a CTA that is running
+// it, so the wait ends unless that CTA stops making progress: it is given
+// up, and the search abandoned, only after kSliceWaitNs without the search's
+// iteration count (sync[1]) moving.  Returns 1: run slice s, 0: the search
+// has finished (nothing to do), -1: gave up.
+__device__ int slice_wait(int *sync, int s) {
+    int d = load_acquire_gpu(sync);
+    if (d < s) {
+        int last = load_relaxed_gpu(sync + 1);
+        unsigned long long t0 = global_timer_ns();
+        while ((d = load_acquire_gpu(sync)) < s) {
+            const int pr = load_relaxed_gpu(sync + 1);
+            const unsigned long long t = global_timer_ns();
+            if (pr != last) {
+                last = pr;
+                t0 = t;
+            } else if (t - t0 > kSliceWaitNs) {
+                atomicOr(sync, kSliceAbandoned);
+                return -1;
+            }
+            __nanosleep(200);
+        }
+    }
+    return d == s ? 1 : 0;
+}
 
 // ---------------------------------------------------------------------------
 // Persistent search kernel.  With csize > 1 it runs as clusters of csize
@@ -48,10 +102,11 @@ namespace {
 template <int G, bool PFX, int NT>
 __global__ void __launch_bounds__(NT, 2) search_kernel(const LaunchItem *__restrict__ items, int count,
                                                       int *__restrict__ queue, int move_cap, int csize,
-                                                      int *__restrict__ gsnap, int gsnap_words) {
+                                                      int *__restrict__ gsnap, int gsnap_words, SliceSched sl) {
     extern __shared__ __align__(16) int sm[];
     __shared__ int s_mq[3];   // compaction and drain cursors, kept snapshots
-    __shared__ int s_item, s_C, s_Cbest, s_widx, s_it, s_improved, s_err, s_it0, s_it_end;
+    __shared__ int s_item, s_C, s_Cbest, s_widx, s_it, s_improved, s_err, s_it0, s_it_end, s_slice_end;
+    __shared__ int s_run;     // 1: run the popped slice, 0: skip it
     __shared__ unsigned long long s_bestp[2], s_t0;      // best key of the iteration, by parity
     __shared__ long long s_eval, s_work;
     __shared__ long long s_tally[kTallies];   // work counters of the decodes (TallyRef)
@@ -65,19 +120,45 @@ __global__ void __launch_bounds__(NT, 2) search_kernel(const LaunchItem *__restr
     const int gw = wl / G;                     // group inside the warp
     const Group<G> g;
 
+    // (the slice values below are recomputed where they are needed, from the
+    // launch parameters and s_item, so that none stays live across the
+    // search loop)
     for (;;) {
-        if (tid == 0 && crank == 0) s_item = atomicAdd(queue, 1);
-        int item;
+        if (tid == 0 && crank == 0) {
+            const int q = atomicAdd(queue, 1);
+            int run = 1;
+            if (sl.nslices > 1 && q < count * sl.nslices) {
+                const int si = q / count, k = q - si * count;
+                run = slice_wait(sl.sync + 2 * k, si);
+                if (run < 0) {
+                    // abandoned: the search reports a device error
+                    const LaunchItem &ik = items[k];
+                    ik.out[2 * ik.h.n + kOutStatus] = RCPSP_E_DEVICE;
+                    run = 0;
+                }
+            }
+            s_item = q;
+            s_run = run;
+        }
+        int item, run;
         if (csize > 1) {
             cg::this_cluster().sync();
             item = *cg::this_cluster().map_shared_rank(&s_item, 0);
+            run = *cg::this_cluster().map_shared_rank(&s_run, 0);
             cg::this_cluster().sync();                      // read before rank 0 pops again
         } else {
             __syncthreads();
             item = s_item;
+            run = s_run;
         }
-        if (item >= count) break;
-        const LaunchItem &it = items[item];
+        if (item >= count * (sl.nslices > 1 ? sl.nslices : 1)) break;
+        if (!run) {
+            if (csize == 1) __syncthreads();                // every thread has read s_item
+            continue;
+        }
+        const int slice = item / count;                     // 0 unless the launch is sliced
+        const int ki = item - slice * count;
+        const LaunchItem &it = items[ki];
         const InstHeader &h = it.h;
         const int n = h.n, mode = it.mode, delta = it.delta, tl = it.tabu_len;
         const int pw = profile_words(mode, h.wps, h.ub, h.sum_cap);
@@ -98,36 +179,56 @@ __global__ void __launch_bounds__(NT, 2) search_kernel(const LaunchItem *__restr
         int *area = sm + S.groups + warp * NG * S.group_words + wl / G;
         const int tcw = (n * delta + 31) / 32;
         int err = 0;
-        if (it.state && (it.ckpt & kCkptResume)) {
-            // continue a saved search: lists, tabu state, iteration and
-            // makespans as they were; the counters so far ride on rank 0
+        // slice state of this search (sliced launches)
+        const bool from_slice = slice > 0;
+        if (from_slice || (it.state && (it.ckpt & kCkptResume))) {
+            // continue a saved search -- the caller's kept state, or the one
+            // the previous slice of this launch left -- with lists, tabu
+            // state, iteration and makespans as they were; the counters so
+            // far ride on rank 0.  Read past L1: another SM wrote them.
             const CkptLayout CL = ckpt_layout(n, tl, delta);
-            const int32_t *sv = it.state;
+            const int32_t *sv = from_slice ? sl.states + it.slice_off : it.state;
             for (int p = tid; p < n; p += nthr) {
-                const int a = sv[CL.W + p];
+                const int a = __ldcg(sv + CL.W + p);
                 W[p] = a;
                 pos[a] = p;
-                Wbest[p] = sv[CL.Wbest + p];
+                Wbest[p] = __ldcg(sv + CL.Wbest + p);
             }
-            for (int x = tid; x < tl; x += nthr) stl[x] = sv[CL.stl + x];
-            for (int x = tid; x < tcw; x += nthr) tc[x] = static_cast<unsigned>(sv[CL.tc + x]);
-            if (tid < kTallies) s_tally[tid] = 0;
+            for (int x = tid; x < tl; x += nthr) stl[x] = __ldcg(sv + CL.stl + x);
+            for (int x = tid; x < tcw; x += nthr) tc[x] = static_cast<unsigned>(__ldcg(sv + CL.tc + x));
+            if (tid < kTallies) {
+                // the work counters are the call's: kept across slices only
+                const int32_t *xt = sv + CL.words + kSlTally + 2 * tid;
+                s_tally[tid] = from_slice && crank == 0
+                                   ? (static_cast<long long>(static_cast<uint32_t>(__ldcg(xt))) |
+                                      (static_cast<long long>(__ldcg(xt + 1)) << 32))
+                                   : 0;
+            }
             if (tid < 32) s_hist[tid] = 0;
             if (tid == 0) {
-                s_t0 = global_timer_ns();
-                s_widx = sv[kCkWidx];
-                s_it = sv[kCkIters];
-                s_it0 = s_it;                     // iterations before this call
-                s_it_end = s_it + it.iterations;
-                s_C = sv[kCkC];
-                s_Cbest = sv[kCkCbest];
-                const long long ev = static_cast<long long>(static_cast<uint32_t>(sv[kCkEvalLo])) |
-                                     (static_cast<long long>(sv[kCkEvalHi]) << 32);
-                const long long wk = static_cast<long long>(static_cast<uint32_t>(sv[kCkWorkLo])) |
-                                     (static_cast<long long>(sv[kCkWorkHi]) << 32);
+                s_widx = __ldcg(sv + kCkWidx);
+                s_it = __ldcg(sv + kCkIters);
+                if (from_slice) {
+                    const int32_t *xs = sv + CL.words;
+                    s_it0 = __ldcg(xs + kSlIt0);
+                    s_t0 = static_cast<unsigned long long>(static_cast<uint32_t>(__ldcg(xs + kSlT0Lo))) |
+                           (static_cast<unsigned long long>(static_cast<uint32_t>(__ldcg(xs + kSlT0Hi))) << 32);
+                    s_err = crank == 0 ? __ldcg(xs + kSlErr) : 0;
+                } else {
+                    s_it0 = s_it;                 // iterations before this call
+                    s_t0 = global_timer_ns();
+                    s_err = 0;
+                }
+                s_it_end = s_it0 + it.iterations;
+                s_slice_end = slice_end(s_it0, it.iterations, slice, sl.nslices);
+                s_C = __ldcg(sv + kCkC);
+                s_Cbest = __ldcg(sv + kCkCbest);
+                const long long ev = static_cast<long long>(static_cast<uint32_t>(__ldcg(sv + kCkEvalLo))) |
+                                     (static_cast<long long>(__ldcg(sv + kCkEvalHi)) << 32);
+                const long long wk = static_cast<long long>(static_cast<uint32_t>(__ldcg(sv + kCkWorkLo))) |
+                                     (static_cast<long long>(__ldcg(sv + kCkWorkHi)) << 32);
                 s_eval = crank == 0 ? ev : 0;
                 s_work = crank == 0 ? wk : 0;
-                s_err = 0;
             }
             __syncthreads();
         } else {
@@ -148,6 +249,7 @@ __global__ void __launch_bounds__(NT, 2) search_kernel(const LaunchItem *__restr
                 s_it = 0;
                 s_it0 = 0;
                 s_it_end = it.iterations;
+                s_slice_end = slice_end(0, it.iterations, slice, sl.nslices);
                 s_eval = 0;
                 s_work = 0;
                 s_err = 0;
@@ -168,7 +270,7 @@ __global__ void __launch_bounds__(NT, 2) search_kernel(const LaunchItem *__restr
         const unsigned dmagic = slot_magic(delta);
         long long my_work = 0;
         for (;;) {
-            if (s_it >= s_it_end || (it.stop_at_cp && s_Cbest == h.cp)) break;
+            if (s_it >= s_slice_end || (it.stop_at_cp && s_Cbest == h.cp)) break;
             const int par = s_it & 1;
             if (tid == 0) s_bestp[par] = ~0ull;
             const unsigned long long my_key =
@@ -216,6 +318,9 @@ __global__ void __launch_bounds__(NT, 2) search_kernel(const LaunchItem *__restr
                     it.trace[3 * (s_it - s_it0) + 2] = s_C;
                 }
                 s_it = s_it + 1;
+                // progress, watched by a CTA that waits for this slice
+                if (sl.nslices > 1 && crank == 0)
+                    *reinterpret_cast<volatile int *>(sl.sync + 2 * (s_item % count) + 1) = s_it;
             }
             __syncthreads();
             if (s_improved)
@@ -239,70 +344,96 @@ __global__ void __launch_bounds__(NT, 2) search_kernel(const LaunchItem *__restr
                 }
             __syncthreads();
         }
-        // outputs: W*, its schedule S*, statistics (rank 0)
+        // finished: the last iteration of the call is done or C* reached the
+        // critical path; otherwise only this slice of a sliced launch is
+        const bool done = sl.nslices <= 1 || s_it >= s_it_end || (it.stop_at_cp && s_Cbest == h.cp);
         int32_t *out = it.out;
         if (crank == 0) {
-        if (warp == 0) {
-            long long w1 = 0;
-            int e1 = 0;
-            const int cb = decode<G>(I, mode, Wbest, 0, 0, gw == 0, area, NG, g, w1, e1, out + n);
-            if (gw == 0) {
-                if (g.lane == 0) {
-                    out[2 * n + kOutCmax] = cb;
-                    if (e1 || cb != s_Cbest) atomicOr(&s_err, 2);
+            if (done) {
+                // outputs: W*, its schedule S*, statistics
+                if (warp == 0) {
+                    long long w1 = 0;
+                    int e1 = 0;
+                    const int cb = decode<G>(I, mode, Wbest, 0, 0, gw == 0, area, NG, g, w1, e1, out + n);
+                    if (gw == 0 && g.lane == 0) {
+                        out[2 * n + kOutCmax] = cb;
+                        if (e1 || cb != s_Cbest) atomicOr(&s_err, 2);
+                    }
+                }
+                for (int p = tid; p < n; p += nthr) out[p] = Wbest[p];
+                __syncthreads();
+                if (tid == 0) {
+                    int32_t *st = out + 2 * n;
+                    st[kOutEvalLo] = static_cast<int32_t>(s_eval & 0xffffffffll);
+                    st[kOutEvalHi] = static_cast<int32_t>(s_eval >> 32);
+                    st[kOutWorkLo] = static_cast<int32_t>(s_work & 0xffffffffll);
+                    st[kOutWorkHi] = static_cast<int32_t>(s_work >> 32);
+                    st[kOutIters] = s_it;
+                    st[kOutIters0] = s_it0;
+                    for (int x = 0; x < kTallies; ++x) {
+                        // loop steps performed = the work counter plus its correction
+                        const long long t = x == kTallySteps ? s_work + s_tally[x] : s_tally[x];
+                        st[kOutPlacedLo + 2 * x] = static_cast<int32_t>(t & 0xffffffffll);
+                        st[kOutPlacedLo + 2 * x + 1] = static_cast<int32_t>(t >> 32);
+                    }
+                    st[kOutMode] = mode;
+                    st[kOutStatus] = s_err ? RCPSP_E_DEVICE : 0;
+                    const unsigned long long t1 = global_timer_ns();
+                    st[kOutT0Lo] = static_cast<int32_t>(s_t0 & 0xffffffffull);
+                    st[kOutT0Hi] = static_cast<int32_t>(s_t0 >> 32);
+                    st[kOutT1Lo] = static_cast<int32_t>(t1 & 0xffffffffull);
+                    st[kOutT1Hi] = static_cast<int32_t>(t1 >> 32);
                 }
             }
-        }
-        for (int p = tid; p < n; p += nthr) out[p] = Wbest[p];
-        __syncthreads();
-        if (tid == 0) {
-            int32_t *st = out + 2 * n;
-            st[kOutEvalLo] = static_cast<int32_t>(s_eval & 0xffffffffll);
-            st[kOutEvalHi] = static_cast<int32_t>(s_eval >> 32);
-            st[kOutWorkLo] = static_cast<int32_t>(s_work & 0xffffffffll);
-            st[kOutWorkHi] = static_cast<int32_t>(s_work >> 32);
-            st[kOutIters] = s_it;
-            st[kOutIters0] = s_it0;
-            for (int x = 0; x < kTallies; ++x) {
-                // loop steps performed = the work counter plus its correction
-                const long long t = x == kTallySteps ? s_work + s_tally[x] : s_tally[x];
-                st[kOutPlacedLo + 2 * x] = static_cast<int32_t>(t & 0xffffffffll);
-                st[kOutPlacedLo + 2 * x + 1] = static_cast<int32_t>(t >> 32);
+            // keep the search where it stopped: for a later call to resume
+            // (the caller's state), or for the next slice of this launch
+            int32_t *sv = done ? ((it.state && (it.ckpt & kCkptSave)) ? it.state : nullptr)
+                               : sl.states + it.slice_off;
+            if (sv) {
+                const CkptLayout CL = ckpt_layout(n, tl, delta);
+                for (int p = tid; p < n; p += nthr) {
+                    __stcg(sv + CL.W + p, W[p]);
+                    __stcg(sv + CL.Wbest + p, Wbest[p]);
+                }
+                for (int x = tid; x < tl; x += nthr) __stcg(sv + CL.stl + x, stl[x]);
+                for (int x = tid; x < tcw; x += nthr) __stcg(sv + CL.tc + x, static_cast<int32_t>(tc[x]));
+                if (tid == 0) {
+                    __stcg(sv + kCkMagic, kCkptMagic);
+                    __stcg(sv + kCkN, n);
+                    __stcg(sv + kCkDelta, delta);
+                    __stcg(sv + kCkTabu, tl);
+                    __stcg(sv + kCkMode, mode);
+                    __stcg(sv + kCkIters, s_it);
+                    __stcg(sv + kCkC, s_C);
+                    __stcg(sv + kCkCbest, s_Cbest);
+                    __stcg(sv + kCkWidx, s_widx);
+                    __stcg(sv + kCkEvalLo, static_cast<int32_t>(s_eval & 0xffffffffll));
+                    __stcg(sv + kCkEvalHi, static_cast<int32_t>(s_eval >> 32));
+                    __stcg(sv + kCkWorkLo, static_cast<int32_t>(s_work & 0xffffffffll));
+                    __stcg(sv + kCkWorkHi, static_cast<int32_t>(s_work >> 32));
+                    if (!done) {
+                        // what the call has counted so far
+                        int32_t *xs = sv + CL.words;
+                        __stcg(xs + kSlIt0, s_it0);
+                        __stcg(xs + kSlT0Lo, static_cast<int32_t>(s_t0 & 0xffffffffull));
+                        __stcg(xs + kSlT0Hi, static_cast<int32_t>(s_t0 >> 32));
+                        __stcg(xs + kSlErr, s_err);
+                        for (int x = 0; x < kTallies; ++x) {
+                            __stcg(xs + kSlTally + 2 * x, static_cast<int32_t>(s_tally[x] & 0xffffffffll));
+                            __stcg(xs + kSlTally + 2 * x + 1, static_cast<int32_t>(s_tally[x] >> 32));
+                        }
+                    }
+                }
             }
-            st[kOutMode] = mode;
-            st[kOutStatus] = s_err ? RCPSP_E_DEVICE : 0;
-            const unsigned long long t1 = global_timer_ns();
-            st[kOutT0Lo] = static_cast<int32_t>(s_t0 & 0xffffffffull);
-            st[kOutT0Hi] = static_cast<int32_t>(s_t0 >> 32);
-            st[kOutT1Lo] = static_cast<int32_t>(t1 & 0xffffffffull);
-            st[kOutT1Hi] = static_cast<int32_t>(t1 >> 32);
-        }
-        if (it.state && (it.ckpt & kCkptSave)) {
-            // keep the search where it stopped, for a later call to resume
-            const CkptLayout CL = ckpt_layout(n, tl, delta);
-            int32_t *sv = it.state;
-            for (int p = tid; p < n; p += nthr) {
-                sv[CL.W + p] = W[p];
-                sv[CL.Wbest + p] = Wbest[p];
+            if (sl.nslices > 1) {
+                // publish: this slice of the search is done (all of it when finished)
+                __syncthreads();
+                if (tid == 0) {
+                    const int q = s_item, qs = q / count;
+                    __threadfence();
+                    atomicMax(sl.sync + 2 * (q - qs * count), done ? sl.nslices : qs + 1);
+                }
             }
-            for (int x = tid; x < tl; x += nthr) sv[CL.stl + x] = stl[x];
-            for (int x = tid; x < tcw; x += nthr) sv[CL.tc + x] = static_cast<int32_t>(tc[x]);
-            if (tid == 0) {
-                sv[kCkMagic] = kCkptMagic;
-                sv[kCkN] = n;
-                sv[kCkDelta] = delta;
-                sv[kCkTabu] = tl;
-                sv[kCkMode] = mode;
-                sv[kCkIters] = s_it;
-                sv[kCkC] = s_C;
-                sv[kCkCbest] = s_Cbest;
-                sv[kCkWidx] = s_widx;
-                sv[kCkEvalLo] = static_cast<int32_t>(s_eval & 0xffffffffll);
-                sv[kCkEvalHi] = static_cast<int32_t>(s_eval >> 32);
-                sv[kCkWorkLo] = static_cast<int32_t>(s_work & 0xffffffffll);
-                sv[kCkWorkHi] = static_cast<int32_t>(s_work >> 32);
-            }
-        }
         }
         __syncthreads();
     }
@@ -338,9 +469,11 @@ cudaError_t occupancy_g(int threads, size_t smem, int csize, int *units) {
 
 template <int G, bool PFX, int NT>
 cudaError_t launch_search_g(const LaunchItem *items, int count, int *queue, int move_cap, int blocks,
-                            int threads, size_t smem, cudaStream_t st, int csize, int *gsnap, int gsnap_words) {
+                            int threads, size_t smem, cudaStream_t st, int csize, int *gsnap, int gsnap_words,
+                            SliceSched sl) {
     if (csize <= 1) {
-        search_kernel<G, PFX, NT><<<blocks, threads, smem, st>>>(items, count, queue, move_cap, 1, gsnap, gsnap_words);
+        search_kernel<G, PFX, NT><<<blocks, threads, smem, st>>>(items, count, queue, move_cap, 1, gsnap, gsnap_words,
+                                                                 sl);
         return cudaGetLastError();
     }
     cudaLaunchConfig_t cfg = {};
@@ -356,7 +489,7 @@ cudaError_t launch_search_g(const LaunchItem *items, int count, int *queue, int 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, search_kernel<G, PFX, NT>, items, count, queue, move_cap, csize, gsnap,
-                              gsnap_words);
+                              gsnap_words, sl);
 }
 
 #define RCPSP_DISPATCH_G(G_, CALL)                 \
@@ -385,13 +518,13 @@ cudaError_t search_occupancy_nt(int group_size, int threads, size_t smem, int cs
 template <int NT>
 cudaError_t launch_search_nt(int group_size, const LaunchItem *items, int count, int *queue, int move_cap,
                              int blocks, int threads, size_t smem, cudaStream_t st, int csize, bool prefix,
-                             int *gsnap, int gsnap_words) {
+                             int *gsnap, int gsnap_words, SliceSched sl) {
     if (prefix)
         RCPSP_DISPATCH_G(group_size, return (launch_search_g<GG, true, NT>(items, count, queue, move_cap, blocks,
                                                                            threads, smem, st, csize, gsnap,
-                                                                           gsnap_words)))
+                                                                           gsnap_words, sl)))
     RCPSP_DISPATCH_G(group_size, return (launch_search_g<GG, false, NT>(items, count, queue, move_cap, blocks,
-                                                                        threads, smem, st, csize, nullptr, 0)))
+                                                                        threads, smem, st, csize, nullptr, 0, sl)))
 }
 
 }  // namespace
@@ -401,6 +534,6 @@ cudaError_t prepare_search_wide(int group_size, size_t smem);
 cudaError_t search_occupancy_wide(int group_size, int threads, size_t smem, int csize, int *units, bool prefix);
 cudaError_t launch_search_wide(int group_size, const LaunchItem *items, int count, int *queue, int move_cap,
                                int blocks, int threads, size_t smem, cudaStream_t st, int csize, bool prefix,
-                               int *gsnap, int gsnap_words);
+                               int *gsnap, int gsnap_words, SliceSched sl);
 
 }  // namespace rcpsp

@@ -17,9 +17,9 @@ cudaError_t search_occupancy_wide(int group_size, int threads, size_t smem, int 
 
 cudaError_t launch_search_wide(int group_size, const LaunchItem *items, int count, int *queue, int move_cap,
                                int blocks, int threads, size_t smem, cudaStream_t st, int csize, bool prefix,
-                               int *gsnap, int gsnap_words) {
+                               int *gsnap, int gsnap_words, SliceSched sl) {
     return launch_search_nt<kWideThreads>(group_size, items, count, queue, move_cap, blocks, threads, smem, st,
-                                          csize, prefix, gsnap, gsnap_words);
+                                          csize, prefix, gsnap, gsnap_words, sl);
 }
 
 }  // namespace rcpsp

@@ -46,7 +46,8 @@ class Params(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("max_swap_dist", C.c_int32), ("tabu_len", C.c_int32),
                 ("eval_mode", C.c_int32), ("stop_at_cp", C.c_int32), ("group_size", C.c_int32),
                 ("warps_per_cta", C.c_int32), ("record_trace", C.c_int32), ("use_graph", C.c_int32),
-                ("cluster_size", C.c_int32), ("checkpoint", C.c_int32), ("resume", C.c_int32)]
+                ("cluster_size", C.c_int32), ("checkpoint", C.c_int32), ("resume", C.c_int32),
+                ("slices", C.c_int32)]
 
 
 class CoopParams(C.Structure):
@@ -74,7 +75,7 @@ assert _STATS_DTYPE.itemsize == C.sizeof(Stats)
 class LaunchInfo(C.Structure):
     _fields_ = [("searches", C.c_int32), ("group_size", C.c_int32), ("warps", C.c_int32),
                 ("cluster_size", C.c_int32), ("ctas", C.c_int32), ("prefix_reuse", C.c_int32),
-                ("shape_source", C.c_int32), ("reserved", C.c_int32), ("smem_bytes", C.c_int64)]
+                ("shape_source", C.c_int32), ("slices", C.c_int32), ("smem_bytes", C.c_int64)]
 
 
 class Peaks(C.Structure):
@@ -313,12 +314,13 @@ class Solver:
     def search(self, ids, iterations: int = 100, delta: int = 0, tabu_len: int = 0, mode: int = EVAL_AUTO,
                stop_at_cp: bool = True, group_size: int = 0, warps_per_cta: int = 0, trace: bool = False,
                use_graph: bool = False, stream=None, cluster_size: int = 0, checkpoint: bool = False,
-               resume: bool = False):
+               resume: bool = False, slices: int = 0):
         """Asynchronous search on ``stream`` (a torch.cuda.Stream, a raw handle or None).
-        checkpoint keeps each search's state on the device; resume continues it."""
+        checkpoint keeps each search's state on the device; resume continues it;
+        slices: 0 automatic, 1 none, k: every search in k slices (same results)."""
         ids = _i32(ids)
         p = Params(iterations, delta, tabu_len, mode, int(stop_at_cp), group_size, warps_per_cta,
-                   int(trace), int(use_graph), cluster_size, int(checkpoint), int(resume))
+                   int(trace), int(use_graph), cluster_size, int(checkpoint), int(resume), slices)
         handle = getattr(stream, "cuda_stream", stream) or None
         self._check(self.lib.rcpsp_tabu_search(self.ctx, _ptr(ids), len(ids), C.byref(p), handle))
 

@@ -71,7 +71,7 @@ def _child(argv):
 
         def last_launches(self):
             return [dict(searches=4, group_size=4, warps=12, cluster_size=1, ctas=4, prefix_reuse=0,
-                         shape_source=0, reserved=0, smem_bytes=1 << 16)]
+                         shape_source=0, slices=1, smem_bytes=1 << 16)]
 
         def kernel_launches(self):
             return self.launches
