@@ -485,11 +485,15 @@ __device__ int decode_capacity(const SInst &I, const int *W, int u, int v, bool 
         const int inext = activity_at<G>(W, p + 1 < n ? p + 1 : p, u, v);
         const int es = esa[i * NG];
         // Eq. 7: es_res = max over used resources of c_k[R_k - r_{i,k}]
+        // (the used resources of i come first in its row of reqk, each as
+        // r << 3 | k; lane q takes the q-th, q+G-th, ... of them)
         int er = 0;
         if (act)
-            for (int k = g.lane; k < m; k += G) {
-                const int r = I.reqk[i * m + k];
-                if (r > 0) er = ::max(er, cst[(I.cbase[k] + I.cap[k] - r) * NG]);
+            for (int q = g.lane; q < m; q += G) {
+                const int e = I.reqk[i * m + q];
+                if (e == 0) break;
+                const int k = e & 7, r = e >> 3;
+                er = ::max(er, cst[(I.cbase[k] + I.cap[k] - r) * NG]);
             }
         er = g.max(er);
         const int s = ::max(es, er);
@@ -507,9 +511,10 @@ __device__ int decode_capacity(const SInst &I, const int *W, int u, int v, bool 
         // up by r from the top down (a batch of reads before its writes, so
         // every read sees the old value) and writes T into [b, b+r).
         if (act && d > 0)
-            for (int k = g.lane; k < m; k += G) {
-                const int r = I.reqk[i * m + k];
-                if (r == 0) continue;
+            for (int q = g.lane; q < m; q += G) {
+                const int e = I.reqk[i * m + q];
+                if (e == 0) break;
+                const int k = e & 7, r = e >> 3;
                 const int R = I.cap[k];
                 const int T = s + d;
                 short *ck = cst + I.cbase[k] * NG;

@@ -220,7 +220,11 @@ int prepare_instance(const rcpsp_instance &in, PackedInstance &out, std::string 
         r[L.cbase + k] = b;
         b += in.cap[k];
     }
-    for (int i = 0; i < n * m; ++i) r[L.reqk + i] = in.req[i];
+    // per activity, its used resources first, each as r_{i,k} << 3 | k,
+    // then zeros (the capacity-indexed decoder's lanes take them in turn)
+    for (int i = 0; i < n; ++i)
+        for (int k = 0, q = 0; k < m; ++k)
+            if (in.req[i * m + k] > 0) r[L.reqk + i * m + q++] = (in.req[i * m + k] << 3) | k;
     for (int i = 0; i <= n; ++i) r[L.poff + i] = poff[i];
     for (int e = 0; e < E; ++e) r[L.plist + e] = plist[e];
     for (int i = 0; i <= n; ++i) r[L.soff + i] = in.succ_off[i];

@@ -107,6 +107,8 @@ enum : int { kTallyPlaced = 0, kTallySteps, kTallyUpd, kTallySucc, kTallyKept, k
 
 RC_HD int align4(int x) { return (x + 3) & ~3; }
 
+static_assert(RCPSP_MAX_M <= 8, "a resource index of the packed demands takes 3 bits");
+
 // Offsets (in 32-bit words) of the shared-memory image of an instance.
 struct InstLayout {
     int dur, reqw, capw, cap, cbase, reqk, poff, plist, soff, slist, words;
@@ -120,7 +122,7 @@ RC_HD InstLayout inst_layout(int n, int m, int wps, int n_arcs) {
     L.capw = o;  o += 4;                  // packed R_k per word (initial profile value)
     L.cap = o;   o += 8;                  // R_k
     L.cbase = o; o += 8;                  // start of c_k in the capacity-indexed state
-    L.reqk = o;  o += align4(n * m);      // r_{i,k}
+    L.reqk = o;  o += align4(n * m);      // used resources of i first: r_{i,k} << 3 | k, then 0
     L.poff = o;  o += align4(n + 1);      // predecessor CSR
     L.plist = o; o += align4(n_arcs);
     L.soff = o;  o += align4(n + 1);      // successor CSR
