@@ -2,11 +2,14 @@
 
 Each rank takes its own shard of instances (no instance solved twice, the
 same shard every run) and the timing reduction returns the slowest rank's
-time and the total count, as the benchmark reports for N GPUs.
+time and the total count, as the benchmark reports for N GPUs.  With one
+batch split by cost, ranks that search their shares (with the oracle, on
+the CPU) and gather on rank 0 give the results of one process.
 """
 import os
 import socket
 
+import numpy as np
 import pytest
 import torch.distributed as dist
 import torch.multiprocessing as mp
@@ -114,3 +117,44 @@ def test_potential_moves_is_the_neighbourhood_size(oracle):
         r = oracle.tabu_search(inst, 1, delta, 5, 1, 0)
         brute = sum(1 for u in range(1, n - 2) for v in range(u + 1, n - 1) if v - u <= delta)
         assert r["evaluated"] == brute == replicas.potential_moves(n, delta)
+
+
+# ------------------- the strong-scaling path with real per-rank search results
+def _lpt_search_rank(rank, world, port, out):
+    """Each rank searches its longest-processing-time share of one batch --
+    with the oracle, the CPU stand-in for a rank's GPU -- and rank 0 gathers
+    the results in batch order, as bench.py --shard lpt does."""
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from oracle import oracle as O
+    from paper_1711_04556_gb300 import instances, replicas
+    batch = instances.config_batch("mixed_batch", 12)
+    parts = replicas.lpt_partition([replicas.estimated_cost(x, 40) for x in batch], world)
+    mine = parts[rank]
+    params = [(40,) + instances.search_params(batch[i].n - 2) + (O.AUTO, 1) for i in mine]
+    found = O.tabu_search_batch([batch[i] for i in mine], params, 2)
+    results = [{"best_cmax": r["best_cmax"], "evaluated": r["evaluated"], "work": r["work"],
+                "best_W": np.asarray(r["best_W"]).tolist(), "rank": rank} for r in found]
+    got = replicas.gather_results(dist, results, mine, len(batch), world, rank)
+    out[rank] = (parts, got)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_lpt_shards_searched_and_gathered_equal_one_process(oracle):
+    world, port = 2, _free_port()
+    mgr = mp.Manager()
+    out = mgr.dict()
+    mp.spawn(_lpt_search_rank, args=(world, port, out), nprocs=world, join=True)
+    from paper_1711_04556_gb300 import instances
+    batch = instances.config_batch("mixed_batch", 12)
+    parts, got = out[0]
+    assert out[1][1] is None and len(got) == len(batch)
+    assert {g["rank"] for g in got} == {0, 1}                     # both ranks did work
+    params = [(40,) + instances.search_params(x.n - 2) + (oracle.AUTO, 1) for x in batch]
+    for g, r in zip(got, oracle.tabu_search_batch(batch, params, 2)):
+        assert g["best_cmax"] == r["best_cmax"] and g["evaluated"] == r["evaluated"] and g["work"] == r["work"]
+        assert g["best_W"] == np.asarray(r["best_W"]).tolist()
