@@ -74,6 +74,7 @@ METRIC = "neighbour schedules evaluated/sec on 1 GB300 (bit-exact) + p50/p99 sol
 UNIT = "schedules/s"
 KERNEL_SOURCES = ["paper_1711_04556_gb300/csrc/search_kernel.cuh", "paper_1711_04556_gb300/csrc/search_kernel.cu",
                   "paper_1711_04556_gb300/csrc/search_kernel_wide.cu",
+                  "paper_1711_04556_gb300/csrc/search_kernel_solo.cu",
                   "paper_1711_04556_gb300/csrc/device_search.cuh",
                   "paper_1711_04556_gb300/csrc/rcpsp_internal.h"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "search_kernel_mixed_batch.traffic.json")

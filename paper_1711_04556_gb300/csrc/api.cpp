@@ -234,6 +234,7 @@ int footprint_class(const LaunchItem &it) {
 struct ClassLaunch {
     int offset = 0, count = 0, G = 0, threads = 0, blocks = 0, move_cap = 0, csize = 1;
     int nslices = 1;             // slices per search (SliceSched); 1: not sliced
+    bool solo = false;           // one CTA per SM: the build that may take all its registers
     size_t slice_off = 0;        // first word of its sync counters and slice states in slice_dev
     bool prefix = false;         // prefix reuse (kernel variant, kept states in global scratch)
     int snap_words = 0;          // kept-state words per CTA
@@ -781,6 +782,13 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
         e = rcpsp::search_occupancy(G, L.threads, smem, L.csize, &units, L.prefix);
         if (e != cudaSuccess) return cuda_err(c, e, "occupancy");
         if (units < 1) return set_err(c, RCPSP_E_TOO_LARGE, "launch shape does not fit on the GPU");
+        // shared memory that holds one CTA per SM anyway: the build whose
+        // threads may use the registers of the whole SM
+        int solo_units = 0;
+        if (L.csize == 1 && units == 1 &&
+            rcpsp::search_occupancy(G, L.threads, smem, 1, &solo_units, L.prefix, true) == cudaSuccess &&
+            solo_units == 1)
+            L.solo = true;
         L.blocks = L.csize == 1 ? std::max(1, std::min(L.count, units * c->prop.multiProcessorCount))
                                 : L.csize * std::max(1, std::min(L.count, units));
         // Outliers: in a class whose searches take one CTA each and decode
@@ -825,6 +833,7 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
                 std::copy(keep.begin(), keep.end(), sorted.begin() + L.offset);
                 std::copy(moved.begin(), moved.end(), sorted.begin() + L.offset + keep.size());
                 ClassLaunch O = L;
+                O.solo = false;
                 O.offset = L.offset + static_cast<int>(keep.size());
                 O.count = static_cast<int>(moved.size());
                 O.csize = oc;
@@ -893,7 +902,7 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
     for (const ClassLaunch &L : launches)
         sig.insert(sig.end(), {L.offset, L.count, L.G, L.threads, L.blocks, L.move_cap, static_cast<long long>(L.smem),
                                L.csize, L.prefix ? 1 : 0, L.snap_words, static_cast<long long>(L.snap_off),
-                               L.nslices, static_cast<long long>(L.slice_off)});
+                               L.nslices, static_cast<long long>(L.slice_off), L.solo ? 1 : 0});
     sig.push_back(reinterpret_cast<long long>(c->snap_dev));
     sig.push_back(reinterpret_cast<long long>(c->slice_dev));
     // device copy of the plan
@@ -944,7 +953,7 @@ int rcpsp_tabu_search(rcpsp_ctx *c, const int32_t *ids, int32_t count, const rcp
                                        L.nslices > 1 ? c->slice_dev + L.slice_off : nullptr};
             r = rcpsp::launch_search(L.G, c->items_dev + L.offset, L.count, c->queue_dev + q, L.move_cap, L.blocks,
                                      L.threads, L.smem, sq, L.csize, L.prefix,
-                                     L.prefix ? c->snap_dev + L.snap_off : nullptr, L.snap_words, sl);
+                                     L.prefix ? c->snap_dev + L.snap_off : nullptr, L.snap_words, sl, L.solo);
             if (r != cudaSuccess) return r;
             if (q > 0 && (r = cudaEventRecord(c->join[q - 1], sq)) != cudaSuccess) return r;
         }

@@ -70,24 +70,30 @@ cudaError_t launch_eval_g(const LaunchItem &item, const int32_t *lists, int coun
 }  // namespace
 
 cudaError_t prepare_search(int group_size, size_t smem) {
-    cudaError_t e = prepare_search_nt<kSearchNarrowThreads>(group_size, smem);
-    return e == cudaSuccess ? prepare_search_wide(group_size, smem) : e;
+    cudaError_t e = prepare_search_nt<kSearchNarrowThreads, 2>(group_size, smem);
+    if (e == cudaSuccess) e = prepare_search_wide(group_size, smem);
+    return e == cudaSuccess ? prepare_search_solo(group_size, smem) : e;
 }
 
-cudaError_t search_occupancy(int group_size, int threads, size_t smem, int csize, int *units, bool prefix) {
+cudaError_t search_occupancy(int group_size, int threads, size_t smem, int csize, int *units, bool prefix,
+                             bool solo) {
+    if (solo) return search_occupancy_solo(group_size, threads, smem, csize, units, prefix);
     if (threads > kSearchNarrowThreads)
         return search_occupancy_wide(group_size, threads, smem, csize, units, prefix);
-    return search_occupancy_nt<kSearchNarrowThreads>(group_size, threads, smem, csize, units, prefix);
+    return search_occupancy_nt<kSearchNarrowThreads, 2>(group_size, threads, smem, csize, units, prefix);
 }
 
 cudaError_t launch_search(int group_size, const LaunchItem *items, int count, int *queue, int move_cap,
                           int blocks, int threads, size_t smem, cudaStream_t st, int csize, bool prefix,
-                          int *gsnap, int gsnap_words, SliceSched sl) {
+                          int *gsnap, int gsnap_words, SliceSched sl, bool solo) {
+    if (solo)
+        return launch_search_solo(group_size, items, count, queue, move_cap, blocks, threads, smem, st, csize,
+                                  prefix, gsnap, gsnap_words, sl);
     if (threads > kSearchNarrowThreads)
         return launch_search_wide(group_size, items, count, queue, move_cap, blocks, threads, smem, st, csize,
                                   prefix, gsnap, gsnap_words, sl);
-    return launch_search_nt<kSearchNarrowThreads>(group_size, items, count, queue, move_cap, blocks, threads, smem,
-                                                  st, csize, prefix, gsnap, gsnap_words, sl);
+    return launch_search_nt<kSearchNarrowThreads, 2>(group_size, items, count, queue, move_cap, blocks, threads,
+                                                     smem, st, csize, prefix, gsnap, gsnap_words, sl);
 }
 
 cudaError_t launch_evaluate(int group_size, const LaunchItem &item, const int32_t *lists, int count,

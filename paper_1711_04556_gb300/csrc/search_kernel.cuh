@@ -97,10 +97,12 @@ __device__ int slice_wait(int *sync, int s) {
 // cluster barrier reads the other CTAs' keys through distributed shared
 // memory; all CTAs then apply the same move.  Rank 0 pops the work queue,
 // sums the counters and writes the results.  NT is the most threads a CTA
-// may have; two CTAs of NT threads share an SM's registers.
+// may have; MB CTAs of NT threads share an SM's registers (MB = 1: a build
+// for launches whose shared memory holds one CTA per SM anyway, which may
+// then take up to twice the registers).
 // ---------------------------------------------------------------------------
-template <int G, bool PFX, int NT>
-__global__ void __launch_bounds__(NT, 2) search_kernel(const LaunchItem *__restrict__ items, int count,
+template <int G, bool PFX, int NT, int MB>
+__global__ void __launch_bounds__(NT, MB) search_kernel(const LaunchItem *__restrict__ items, int count,
                                                       int *__restrict__ queue, int move_cap, int csize,
                                                       int *__restrict__ gsnap, int gsnap_words, SliceSched sl) {
     extern __shared__ __align__(16) int sm[];
@@ -439,20 +441,20 @@ __global__ void __launch_bounds__(NT, 2) search_kernel(const LaunchItem *__restr
     }
 }
 
-template <int G, int NT>
+template <int G, int NT, int MB>
 cudaError_t prepare_search_g(size_t smem) {
-    cudaError_t e = cudaFuncSetAttribute(search_kernel<G, false, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(search_kernel<G, false, NT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(search_kernel<G, true, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(search_kernel<G, true, NT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(smem));
     return e;
 }
 
-template <int G, bool PFX, int NT>
+template <int G, bool PFX, int NT, int MB>
 cudaError_t occupancy_g(int threads, size_t smem, int csize, int *units) {
     if (csize <= 1)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(units, search_kernel<G, PFX, NT>, threads, smem);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(units, search_kernel<G, PFX, NT, MB>, threads, smem);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(csize);
     cfg.blockDim = dim3(threads);
@@ -464,15 +466,15 @@ cudaError_t occupancy_g(int threads, size_t smem, int csize, int *units) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaOccupancyMaxActiveClusters(units, search_kernel<G, PFX, NT>, &cfg);
+    return cudaOccupancyMaxActiveClusters(units, search_kernel<G, PFX, NT, MB>, &cfg);
 }
 
-template <int G, bool PFX, int NT>
+template <int G, bool PFX, int NT, int MB>
 cudaError_t launch_search_g(const LaunchItem *items, int count, int *queue, int move_cap, int blocks,
                             int threads, size_t smem, cudaStream_t st, int csize, int *gsnap, int gsnap_words,
                             SliceSched sl) {
     if (csize <= 1) {
-        search_kernel<G, PFX, NT><<<blocks, threads, smem, st>>>(items, count, queue, move_cap, 1, gsnap, gsnap_words,
+        search_kernel<G, PFX, NT, MB><<<blocks, threads, smem, st>>>(items, count, queue, move_cap, 1, gsnap, gsnap_words,
                                                                  sl);
         return cudaGetLastError();
     }
@@ -488,7 +490,7 @@ cudaError_t launch_search_g(const LaunchItem *items, int count, int *queue, int 
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, search_kernel<G, PFX, NT>, items, count, queue, move_cap, csize, gsnap,
+    return cudaLaunchKernelEx(&cfg, search_kernel<G, PFX, NT, MB>, items, count, queue, move_cap, csize, gsnap,
                               gsnap_words, sl);
 }
 
@@ -503,36 +505,43 @@ cudaError_t launch_search_g(const LaunchItem *items, int count, int *queue, int 
         default: return cudaErrorInvalidValue;     \
     }
 
-// The entry points of one thread bound NT, for every group size.
-template <int NT>
+// The entry points of one build (thread bound NT, MB CTAs per SM), for
+// every group size.
+template <int NT, int MB>
 cudaError_t prepare_search_nt(int group_size, size_t smem) {
-    RCPSP_DISPATCH_G(group_size, return (prepare_search_g<GG, NT>(smem)))
+    RCPSP_DISPATCH_G(group_size, return (prepare_search_g<GG, NT, MB>(smem)))
 }
 
-template <int NT>
+template <int NT, int MB>
 cudaError_t search_occupancy_nt(int group_size, int threads, size_t smem, int csize, int *units, bool prefix) {
-    if (prefix) RCPSP_DISPATCH_G(group_size, return (occupancy_g<GG, true, NT>(threads, smem, csize, units)))
-    RCPSP_DISPATCH_G(group_size, return (occupancy_g<GG, false, NT>(threads, smem, csize, units)))
+    if (prefix) RCPSP_DISPATCH_G(group_size, return (occupancy_g<GG, true, NT, MB>(threads, smem, csize, units)))
+    RCPSP_DISPATCH_G(group_size, return (occupancy_g<GG, false, NT, MB>(threads, smem, csize, units)))
 }
 
-template <int NT>
+template <int NT, int MB>
 cudaError_t launch_search_nt(int group_size, const LaunchItem *items, int count, int *queue, int move_cap,
                              int blocks, int threads, size_t smem, cudaStream_t st, int csize, bool prefix,
                              int *gsnap, int gsnap_words, SliceSched sl) {
     if (prefix)
-        RCPSP_DISPATCH_G(group_size, return (launch_search_g<GG, true, NT>(items, count, queue, move_cap, blocks,
+        RCPSP_DISPATCH_G(group_size, return (launch_search_g<GG, true, NT, MB>(items, count, queue, move_cap, blocks,
                                                                            threads, smem, st, csize, gsnap,
                                                                            gsnap_words, sl)))
-    RCPSP_DISPATCH_G(group_size, return (launch_search_g<GG, false, NT>(items, count, queue, move_cap, blocks,
+    RCPSP_DISPATCH_G(group_size, return (launch_search_g<GG, false, NT, MB>(items, count, queue, move_cap, blocks,
                                                                         threads, smem, st, csize, nullptr, 0, sl)))
 }
 
 }  // namespace
 
-// The 512-thread instances (search_kernel_wide.cu).
+// The 512-thread instances (search_kernel_wide.cu) and the one-CTA-per-SM
+// instances (search_kernel_solo.cu).
 cudaError_t prepare_search_wide(int group_size, size_t smem);
 cudaError_t search_occupancy_wide(int group_size, int threads, size_t smem, int csize, int *units, bool prefix);
 cudaError_t launch_search_wide(int group_size, const LaunchItem *items, int count, int *queue, int move_cap,
+                               int blocks, int threads, size_t smem, cudaStream_t st, int csize, bool prefix,
+                               int *gsnap, int gsnap_words, SliceSched sl);
+cudaError_t prepare_search_solo(int group_size, size_t smem);
+cudaError_t search_occupancy_solo(int group_size, int threads, size_t smem, int csize, int *units, bool prefix);
+cudaError_t launch_search_solo(int group_size, const LaunchItem *items, int count, int *queue, int move_cap,
                                int blocks, int threads, size_t smem, cudaStream_t st, int csize, bool prefix,
                                int *gsnap, int gsnap_words, SliceSched sl);
 
