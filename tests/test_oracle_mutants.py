@@ -63,6 +63,8 @@ MUTANTS = {
     "write_ic_without_read_ic": ("f->IC = x->ICread + x->since;", "f->IC = x->since;"),
     # a block's aspiration threshold its own best instead of C*_max (reading C2)
     "aspiration_block_best": ("if (tabu && !(c < Casp)) continue;", "if (tabu && !(c < x->Cbb)) continue;"),
+    # a successor released one step after its predecessor's finish (feasible, but leaves idle steps)
+    "precedence_lag": ("es_prec = imax(es_prec, S[j] + in->dur[j]);", "es_prec = imax(es_prec, S[j] + in->dur[j] + 1);"),
     # an empty iteration (no admissible move) does not advance the tabu list
     "empty_move_stalls": ("writeIndex = (writeIndex + 1) % p->tabu_len;\n        if (found && C < Cbest)",
                           "writeIndex = (writeIndex + found) % p->tabu_len;\n        if (found && C < Cbest)"),
@@ -120,6 +122,12 @@ def test_mutant_alg5_breaks_earliest_fit_pin(oracle, tmp_path):
     with mutant(oracle, tmp_path, "alg5_no_restart"):
         with pytest.raises(AssertionError):
             pins.test_decoders_on_random_lists(oracle)
+
+
+def test_mutant_precedence_lag_breaks_no_idle_pin(oracle, tmp_path):
+    with mutant(oracle, tmp_path, "precedence_lag"):
+        with pytest.raises(AssertionError):
+            pins.test_serial_sgs_leaves_no_idle_step(oracle)
 
 
 def test_mutant_eq8_weights_break_closed_forms(oracle, tmp_path):

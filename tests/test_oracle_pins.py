@@ -265,6 +265,30 @@ def test_decoders_on_random_lists(oracle):
             assert c_cap == c_env and S_c.tolist() == S_env.tolist()
 
 
+def test_serial_sgs_leaves_no_idle_step(oracle):
+    """Every step before the makespan is covered by some activity of
+    positive duration, whichever evaluator decodes and whatever the list.
+    (Take an idle step t and, among the activities that start after it, the
+    first in list order: everything scheduled before it ends by t, so its
+    predecessors do and the resources are free from t on, and the serial
+    SGS would have started it by t.)  It is why no horizon below
+    UB = sum d_i holds for every list, and why the makespan never exceeds UB."""
+    rng = np.random.default_rng(23)
+    insts = medium_instances(20, first=400) + small_instances(60, n=7, m=2, dmax=4, rmax=4, first=900)
+    for inst in insts:
+        ub = int(sum(inst.dur))
+        for _ in range(4):
+            W = random_feasible_list(inst, rng)
+            for mode in (1, 2):
+                cmax, S, _ = oracle.decode(inst, W, mode)
+                assert cmax <= ub
+                covered = np.zeros(max(cmax, 1), bool)
+                for i in range(inst.n):
+                    if inst.dur[i] > 0:
+                        covered[S[i]:S[i] + inst.dur[i]] = True
+                assert cmax == 0 or covered[:cmax].all(), (mode, np.flatnonzero(~covered[:cmax])[:5])
+
+
 def test_capacity_work_counter_matches_envelopes(oracle):
     """The capacity-indexed work count (Alg. 4 loop steps) equals the one
     read off explicit usage envelopes."""
