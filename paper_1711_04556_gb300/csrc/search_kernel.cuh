@@ -1,6 +1,7 @@
 // sm_103a tabu search kernel for the RCPSP (Bukata, Sucha, Hanzalek), the
-// template shared by search_kernel.cu (CTAs of up to 384 threads) and
-// search_kernel_wide.cu (up to 512), which compile in parallel.
+// template shared by search_kernel.cu (CTAs of up to 384 threads, two per
+// SM), search_kernel_wide.cu (up to 512, two per SM) and
+// search_kernel_solo.cu (up to 512, one per SM), which compile in parallel.
 //
 // One persistent CTA runs one search at a time and pops the next instance
 // from a device work queue when it is done (Sec. 6: one block = one tabu
@@ -26,11 +27,11 @@
 //   4. warp-shuffle min, then a shared-memory atomicMin, give the move;
 //   5. one thread applies it and updates the simple tabu list (Alg. 3).
 //
-// The work queue is a single atomicAdd.  The kernel waits on another CTA in
-// two places only, each bounded: a sliced launch (SliceSched) may pop a
-// slice whose previous slice another CTA is still running, and with prefix
-// reuse a neighbour decode may wait for a kept state that warp 0 is still
-// writing.  Internal inconsistencies set an error word that the host reads
+// The work queue is a single atomicAdd.  The kernel waits in two places
+// only, each bounded by the global timer: a CTA of a sliced launch
+// (SliceSched) may pop a slice whose previous slice another CTA is still
+// running, and with prefix reuse a warp's neighbour decodes may wait for a
+// kept state that warp 0 of the same CTA is still writing.  Internal inconsistencies set an error word that the host reads
 // as a status.
 #pragma once
 
